@@ -1,0 +1,21 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA device (GB300, sm_103a)")
+
+
+@pytest.fixture(scope="session")
+def lib():
+    """The CUDA library's Python binding, built in-tree if needed."""
+    from paper_2505_02438_gb300 import build as _b
+    _b.build_library()
+    import paper_2505_02438_gb300 as pkg
+    return pkg
