@@ -1,0 +1,344 @@
+"""Benchmark of the SIMP assembly hot path on GB300.
+
+One step = one iteration's hot path on one synthetic design: K(rho) into the
+fixed CSR pattern plus the element sensitivities dc and the compliance c
+(Sec. 2.2, Appendix D).  The default workload is the 3D cantilever box,
+120 x 40 x 40 trilinear hexahedra (192,000 cells, 610,203 dofs, 47,568,609
+nonzeros), FP64, rho ~ U(0.001, 1), u ~ N(0, 1), seeded.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  N > 1 runs under torchrun, one rank per GPU, each rank
+solving its own copy of the design (independent problems: weak scaling, no
+collective on the data path).  --impl reference times the plain FP64 CPU
+oracle (the reference implementation of this build) on a bounded sample of the
+same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "K(ρ) assembly GNNZ/s + sensitivity elems/s, % HBM peak; served p50/p99 ms"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def workload(name):
+    from paper_2505_02438_gb300 import workloads as W
+    if name == "hex":
+        return W.cantilever_hex(120, 40, 40)
+    if name == "tet":
+        return W.jittered_tet(60, 20, 20)
+    if name == "tri":
+        return W.jittered_tri(400, 200)
+    if name == "q4":
+        return W.mbb_q4(60, 20)
+    raise ValueError(name)
+
+
+def algorithmic_bytes(wl, nnz, ndof):
+    """Minimum bytes one step must move: write K values and dc, read rho, u,
+    the connectivity and the coordinates."""
+    nc, nv = wl.cells.shape
+    return dict(
+        step=8 * nnz + 16 * nc + 8 * ndof + 4 * nc * nv + 8 * wl.dim * len(wl.coords),
+        assemble=8 * nnz + 8 * nc + 4 * nc * nv + 8 * wl.dim * len(wl.coords),
+        sensitivity=16 * nc + 8 * ndof + 4 * nc * nv + 8 * wl.dim * len(wl.coords),
+    )
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", "soptx_clocks_%d_%d.csv" % (os.getpid(), gpu_index))
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def traffic_record(kernel_file, kernel_name):
+    """dram bytes per launch of `kernel_name` from the committed ncu summary,
+    valid only while the kernel source is unchanged (its sha256 matches)."""
+    src = os.path.join(ROOT, "paper_2505_02438_gb300", "csrc", kernel_file)
+    rec = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not (os.path.exists(src) and os.path.exists(rec)):
+        return None
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for line in open(rec):
+        kv = dict(x.split("=", 1) for x in line.split() if "=" in x)
+        if kv.get("kernel") == kernel_name and kv.get("source_sha") == h:
+            return float(kv["dram_bytes_per_launch"])
+    return None
+
+
+def cpu_oracle_sample(wl_name, budget_s):
+    """The oracle as it stands (single thread) on a sub-box of the workload
+    sized to about budget_s seconds; returns (GNNZ/s, description)."""
+    import oracle
+    from paper_2505_02438_gb300 import workloads as W
+    rate = 1.9e6   # nnz/s of the oracle on one x86 core (assembly + sensitivity)
+    target = max(budget_s * rate, 2e3)
+    if wl_name == "hex":
+        nx = 1
+        while nx < 120 and 243 * (nx + 2) * 41 * 41 <= target:
+            nx += 1
+        ny = nz = 40
+        if 243 * (nx + 1) * 41 * 41 > target:
+            s = max(1, int(round((target / 243 / 3) ** (1 / 3))) - 1)
+            nx, ny, nz = min(120, 3 * s), s, s
+        wl = W.cantilever_hex(nx, ny, nz)
+    else:
+        wl = workload(wl_name)
+    t0 = time.perf_counter()
+    rp, ci, v, ndof = oracle.assemble(wl.cell, wl.order, wl.coords, wl.cells, wl.mat, wl.rho)
+    u = wl.displacement(ndof)
+    oracle.sensitivity(wl.cell, wl.order, wl.coords, wl.cells, wl.mat, wl.rho, u)
+    dt = time.perf_counter() - t0
+    return len(v) / dt / 1e9, "%s sub-box (%d cells, %d nnz), assembly + sensitivity, %.2f s" % (
+        wl.name, len(wl.cells), len(v), dt)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    budget = min(2.0, 120.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_oracle_sample(args.workload, budget)
+    total, desc = 0.0, ""
+    rates = []
+    for _ in range(args.steps):
+        r, desc = cpu_oracle_sample(args.workload, budget)
+        rates.append(r)
+    value = float(np.mean(rates))
+    line = {"metric": METRIC, "impl": "reference", "value": value, "unit": "GNNZ/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC[args.workload], "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "GNNZ/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "GNNZ/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+WORKLOAD_DESC = {
+    "hex": "3D cantilever box 120x40x40 trilinear hex Q1 (192,000 cells, 610,203 dofs), FP64 K(rho) CSR + dc + c",
+    "tet": "Kuhn P2 tetrahedra 60x20x20x6 (144,000 cells), jittered, FP64 K(rho) CSR + dc + c",
+    "tri": "P3 triangles 400x200x2 (160,000 cells), jittered, FP64 K(rho) CSR + dc + c",
+    "q4": "Q4 plane stress 60x20 (1,200 cells), FP64 K(rho) CSR + dc + c",
+}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2505_02438_gb300 as P
+    from paper_2505_02438_gb300 import build as B
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if rank == 0:
+        B.build_library()
+    if world > 1:
+        torch.distributed.barrier()
+    wl = workload(args.workload)
+    t0 = time.perf_counter()
+    mesh = P.Mesh.from_workload(wl, elem_prec=args.elem_prec)
+    setup_s = time.perf_counter() - t0
+    nnz, ndof, nc = mesh.nnz, mesh.ndof, mesh.n_cells
+    rho = torch.as_tensor(wl.rho, device=dev)
+    u = torch.as_tensor(wl.displacement(ndof), device=dev)
+    vals = torch.empty(nnz, dtype=torch.float64, device=dev)
+    dc = torch.empty(nc, dtype=torch.float64, device=dev)
+    c = torch.empty(1, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        mesh.assemble_K(rho, vals)
+        mesh.sensitivity(rho, u, dc, c)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    sampler = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else local_rank)
+    with sampler:
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for k in range(K):
+            flush.zero_()                       # L2 flush between steps (not timed)
+            ev[k][0].record(stream)
+            mesh.assemble_K(rho, vals)
+            ev[k][1].record(stream)
+            mesh.sensitivity(rho, u, dc, c)
+            ev[k][2].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        wall = time.perf_counter() - wall0
+    asm_ms = sum(e[0].elapsed_time(e[1]) for e in ev)
+    sens_ms = sum(e[1].elapsed_time(e[2]) for e in ev)
+    step_ms = asm_ms + sens_ms
+    t = torch.tensor([step_ms, asm_ms, sens_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    step_ms, asm_ms, sens_ms = [float(x) for x in t.cpu()]
+    clocks = sampler.summary()
+
+    # end to end: pinned host inputs -> device, step, dc and c back to the host
+    n_e2e = min(K, 200)
+    rho_h = torch.as_tensor(wl.rho).pin_memory()
+    u_h = u.cpu().pin_memory()
+    dc_h = torch.empty(nc, dtype=torch.float64).pin_memory()
+    c_h = torch.empty(1, dtype=torch.float64).pin_memory()
+    rho_d = torch.empty_like(rho)
+    u_d = torch.empty_like(u)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_ms = 0.0
+    for k in range(n_e2e):
+        flush.zero_()
+        e0.record(stream)
+        rho_d.copy_(rho_h, non_blocking=True)
+        u_d.copy_(u_h, non_blocking=True)
+        mesh.step(rho_d, u_d, vals, dc, c)
+        dc_h.copy_(dc, non_blocking=True)
+        c_h.copy_(c, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+    e2e_ms = float(te.item())
+
+    if rank != 0:
+        return
+    ab = algorithmic_bytes(wl, nnz, ndof)
+    peak, peak_kind = peaks()
+    asm_avg_s = asm_ms / K / 1e3
+    achieved = ab["assemble"] / asm_avg_s / 1e9
+    kernel_name = "k_lattice_assemble" if mesh.path == "lattice" else "k_assemble_gather"
+    kernel_file = "lattice.cu" if mesh.path == "lattice" else "kernels.cu"
+    traffic = traffic_record(kernel_file, kernel_name)
+    value = world * nnz * K / (step_ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "GNNZ/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": step_ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.elem_prec == "fp64" else "f32-elem/f64-acc",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC[args.workload], "path": mesh.path, "nnz": nnz, "ndof": ndof,
+                   "n_cells": nc, "elem_prec": args.elem_prec, "l2": "flushed (256 MiB write) between steps",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "sens_elems_per_s": world * nc * K / (step_ms / 1e3),
+        "assemble_ms": asm_ms / K, "sensitivity_ms": sens_ms / K, "setup_s": setup_s,
+        "step_alg_bytes": ab["step"], "step_hbm_frac": ab["step"] / (step_ms / K / 1e3) / 1e9 / peak,
+        "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "alg_bytes_per_launch": ab["assemble"]},
+        "clocks": clocks,
+        "e2e": {"value": world * nnz * n_e2e / (e2e_ms / 1e3) / 1e9, "unit": "GNNZ/s",
+                "h2d_bytes_per_step": 8 * (nc + ndof), "d2h_bytes_per_step": 8 * (nc + 1),
+                "steps": n_e2e},
+        "gpu_launches": 3 * K,
+        "wall_s_timed_region": wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        r, desc = cpu_oracle_sample(args.workload, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": r, "unit": "GNNZ/s", "cores": 1, "kind": "oracle", "sample": desc}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="hex", choices=sorted(WORKLOAD_DESC))
+    ap.add_argument("--elem-prec", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

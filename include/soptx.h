@@ -1,0 +1,206 @@
+/*
+ * soptx.h -- C ABI of the GB300 (sm_103a) SIMP stiffness-assembly library.
+ *
+ * The library computes, on one GPU, the per-iteration hot path of density-based
+ * topology optimisation with the modified SIMP model (SOPTX, arXiv 2505.02438):
+ *
+ *   E(rho_e)  = Emin + rho_e^p (E0 - Emin)                       (Sec. 2.1)
+ *   K(rho)    = sum_e E(rho_e) K_e^0   into a fixed CSR pattern   (Sec. 2.2)
+ *   dc_e      = -p rho_e^(p-1) (E0 - Emin) u_e^T K_e^0 u_e        (Appendix D)
+ *   c         = sum_e E(rho_e) u_e^T K_e^0 u_e  (= u^T K(rho) u)
+ *
+ * where K_e^0 is the linear-elasticity element matrix at unit Young's modulus
+ * (Sec. 2.2).  Following the paper's fast / symbolic-fast assembly (Sec. 3.2.2,
+ * Sec. 5.5), the element-independent part (exact reference-cell integrals of
+ * basis-gradient products) is computed once per mesh and contracted with each
+ * element's Jacobian; everything that does not depend on rho is kept resident
+ * on the device between calls.
+ *
+ * Conventions shared by every call:
+ *  - Pointers named d_* are DEVICE pointers owned by the caller (contiguous,
+ *    dtype as declared).  Pointers without the prefix are host pointers.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Every call except soptx_mesh_create / soptx_mesh_destroy only
+ *    enqueues work on `stream` and returns without synchronising.
+ *  - A mesh owns a small device scratch area, so calls on ONE mesh must be
+ *    ordered on the device (same stream, or explicit events); calls on
+ *    different meshes may overlap freely.
+ *  - No call aborts, traps or prints.  On failure the call returns a non-zero
+ *    soptx_status and soptx_last_error() describes it (thread-local).
+ *  - Degrees of freedom are node-interleaved: dof = dim * node + component.
+ *  - Cells: dim 2 = SOPTX_TRI / SOPTX_QUAD, dim 3 = SOPTX_TET / SOPTX_HEX.
+ *    Vertex order inside a cell: simplices list the vertex at the reference
+ *    origin first, then the vertices at the unit vectors e_1..e_d (either
+ *    orientation is accepted; |det J| is used); quads and hexes list their
+ *    corners lexicographically on the unit square / cube, x fastest, and must
+ *    be parallelograms / parallelepipeds (affine), so that reference integrals
+ *    are exact.
+ *  - Lagrange order 1..3.  Higher-order nodes are numbered after the vertices:
+ *    edge nodes (edges sorted by (min vertex id, max vertex id), the order-1
+ *    nodes of an edge running from the min-id vertex to the max-id vertex),
+ *    then face nodes of 3D cells (faces sorted by their sorted vertex ids; on a
+ *    quad face the nodes run in the frame of its smallest vertex o, first axis
+ *    toward the smaller-id neighbour of o), then interior nodes cell by cell.
+ *  - The CSR pattern is the full symmetric structural pattern over all dofs
+ *    (no boundary-condition elimination), column indices sorted ascending per
+ *    row; entries that cancel to zero are kept.
+ */
+#ifndef SOPTX_H
+#define SOPTX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SOPTX_OK = 0,
+    SOPTX_EINVAL = 1,     /* an argument is invalid (see soptx_last_error)   */
+    SOPTX_ENOMEM = 2,     /* a device or host allocation failed              */
+    SOPTX_ECUDA = 3,      /* a CUDA runtime call failed                      */
+    SOPTX_EBUSY = 4,      /* server: no slot and the queue is full           */
+    SOPTX_ETIMEOUT = 5,   /* server: a bounded wait ran out                  */
+    SOPTX_ENOTFOUND = 6,  /* server: unknown ticket                          */
+    SOPTX_EINTERNAL = 7   /* a device-side consistency check failed          */
+} soptx_status;
+
+typedef enum { SOPTX_TRI = 0, SOPTX_TET = 1, SOPTX_QUAD = 2, SOPTX_HEX = 3 } soptx_cell;
+
+/* Precision of the element matrices K_e^0.  The CSR accumulation, the
+ * sensitivities and c are FP64-accurate in both modes (Sec. 2.2 is stated in
+ * exact arithmetic; the paper fixes no precision). */
+typedef enum { SOPTX_ELEM_FP64 = 0, SOPTX_ELEM_FP32 = 1 } soptx_elem_prec;
+
+/* Modified SIMP material (Sec. 2.1, Sec. 3.2.1): E0 solid modulus, Emin void
+ * modulus (the paper uses 1e-9 E0), nu Poisson ratio, p penalisation.  In 2D,
+ * plane_strain = 0 selects plane stress (unit thickness). */
+typedef struct {
+    double E0, Emin, nu, p;
+    int32_t plane_strain;
+} soptx_material;
+
+typedef struct soptx_mesh_s *soptx_mesh;
+
+/* Which device path a mesh was given (soptx_mesh_path). */
+typedef enum {
+    SOPTX_PATH_LATTICE = 0,   /* order-1 box lattice: implicit maps, one K^0   */
+    SOPTX_PATH_UNIFORM = 1,   /* every cell has the same Jacobian: one K^0     */
+    SOPTX_PATH_CACHED = 2     /* per-cell K_e^0 cached on the device           */
+} soptx_path;
+
+/*
+ * Build a device-resident mesh (Sec. 3.2.2 "fast matrix assembly": everything
+ * independent of rho is computed here, once).
+ *   dim, cell, order : 2/3, cell type, Lagrange order 1..3
+ *   coords           : host, float64 [n_vertices][dim]
+ *   cell_vertices    : host, int32 [n_cells][nv] (nv = 3, 4, 4, 8 for
+ *                      TRI, TET, QUAD, HEX), ids in [0, n_vertices)
+ *   mat              : host, material; nu in (-1, 0.5), p >= 1, E0 > Emin >= 0
+ *   prec             : element-matrix precision
+ *   stream           : stream for the setup copies and kernels
+ *   out              : receives the mesh handle
+ * Allocates device memory (reported by soptx_mesh_device_bytes) and
+ * synchronises `stream`.  Errors: EINVAL (bad sizes, ids, degenerate or
+ * non-affine cell, ndof >= 2^31), ENOMEM, ECUDA.  n_cells = 0 is allowed.
+ */
+soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order,
+                               int64_t n_vertices, const double *coords,
+                               int64_t n_cells, const int32_t *cell_vertices,
+                               const soptx_material *mat, soptx_elem_prec prec,
+                               void *stream, soptx_mesh *out);
+
+/* Sizes: ndof = dim * n_nodes, nnz of the CSR pattern, n_cells, local dofs per
+ * cell.  Any output pointer may be NULL. */
+soptx_status soptx_mesh_info(soptx_mesh mesh, int64_t *ndof, int64_t *nnz,
+                             int64_t *n_cells, int32_t *ldof);
+
+/* Borrowed device pointers, valid until soptx_mesh_destroy:
+ * d_indptr int64 [ndof+1], d_indices int32 [nnz]. */
+soptx_status soptx_mesh_pattern(soptx_mesh mesh, const int64_t **d_indptr,
+                                const int32_t **d_indices);
+
+/* Borrowed device pointer to the cell -> node map, int32 [n_cells][nb]
+ * (nb = ldof / dim); dof of (cell e, local node a, component i) is
+ * dim * map[e][a] + i.  The local node order is the library's own. */
+soptx_status soptx_mesh_cell_nodes(soptx_mesh mesh, const int32_t **d_cell_nodes, int32_t *nb);
+
+/* Copy the pattern / cell -> node map into caller-owned device buffers
+ * (d_indptr int64 [ndof+1], d_indices int32 [nnz], d_cell_nodes int32
+ * [n_cells][nb]); enqueued on `stream`.  Either pattern pointer may be NULL. */
+soptx_status soptx_mesh_copy_pattern(soptx_mesh mesh, int64_t *d_indptr, int32_t *d_indices, void *stream);
+soptx_status soptx_mesh_copy_cell_nodes(soptx_mesh mesh, int32_t *d_cell_nodes, void *stream);
+
+/* Device path chosen for the mesh and the device bytes the mesh holds. */
+soptx_status soptx_mesh_path(soptx_mesh mesh, soptx_path *path);
+soptx_status soptx_mesh_device_bytes(soptx_mesh mesh, int64_t *bytes);
+
+/*
+ * K(rho) = sum_e E(rho_e) K_e^0 into the mesh's CSR pattern (Sec. 2.2).
+ *   d_rho  : device float64 [n_cells], element densities (any real values;
+ *            the SIMP power is evaluated as given)
+ *   d_vals : device float64 [nnz], overwritten with the CSR values
+ * Each value is the sum of its element contributions in ascending element
+ * order, without atomics: the result is bitwise reproducible run to run.
+ */
+soptx_status soptx_assemble_K(soptx_mesh mesh, const double *d_rho, double *d_vals, void *stream);
+
+/*
+ * Element compliance sensitivities (Appendix D; Sec. 2.2):
+ *   d_dc[e] = -p rho_e^(p-1) (E0 - Emin) u_e^T K_e^0 u_e
+ *   *d_c    = sum_e E(rho_e) u_e^T K_e^0 u_e   (skipped when d_c is NULL)
+ *   d_u    : device float64 [ndof]
+ *   d_dc   : device float64 [n_cells]
+ *   d_c    : device float64 [1] or NULL; summed in a fixed order.
+ */
+soptx_status soptx_sensitivity(soptx_mesh mesh, const double *d_rho, const double *d_u,
+                               double *d_dc, double *d_c, void *stream);
+
+/* One pass that produces both K(rho) and the sensitivities (the per-iteration
+ * step); same arguments and results as the two calls above. */
+soptx_status soptx_assemble_and_sensitivity(soptx_mesh mesh, const double *d_rho,
+                                            const double *d_u, double *d_vals,
+                                            double *d_dc, double *d_c, void *stream);
+
+/*
+ * Backward of f(rho, u) = u^T K(rho) u (the compliance written as a function
+ * of an independent u) scaled by the incoming gradient g = *d_gout:
+ *   d_grad_rho[e] = g p rho_e^(p-1) (E0 - Emin) u_e^T K_e^0 u_e   (= -g dc_e)
+ *   d_grad_u      = 2 g K(rho) u          (skipped when d_grad_u is NULL)
+ * d_gout is a device float64 [1]; d_grad_rho [n_cells]; d_grad_u [ndof].
+ */
+soptx_status soptx_compliance_vjp(soptx_mesh mesh, const double *d_rho, const double *d_u,
+                                  const double *d_gout, double *d_grad_rho, double *d_grad_u,
+                                  void *stream);
+
+/* Frees the mesh's device memory (synchronises the device first). */
+soptx_status soptx_mesh_destroy(soptx_mesh mesh);
+
+/*
+ * Host-only planning (no device work, usable without a GPU): runs the same
+ * validation, numbering and pattern construction as soptx_mesh_create and
+ * returns the sizes and, for non-NULL host buffers, the results:
+ *   indptr int64 [ndof+1], indices int32 [nnz], cell_nodes int32 [n_cells][nb],
+ *   *path the device path a mesh would take.  Call once with NULL buffers to
+ *   learn ndof / nnz, then again with buffers of those sizes.
+ */
+soptx_status soptx_host_plan(int dim, soptx_cell cell, int order, int64_t n_vertices,
+                             const double *coords, int64_t n_cells, const int32_t *cell_vertices,
+                             int64_t *ndof, int64_t *nnz, int32_t *nb, soptx_path *path,
+                             int64_t *indptr, int32_t *indices, int32_t *cell_nodes);
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char *soptx_last_error(void);
+
+/* Library version string. */
+const char *soptx_version(void);
+
+/* Test hook for failure handling: the n-th device allocation from now on
+ * (n >= 1) fails as if the device were out of memory; n <= 0 disables. */
+void soptx_debug_fail_alloc_after(int64_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SOPTX_H */

@@ -53,9 +53,9 @@ def _L():
         lib.or_number.argtypes = [i32, i32, i64, i64, P, P, P]
         lib.or_node_coords.argtypes = [i32, i32, i64, P, P, P, i64, P]
         lib.or_assemble_rows.argtypes = [i32, i32, i64, P, i64, P, dbl, dbl, dbl, dbl, i32,
-                                         P, i64, P, P, P, P, P, P]
+                                         P, i64, P, i32, P, P, P, P, P]
         lib.or_sensitivity.argtypes = [i32, i32, i64, P, i64, P, dbl, dbl, dbl, dbl, i32,
-                                       P, P, i64, P, P, P, P]
+                                       P, P, i64, P, P, P, P, P]
         lib.or_compliance_vjp.argtypes = [i32, i32, i64, P, i64, P, dbl, dbl, dbl, dbl, i32,
                                           P, P, dbl, P, P]
         lib.or_free.argtypes = [P]
@@ -142,9 +142,10 @@ def node_coords(cell, k, coords, cells):
     return xn
 
 
-def assemble(cell, k, coords, cells, mat, rho, rows=None):
+def assemble(cell, k, coords, cells, mat, rho, rows=None, absval=False):
     """K(rho) in CSR.  rows=None: every row; else only the listed dof rows, in
-    that order.  Returns (rowptr int64, cols int32, vals float64, ndof)."""
+    that order.  absval=True sums |E_e K_e^0[a,b]| instead (the per-entry
+    rounding scale).  Returns (rowptr int64, cols int32, vals float64, ndof)."""
     lib = _L()
     coords = np.ascontiguousarray(coords, np.float64)
     cells = np.ascontiguousarray(cells, np.int32)
@@ -162,7 +163,7 @@ def assemble(cell, k, coords, cells, mat, rho, rows=None):
     vv = ctypes.POINTER(ctypes.c_double)()
     rc = lib.or_assemble_rows(CELL[cell], k, len(coords), _p(coords), len(cells), _p(cells),
                               E0, Emin, nu, p, int(ps), _p(rho), nsel,
-                              _p(sel) if sel is not None else None,
+                              _p(sel) if sel is not None else None, int(bool(absval)),
                               ctypes.byref(nnz), ctypes.byref(rp), ctypes.byref(ci),
                               ctypes.byref(vv), ctypes.byref(ndof))
     _check(rc, "assemble")
@@ -175,9 +176,10 @@ def assemble(cell, k, coords, cells, mat, rho, rows=None):
     return rowptr, cols, vals, ndof.value
 
 
-def sensitivity(cell, k, coords, cells, mat, rho, u, sel=None):
+def sensitivity(cell, k, coords, cells, mat, rho, u, sel=None, with_abs=False):
     """(dc, s, c): dc_e = -E'(rho_e) s_e, s_e = u_e^T K_e^0 u_e, c = sum_e E_e s_e
-    (c is NaN when only a subset of cells is selected)."""
+    (c is NaN when only a subset of cells is selected).  with_abs=True appends
+    sabs_e = sum_ab |u_a K_ab u_b| (the rounding scale of s_e)."""
     coords = np.ascontiguousarray(coords, np.float64)
     cells = np.ascontiguousarray(cells, np.int32)
     rho = np.ascontiguousarray(rho, np.float64)
@@ -190,10 +192,13 @@ def sensitivity(cell, k, coords, cells, mat, rho, u, sel=None):
         n, nsel, selp = len(sel), len(sel), _p(sel)
     dc = np.zeros(n)
     s = np.zeros(n)
+    sa = np.zeros(n)
     c = ctypes.c_double(0.0)
     _check(_L().or_sensitivity(CELL[cell], k, len(coords), _p(coords), len(cells), _p(cells),
                                E0, Emin, nu, p, int(ps), _p(rho), _p(u), nsel, selp,
-                               _p(dc), _p(s), ctypes.byref(c)), "sensitivity")
+                               _p(dc), _p(s), _p(sa), ctypes.byref(c)), "sensitivity")
+    if with_abs:
+        return dc, s, c.value, sa
     return dc, s, c.value
 
 

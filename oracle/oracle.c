@@ -704,6 +704,8 @@ static void cell_coords(const elem_ctx *c, const double *coords, const int32_t *
 
 /*
  * Assemble the rows sel[0..nsel) of K(rho) (nsel < 0: every row, in order).
+ * absval != 0 sums |E_e K_e^0[a][b]| instead: the scale against which a
+ * computed entry's rounding error is judged.
  * Outputs are malloc'ed here and released with or_free():
  *   rowptr [nrows+1] int64, cols [nnz] int32, vals [nnz] double.
  * Also returns ndof, and NN through nn_out (both may be NULL).
@@ -711,7 +713,7 @@ static void cell_coords(const elem_ctx *c, const double *coords, const int32_t *
 int or_assemble_rows(int cell, int k, int64_t nv_total, const double *coords,
                      int64_t nc, const int32_t *cv,
                      double E0, double Emin, double nu, double p, int plane_strain,
-                     const double *rho, int64_t nsel, const int64_t *sel,
+                     const double *rho, int64_t nsel, const int64_t *sel, int absval,
                      int64_t *nnz_out, int64_t **rowptr_out, int32_t **cols_out,
                      double **vals_out, int64_t *ndof_out)
 {
@@ -764,6 +766,7 @@ int or_assemble_rows(int cell, int k, int64_t nv_total, const double *coords,
                         T[t].col = d * (int64_t)cn[e * nb + b] + j;
                         T[t].seq = seq++;
                         T[t].val = Ee * Ke[(d * a + i) * ldof + d * b + j];
+                        if (absval) T[t].val = fabs(T[t].val);
                         t++;
                     }
             }
@@ -805,13 +808,14 @@ void or_free(void *ptr) { free(ptr); }
  *   s_e  = u_e^T K_e^0 u_e                      (strain-energy density form)
  *   dc_e = -E'(rho_e) s_e
  * and, when every cell is selected, c = sum_e E(rho_e) s_e in element order.
- * s_out may be NULL.
+ * s_out and sabs_out (sum_ab |u_a K_ab u_b|, the rounding-error scale of s_e)
+ * may be NULL.
  */
 int or_sensitivity(int cell, int k, int64_t nv_total, const double *coords,
                    int64_t nc, const int32_t *cv,
                    double E0, double Emin, double nu, double p, int plane_strain,
                    const double *rho, const double *u, int64_t nsel, const int64_t *sel,
-                   double *dc, double *s_out, double *c_out)
+                   double *dc, double *s_out, double *sabs_out, double *c_out)
 {
     if (!valid_cell(cell, k)) return OR_EINVAL;
     elem_ctx *c = malloc(sizeof(elem_ctx));
@@ -833,12 +837,16 @@ int or_sensitivity(int cell, int k, int64_t nv_total, const double *coords,
         if (elem_matrix(c, xv, Ke)) { rc = OR_EINVAL; break; }
         for (int a = 0; a < nb; a++)
             for (int i = 0; i < d; i++) ue[d * a + i] = u[d * (int64_t)cn[e * nb + a] + i];
-        double se = 0.0;
+        double se = 0.0, sa = 0.0;
         for (int r = 0; r < ldof; r++) {
             double kr = 0.0;
-            for (int col = 0; col < ldof; col++) kr += Ke[r * ldof + col] * ue[col];
+            for (int col = 0; col < ldof; col++) {
+                kr += Ke[r * ldof + col] * ue[col];
+                sa += fabs(ue[r] * Ke[r * ldof + col] * ue[col]);
+            }
             se += ue[r] * kr;
         }
+        if (sabs_out) sabs_out[q] = sa;
         dc[q] = -simp_dE(rho[e], E0, Emin, p) * se;
         if (s_out) s_out[q] = se;
         ctot += simp_E(rho[e], E0, Emin, p) * se;
@@ -863,7 +871,7 @@ int or_compliance_vjp(int cell, int k, int64_t nv_total, const double *coords,
     double *dc = malloc(sizeof(double) * (size_t)(nc + 1));
     if (!s || !dc) { free(s); free(dc); return OR_ENOMEM; }
     int rc = or_sensitivity(cell, k, nv_total, coords, nc, cv, E0, Emin, nu, p, plane_strain,
-                            rho, u, -1, NULL, dc, s, NULL);
+                            rho, u, -1, NULL, dc, s, NULL, NULL);
     if (rc) { free(s); free(dc); return rc; }
     for (int64_t e = 0; e < nc; e++) grad_rho[e] = g * simp_dE(rho[e], E0, Emin, p) * s[e];
     free(s); free(dc);
@@ -872,7 +880,7 @@ int or_compliance_vjp(int cell, int k, int64_t nv_total, const double *coords,
     int32_t *ci = NULL;
     double *v = NULL;
     rc = or_assemble_rows(cell, k, nv_total, coords, nc, cv, E0, Emin, nu, p, plane_strain,
-                          rho, -1, NULL, &nnz, &rp, &ci, &v, &ndof);
+                          rho, -1, NULL, 0, &nnz, &rp, &ci, &v, &ndof);
     if (rc) return rc;
     for (int64_t r = 0; r < ndof; r++) {
         double acc = 0.0;

@@ -1,0 +1,159 @@
+"""Python binding of the SIMP assembly library: torch tensors in, torch tensors out.
+
+Each method marshals its arguments (device pointers of contiguous CUDA float64
+tensors, the current CUDA stream) and calls the C ABI; every step of the path
+runs in the library's kernels.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t, dtype, n, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must have dtype %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous() or t.numel() != n:
+        raise ValueError("%s must be contiguous with %d elements (got %s)" % (name, n, tuple(t.shape)))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Mesh:
+    """A device-resident mesh: pattern, maps and element data (Sec. 3.2.2).
+
+    cell: "tri" | "tet" | "quad" | "hex"; order 1..3; coords float64 [NV, d];
+    cells int [NC, nv] in reference vertex order; elem_prec "fp64" | "fp32".
+    """
+
+    def __init__(self, cell, order, coords, cells, E0=1.0, Emin=1e-9, nu=0.3, p=3.0,
+                 plane_strain=False, elem_prec="fp64", stream=None):
+        L = N.lib()
+        coords = np.ascontiguousarray(coords, np.float64)
+        cells = np.ascontiguousarray(cells, np.int32)
+        self.cell, self.order = cell, int(order)
+        self.dim = coords.shape[1]
+        self.material = N.Material(E0, Emin, nu, p, int(bool(plane_strain)))
+        self.elem_prec = elem_prec
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        h = ctypes.c_void_p()
+        N.check(L.soptx_mesh_create(self.dim, N.CELL[cell], self.order, coords.shape[0],
+                                    coords.ctypes.data_as(ctypes.c_void_p), cells.shape[0],
+                                    cells.ctypes.data_as(ctypes.c_void_p) if cells.size else None,
+                                    ctypes.byref(self.material), N.PREC[elem_prec], _stream(stream),
+                                    ctypes.byref(h)))
+        self._h = h
+        ndof, nnz, nc, ldof = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        N.check(L.soptx_mesh_info(h, ctypes.byref(ndof), ctypes.byref(nnz), ctypes.byref(nc), ctypes.byref(ldof)))
+        self.ndof, self.nnz, self.n_cells, self.ldof = ndof.value, nnz.value, nc.value, ldof.value
+        self.nb = self.ldof // self.dim
+        path, nbytes = ctypes.c_int32(), ctypes.c_int64()
+        N.check(L.soptx_mesh_path(h, ctypes.byref(path)))
+        N.check(L.soptx_mesh_device_bytes(h, ctypes.byref(nbytes)))
+        self.path = N.PATH[path.value]
+        self.device_bytes = nbytes.value
+
+    @classmethod
+    def from_workload(cls, wl, elem_prec="fp64", stream=None):
+        return cls(wl.cell, wl.order, wl.coords, wl.cells, wl.E0, wl.Emin, wl.nu, wl.p, wl.plane_strain,
+                   elem_prec, stream)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            N.lib().soptx_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ structure
+    def pattern(self, stream=None):
+        indptr = torch.empty(self.ndof + 1, dtype=torch.int64, device=self.device)
+        indices = torch.empty(self.nnz, dtype=torch.int32, device=self.device)
+        N.check(N.lib().soptx_mesh_copy_pattern(self._h, ctypes.c_void_p(indptr.data_ptr()),
+                                                ctypes.c_void_p(indices.data_ptr()), _stream(stream)))
+        return indptr, indices
+
+    def cell_nodes(self, stream=None):
+        out = torch.empty((self.n_cells, self.nb), dtype=torch.int32, device=self.device)
+        if self.n_cells:
+            N.check(N.lib().soptx_mesh_copy_cell_nodes(self._h, ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
+
+    # ------------------------------------------------------------ hot path
+    def assemble_K(self, rho, vals=None, stream=None):
+        if vals is None:
+            vals = torch.empty(self.nnz, dtype=torch.float64, device=self.device)
+        N.check(N.lib().soptx_assemble_K(self._h, _dptr(rho, torch.float64, self.n_cells, "rho"),
+                                         _dptr(vals, torch.float64, self.nnz, "vals"), _stream(stream)))
+        return vals
+
+    def sensitivity(self, rho, u, dc=None, c=None, want_c=True, stream=None):
+        if dc is None:
+            dc = torch.empty(self.n_cells, dtype=torch.float64, device=self.device)
+        if want_c and c is None:
+            c = torch.empty(1, dtype=torch.float64, device=self.device)
+        N.check(N.lib().soptx_sensitivity(self._h, _dptr(rho, torch.float64, self.n_cells, "rho"),
+                                          _dptr(u, torch.float64, self.ndof, "u"),
+                                          _dptr(dc, torch.float64, self.n_cells, "dc"),
+                                          _dptr(c, torch.float64, 1, "c") if want_c else None, _stream(stream)))
+        return dc, (c if want_c else None)
+
+    def step(self, rho, u, vals=None, dc=None, c=None, stream=None):
+        """K(rho), dc and c in one call (the per-iteration hot path)."""
+        if vals is None:
+            vals = torch.empty(self.nnz, dtype=torch.float64, device=self.device)
+        if dc is None:
+            dc = torch.empty(self.n_cells, dtype=torch.float64, device=self.device)
+        if c is None:
+            c = torch.empty(1, dtype=torch.float64, device=self.device)
+        N.check(N.lib().soptx_assemble_and_sensitivity(
+            self._h, _dptr(rho, torch.float64, self.n_cells, "rho"), _dptr(u, torch.float64, self.ndof, "u"),
+            _dptr(vals, torch.float64, self.nnz, "vals"), _dptr(dc, torch.float64, self.n_cells, "dc"),
+            _dptr(c, torch.float64, 1, "c"), _stream(stream)))
+        return vals, dc, c
+
+    def compliance_vjp(self, rho, u, gout, want_u=True, stream=None):
+        grad_rho = torch.empty(self.n_cells, dtype=torch.float64, device=self.device)
+        grad_u = torch.empty(self.ndof, dtype=torch.float64, device=self.device) if want_u else None
+        N.check(N.lib().soptx_compliance_vjp(
+            self._h, _dptr(rho, torch.float64, self.n_cells, "rho"), _dptr(u, torch.float64, self.ndof, "u"),
+            _dptr(gout, torch.float64, 1, "gout"), _dptr(grad_rho, torch.float64, self.n_cells, "grad_rho"),
+            _dptr(grad_u, torch.float64, self.ndof, "grad_u") if want_u else None, _stream(stream)))
+        return grad_rho, grad_u
+
+
+def version():
+    return N.lib().soptx_version().decode()
+
+
+def host_plan(cell, order, coords, cells):
+    """Host-only numbering and pattern (no GPU needed):
+    returns dict(ndof, nnz, nb, path, indptr, indices, cell_nodes) as numpy arrays."""
+    L = N.lib()
+    coords = np.ascontiguousarray(coords, np.float64)
+    cells = np.ascontiguousarray(cells, np.int32)
+    dim = coords.shape[1]
+    ndof, nnz, nb, path = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+    args = [dim, N.CELL[cell], int(order), coords.shape[0], coords.ctypes.data_as(ctypes.c_void_p), cells.shape[0],
+            cells.ctypes.data_as(ctypes.c_void_p) if cells.size else None]
+    N.check(L.soptx_host_plan(*args, ctypes.byref(ndof), ctypes.byref(nnz), ctypes.byref(nb), ctypes.byref(path),
+                              None, None, None))
+    indptr = np.zeros(ndof.value + 1, np.int64)
+    indices = np.zeros(max(nnz.value, 1), np.int32)
+    cn = np.zeros((cells.shape[0], nb.value), np.int32)
+    N.check(L.soptx_host_plan(*args, None, None, None, None, indptr.ctypes.data_as(ctypes.c_void_p),
+                              indices.ctypes.data_as(ctypes.c_void_p), cn.ctypes.data_as(ctypes.c_void_p)))
+    return dict(ndof=ndof.value, nnz=nnz.value, nb=nb.value, path=N.PATH[path.value], indptr=indptr,
+                indices=indices[: nnz.value], cell_nodes=cn)

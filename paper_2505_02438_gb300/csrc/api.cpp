@@ -1,0 +1,342 @@
+// The C ABI (include/soptx.h): argument validation, device residency of a mesh
+// and dispatch to the kernels.
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+
+namespace soptx {
+
+static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_fail_after{0};
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+cudaError_t dev_alloc(void **p, size_t bytes)
+{
+    *p = nullptr;
+    int64_t n = g_fail_after.load();
+    if (n > 0) {
+        if (n == 1) {
+            g_fail_after.store(0);
+            return cudaErrorMemoryAllocation;
+        }
+        g_fail_after.store(n - 1);
+    }
+    if (bytes == 0) bytes = 16;
+    return cudaMalloc(p, bytes);
+}
+
+static void free_device(DeviceMesh &d)
+{
+    void *ptrs[] = {d.indptr, d.indices, d.cell_node, d.node_off, d.inc_ptr, d.inc,
+                    d.pos, d.geo, d.M, d.K, d.scratch};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    d = DeviceMesh{};
+}
+
+static soptx_status cuda_status(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return SOPTX_OK;
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? SOPTX_ENOMEM : SOPTX_ECUDA;
+}
+
+template <typename T>
+static soptx_status upload(T **dst, const std::vector<T> &src, cudaStream_t st, int64_t &bytes, const char *what)
+{
+    size_t n = src.size() * sizeof(T);
+    cudaError_t e = dev_alloc((void **)dst, n);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_status(e, what);
+    }
+    bytes += (int64_t)(n ? n : 16);
+    if (n) {
+        e = cudaMemcpyAsync(*dst, src.data(), n, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_status(e, what);
+    }
+    return SOPTX_OK;
+}
+
+static bool material_ok(const soptx_material *m, int dim, Material &out, std::string &err)
+{
+    if (!m) { err = "material is NULL"; return false; }
+    if (!std::isfinite(m->E0) || !std::isfinite(m->Emin) || !std::isfinite(m->nu) || !std::isfinite(m->p)) {
+        err = "material parameters must be finite";
+        return false;
+    }
+    if (!(m->Emin >= 0.0) || !(m->E0 > m->Emin)) { err = "need E0 > Emin >= 0"; return false; }
+    if (!(m->nu > -1.0 && m->nu < 0.5)) { err = "need -1 < nu < 0.5"; return false; }
+    if (!(m->p >= 1.0)) { err = "need p >= 1"; return false; }
+    out.E0 = m->E0;
+    out.Emin = m->Emin;
+    out.nu = m->nu;
+    out.p = m->p;
+    out.dE = m->E0 - m->Emin;
+    out.p_int = (m->p == std::floor(m->p) && m->p <= 16.0) ? (int)m->p : 0;
+    const double nu = m->nu;
+    out.mu = 1.0 / (2.0 * (1.0 + nu));
+    if (dim == 2 && !m->plane_strain) out.lam = nu / (1.0 - nu * nu);      // plane stress lambda*
+    else out.lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    return true;
+}
+
+}  // namespace soptx
+
+using namespace soptx;
+
+extern "C" {
+
+const char *soptx_last_error(void) { return g_last_error.c_str(); }
+const char *soptx_version(void) { return "soptx-gb300 0.1 (sm_103a)"; }
+void soptx_debug_fail_alloc_after(int64_t n) { g_fail_after.store(n > 0 ? n : 0); }
+
+soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_vertices, const double *coords,
+                               int64_t n_cells, const int32_t *cell_vertices, const soptx_material *mat,
+                               soptx_elem_prec prec, void *stream, soptx_mesh *out)
+{
+    g_last_error.clear();
+    if (!out) SOPTX_FAIL(SOPTX_EINVAL, "out is NULL");
+    *out = nullptr;
+    if ((int)cell < SOPTX_TRI || (int)cell > SOPTX_HEX) SOPTX_FAIL(SOPTX_EINVAL, "unknown cell type");
+    if (cell_dim(cell) != dim) SOPTX_FAIL(SOPTX_EINVAL, "dim does not match the cell type");
+    if (order < 1 || order > 3) SOPTX_FAIL(SOPTX_EINVAL, "order must be 1, 2 or 3");
+    if (prec != SOPTX_ELEM_FP64 && prec != SOPTX_ELEM_FP32) SOPTX_FAIL(SOPTX_EINVAL, "unknown element precision");
+    if (n_vertices < 1 || n_cells < 0) SOPTX_FAIL(SOPTX_EINVAL, "need n_vertices >= 1 and n_cells >= 0");
+    if (n_vertices >= ((int64_t)1 << 31) || n_cells >= ((int64_t)1 << 31))
+        SOPTX_FAIL(SOPTX_EINVAL, "vertex and cell counts must stay below 2^31");
+    if (!coords || (n_cells > 0 && !cell_vertices)) SOPTX_FAIL(SOPTX_EINVAL, "coords / cell_vertices is NULL");
+    Material mt;
+    std::string err;
+    if (!material_ok(mat, dim, mt, err)) SOPTX_FAIL(SOPTX_EINVAL, err);
+
+    soptx_mesh_s *m = new (std::nothrow) soptx_mesh_s();
+    if (!m) SOPTX_FAIL(SOPTX_ENOMEM, "host allocation failed");
+    m->mat = mt;
+    m->user_mat = *mat;
+    m->prec = prec;
+    RefElement ref;
+    try {
+        if (!build_ref_element(cell, order, ref, err) ||
+            !setup_host_mesh(dim, cell, order, n_vertices, coords, n_cells, cell_vertices, ref, m->h, err)) {
+            delete m;
+            SOPTX_FAIL(SOPTX_EINVAL, err);
+        }
+    } catch (const std::bad_alloc &) {
+        delete m;
+        SOPTX_FAIL(SOPTX_ENOMEM, "host allocation failed during mesh setup");
+    }
+    HostMesh &h = m->h;
+    m->path = h.lattice ? SOPTX_PATH_LATTICE : (h.uniform ? SOPTX_PATH_UNIFORM : SOPTX_PATH_CACHED);
+
+    cudaStream_t st = (cudaStream_t)stream;
+    soptx_status s = SOPTX_OK;
+    int64_t &B = m->device_bytes;
+    std::vector<int64_t> indptr;
+    std::vector<int32_t> indices;
+    try {
+        build_csr(h, indptr, indices);
+    } catch (const std::bad_alloc &) {
+        delete m;
+        SOPTX_FAIL(SOPTX_ENOMEM, "host allocation failed building the CSR pattern");
+    }
+    DeviceMesh &d = m->d;
+#define UP(dst, src, what)                                  \
+    if (s == SOPTX_OK) s = upload(&(dst), (src), st, B, what);
+    UP(d.indptr, indptr, "indptr");
+    UP(d.indices, indices, "indices");
+    UP(d.cell_node, h.cell_node, "cell_node");
+    UP(d.node_off, h.node_off, "node_off");
+    UP(d.inc_ptr, h.inc_ptr, "inc_ptr");
+    UP(d.inc, h.inc, "inc");
+    UP(d.pos, h.pos, "pos");
+    UP(d.M, ref.M, "reference integrals");
+#undef UP
+    // geometry: all cells when cached, one otherwise
+    if (s == SOPTX_OK) {
+        std::vector<double> geo = h.geo;
+        if (m->path != SOPTX_PATH_CACHED && h.nc > 0) geo.resize((size_t)(h.dim * h.dim + 1));
+        s = upload(&d.geo, geo, st, B, "geometry");
+    }
+    const int64_t n_elem_mats = (m->path == SOPTX_PATH_CACHED) ? h.nc : (h.nc > 0 ? 1 : 0);
+    if (s == SOPTX_OK) {
+        size_t esz = (prec == SOPTX_ELEM_FP32) ? 4 : 8;
+        size_t bytes = (size_t)std::max<int64_t>(n_elem_mats, 1) * h.ldof * h.ldof * esz;
+        cudaError_t e = dev_alloc(&d.K, bytes);
+        if (e != cudaSuccess) { cudaGetLastError(); s = cuda_status(e, "element matrices"); }
+        else B += (int64_t)bytes;
+    }
+    if (s == SOPTX_OK) {
+        d.scratch_len = std::max<int64_t>(sensitivity_scratch_len(*m), 1);
+        cudaError_t e = dev_alloc((void **)&d.scratch, d.scratch_len * sizeof(double));
+        if (e != cudaSuccess) { cudaGetLastError(); s = cuda_status(e, "scratch"); }
+        else B += d.scratch_len * (int64_t)sizeof(double);
+    }
+    if (s == SOPTX_OK) s = cuda_status(launch_element_matrices(*m, n_elem_mats, st), "element matrices kernel");
+    if (s == SOPTX_OK) s = cuda_status(cudaStreamSynchronize(st), "mesh setup");
+    if (s != SOPTX_OK) {
+        std::string msg = g_last_error;
+        cudaStreamSynchronize(st);
+        free_device(m->d);
+        delete m;
+        set_error(msg);
+        return s;
+    }
+    // host copies that the kernels do not need any more
+    std::vector<uint16_t>().swap(h.pos);
+    std::vector<int32_t>().swap(h.inc);
+    *out = m;
+    return SOPTX_OK;
+}
+
+soptx_status soptx_host_plan(int dim, soptx_cell cell, int order, int64_t n_vertices, const double *coords,
+                             int64_t n_cells, const int32_t *cell_vertices, int64_t *ndof, int64_t *nnz,
+                             int32_t *nb, soptx_path *path, int64_t *indptr, int32_t *indices,
+                             int32_t *cell_nodes)
+{
+    g_last_error.clear();
+    if ((int)cell < SOPTX_TRI || (int)cell > SOPTX_HEX) SOPTX_FAIL(SOPTX_EINVAL, "unknown cell type");
+    if (cell_dim(cell) != dim) SOPTX_FAIL(SOPTX_EINVAL, "dim does not match the cell type");
+    if (order < 1 || order > 3) SOPTX_FAIL(SOPTX_EINVAL, "order must be 1, 2 or 3");
+    if (n_vertices < 1 || n_cells < 0) SOPTX_FAIL(SOPTX_EINVAL, "need n_vertices >= 1 and n_cells >= 0");
+    if (!coords || (n_cells > 0 && !cell_vertices)) SOPTX_FAIL(SOPTX_EINVAL, "coords / cell_vertices is NULL");
+    RefElement ref;
+    HostMesh h;
+    std::string err;
+    try {
+        if (!build_ref_element(cell, order, ref, err) ||
+            !setup_host_mesh(dim, cell, order, n_vertices, coords, n_cells, cell_vertices, ref, h, err))
+            SOPTX_FAIL(SOPTX_EINVAL, err);
+        if (ndof) *ndof = h.ndof;
+        if (nnz) *nnz = h.nnz;
+        if (nb) *nb = h.nb;
+        if (path) *path = h.lattice ? SOPTX_PATH_LATTICE : (h.uniform ? SOPTX_PATH_UNIFORM : SOPTX_PATH_CACHED);
+        if (indptr || indices) {
+            std::vector<int64_t> ip;
+            std::vector<int32_t> ix;
+            build_csr(h, ip, ix);
+            if (indptr) std::memcpy(indptr, ip.data(), ip.size() * sizeof(int64_t));
+            if (indices && !ix.empty()) std::memcpy(indices, ix.data(), ix.size() * sizeof(int32_t));
+        }
+        if (cell_nodes && !h.cell_node.empty())
+            std::memcpy(cell_nodes, h.cell_node.data(), h.cell_node.size() * sizeof(int32_t));
+    } catch (const std::bad_alloc &) {
+        SOPTX_FAIL(SOPTX_ENOMEM, "host allocation failed");
+    }
+    return SOPTX_OK;
+}
+
+soptx_status soptx_mesh_info(soptx_mesh m, int64_t *ndof, int64_t *nnz, int64_t *n_cells, int32_t *ldof)
+{
+    if (!m) SOPTX_FAIL(SOPTX_EINVAL, "mesh is NULL");
+    if (ndof) *ndof = m->h.ndof;
+    if (nnz) *nnz = m->h.nnz;
+    if (n_cells) *n_cells = m->h.nc;
+    if (ldof) *ldof = m->h.ldof;
+    return SOPTX_OK;
+}
+
+soptx_status soptx_mesh_pattern(soptx_mesh m, const int64_t **d_indptr, const int32_t **d_indices)
+{
+    if (!m) SOPTX_FAIL(SOPTX_EINVAL, "mesh is NULL");
+    if (d_indptr) *d_indptr = m->d.indptr;
+    if (d_indices) *d_indices = m->d.indices;
+    return SOPTX_OK;
+}
+
+soptx_status soptx_mesh_cell_nodes(soptx_mesh m, const int32_t **d_cell_nodes, int32_t *nb)
+{
+    if (!m) SOPTX_FAIL(SOPTX_EINVAL, "mesh is NULL");
+    if (d_cell_nodes) *d_cell_nodes = m->d.cell_node;
+    if (nb) *nb = m->h.nb;
+    return SOPTX_OK;
+}
+
+soptx_status soptx_mesh_copy_pattern(soptx_mesh m, int64_t *d_indptr, int32_t *d_indices, void *stream)
+{
+    if (!m) SOPTX_FAIL(SOPTX_EINVAL, "mesh is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (d_indptr) {
+        soptx_status s = cuda_status(cudaMemcpyAsync(d_indptr, m->d.indptr, (m->h.ndof + 1) * sizeof(int64_t),
+                                                     cudaMemcpyDeviceToDevice, st), "copy indptr");
+        if (s != SOPTX_OK) return s;
+    }
+    if (d_indices && m->h.nnz > 0)
+        return cuda_status(cudaMemcpyAsync(d_indices, m->d.indices, m->h.nnz * sizeof(int32_t),
+                                           cudaMemcpyDeviceToDevice, st), "copy indices");
+    return SOPTX_OK;
+}
+
+soptx_status soptx_mesh_copy_cell_nodes(soptx_mesh m, int32_t *d_cell_nodes, void *stream)
+{
+    if (!m || !d_cell_nodes) SOPTX_FAIL(SOPTX_EINVAL, "mesh or d_cell_nodes is NULL");
+    if (m->h.nc == 0) return SOPTX_OK;
+    return cuda_status(cudaMemcpyAsync(d_cell_nodes, m->d.cell_node, m->h.nc * m->h.nb * sizeof(int32_t),
+                                       cudaMemcpyDeviceToDevice, (cudaStream_t)stream), "copy cell nodes");
+}
+
+soptx_status soptx_mesh_path(soptx_mesh m, soptx_path *path)
+{
+    if (!m || !path) SOPTX_FAIL(SOPTX_EINVAL, "mesh or path is NULL");
+    *path = m->path;
+    return SOPTX_OK;
+}
+
+soptx_status soptx_mesh_device_bytes(soptx_mesh m, int64_t *bytes)
+{
+    if (!m || !bytes) SOPTX_FAIL(SOPTX_EINVAL, "mesh or bytes is NULL");
+    *bytes = m->device_bytes;
+    return SOPTX_OK;
+}
+
+soptx_status soptx_assemble_K(soptx_mesh m, const double *d_rho, double *d_vals, void *stream)
+{
+    if (!m) SOPTX_FAIL(SOPTX_EINVAL, "mesh is NULL");
+    if ((!d_rho && m->h.nc > 0) || (!d_vals && m->h.nnz > 0)) SOPTX_FAIL(SOPTX_EINVAL, "d_rho / d_vals is NULL");
+    return cuda_status(launch_assemble(*m, d_rho, d_vals, (cudaStream_t)stream), "soptx_assemble_K");
+}
+
+soptx_status soptx_sensitivity(soptx_mesh m, const double *d_rho, const double *d_u, double *d_dc, double *d_c,
+                               void *stream)
+{
+    if (!m) SOPTX_FAIL(SOPTX_EINVAL, "mesh is NULL");
+    if (m->h.nc > 0 && (!d_rho || !d_u || !d_dc)) SOPTX_FAIL(SOPTX_EINVAL, "d_rho / d_u / d_dc is NULL");
+    return cuda_status(launch_sensitivity(*m, d_rho, d_u, d_dc, d_c, -1.0, nullptr, (cudaStream_t)stream),
+                       "soptx_sensitivity");
+}
+
+soptx_status soptx_assemble_and_sensitivity(soptx_mesh m, const double *d_rho, const double *d_u, double *d_vals,
+                                            double *d_dc, double *d_c, void *stream)
+{
+    soptx_status s = soptx_assemble_K(m, d_rho, d_vals, stream);
+    if (s != SOPTX_OK) return s;
+    return soptx_sensitivity(m, d_rho, d_u, d_dc, d_c, stream);
+}
+
+soptx_status soptx_compliance_vjp(soptx_mesh m, const double *d_rho, const double *d_u, const double *d_gout,
+                                  double *d_grad_rho, double *d_grad_u, void *stream)
+{
+    if (!m) SOPTX_FAIL(SOPTX_EINVAL, "mesh is NULL");
+    if (!d_gout) SOPTX_FAIL(SOPTX_EINVAL, "d_gout is NULL");
+    if (m->h.nc > 0 && (!d_rho || !d_u || !d_grad_rho)) SOPTX_FAIL(SOPTX_EINVAL, "d_rho / d_u / d_grad_rho is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    soptx_status s = cuda_status(launch_sensitivity(*m, d_rho, d_u, d_grad_rho, nullptr, 1.0, d_gout, st),
+                                 "soptx_compliance_vjp");
+    if (s != SOPTX_OK || !d_grad_u) return s;
+    return cuda_status(launch_Ku(*m, d_rho, d_u, d_gout, d_grad_u, st), "soptx_compliance_vjp");
+}
+
+soptx_status soptx_mesh_destroy(soptx_mesh m)
+{
+    if (!m) return SOPTX_OK;
+    cudaDeviceSynchronize();
+    free_device(m->d);
+    delete m;
+    return SOPTX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,113 @@
+// Internal declarations shared by the host setup, the kernels and the ABI.
+#pragma once
+
+#include <array>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/soptx.h"
+
+namespace soptx {
+
+constexpr int kMaxNb = 64;       // hex Q3
+constexpr int kMaxLdof = 192;
+
+inline int cell_dim(int cell) { return (cell == SOPTX_TRI || cell == SOPTX_QUAD) ? 2 : 3; }
+inline bool is_simplex(int cell) { return cell == SOPTX_TRI || cell == SOPTX_TET; }
+inline int cell_nverts(int cell) { return cell == SOPTX_TRI ? 3 : (cell == SOPTX_HEX ? 8 : 4); }
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+struct Status {
+    soptx_status code = SOPTX_OK;
+};
+#define SOPTX_FAIL(code, msg)            \
+    do {                                 \
+        ::soptx::set_error(msg);         \
+        return (code);                   \
+    } while (0)
+
+// Device allocation with the failure-injection test hook.
+cudaError_t dev_alloc(void **p, size_t bytes);
+
+// ---------------------------------------------------------------- reference element
+// Local nodes of the library's own reference element and the exact integrals
+// M[k][l][a][b] = int_ref d_k phi_a d_l phi_b (rational arithmetic, rounded once).
+struct RefElement {
+    int cell = 0, order = 1, dim = 2, nb = 0;
+    // Lattice coordinates of each local node (multiples of 1/order).  Simplices
+    // carry barycentric indices lam[0..dim] (lam[0] = order - sum of the rest).
+    std::vector<std::array<int, 4>> lat;
+    std::vector<double> M;   // [dim][dim][nb][nb]
+};
+bool build_ref_element(int cell, int order, RefElement &ref, std::string &err);
+
+// ---------------------------------------------------------------- host mesh setup
+struct HostMesh {
+    int dim = 0, cell = 0, order = 0, nb = 0, ldof = 0, nvc = 0;
+    int64_t nv = 0, nc = 0, nn = 0, ndof = 0, nnz = 0, ninc = 0;
+    std::vector<int32_t> cell_node;     // [nc][nb]
+    std::vector<int64_t> node_off;      // [nn+1] prefix of node degrees
+    std::vector<int32_t> nbr;           // [node_off[nn]] sorted neighbour nodes
+    std::vector<int32_t> inc_ptr;       // [nn+1]
+    std::vector<int32_t> inc;           // [ninc] e * nb + a, ascending e per node
+    std::vector<uint16_t> pos;          // [ninc][nb] column block of node b in row n
+    std::vector<double> geo;            // [nc][dim*dim + 1]: G = J^-1 (row-major), |det J|
+    bool uniform = false;               // every cell has the same Jacobian
+    bool lattice = false;               // order-1 box lattice in canonical numbering
+    int lat_n[3] = {1, 1, 1};           // cells per axis
+    int max_deg = 0;
+};
+
+bool setup_host_mesh(int dim, int cell, int order, int64_t nv, const double *coords, int64_t nc,
+                     const int32_t *cv, const RefElement &ref, HostMesh &hm, std::string &err);
+void build_csr(const HostMesh &hm, std::vector<int64_t> &indptr, std::vector<int32_t> &indices);
+
+// ---------------------------------------------------------------- device mesh
+struct DeviceMesh {
+    int64_t *indptr = nullptr;     // [ndof+1]
+    int32_t *indices = nullptr;    // [nnz]
+    int32_t *cell_node = nullptr;  // [nc][nb]
+    int64_t *node_off = nullptr;   // [nn+1]
+    int32_t *inc_ptr = nullptr;    // [nn+1]
+    int32_t *inc = nullptr;        // [ninc]
+    uint16_t *pos = nullptr;       // [ninc][nb]
+    double *geo = nullptr;         // [nc][dim*dim+1]
+    double *M = nullptr;           // reference integrals [dim][dim][nb][nb]
+    void *K = nullptr;             // uniform: [ldof][ldof]; cached: [nc][ldof][ldof]
+    double *scratch = nullptr;     // partial sums
+    int64_t scratch_len = 0;
+};
+
+struct Material {
+    double E0, Emin, nu, p;
+    double dE;          // E0 - Emin
+    double lam, mu;     // Lame constants at E = 1 (plane stress: lam*)
+    int p_int;          // p when p is a small positive integer, else 0
+};
+
+}  // namespace soptx
+
+struct soptx_mesh_s {
+    soptx::HostMesh h;
+    soptx::DeviceMesh d;
+    soptx::Material mat;
+    soptx_material user_mat;
+    int prec = SOPTX_ELEM_FP64;
+    soptx_path path = SOPTX_PATH_CACHED;
+    int64_t device_bytes = 0;
+};
+
+namespace soptx {
+// ---------------------------------------------------------------- launchers (kernels.cu)
+cudaError_t launch_element_matrices(const soptx_mesh_s &m, int64_t n_elems, cudaStream_t st);
+cudaError_t launch_assemble(const soptx_mesh_s &m, const double *rho, double *vals, cudaStream_t st);
+cudaError_t launch_sensitivity(const soptx_mesh_s &m, const double *rho, const double *u, double *dc,
+                               double *c, double scale, const double *gscale, cudaStream_t st);
+cudaError_t launch_Ku(const soptx_mesh_s &m, const double *rho, const double *u, const double *gout,
+                      double *out, cudaStream_t st);
+int64_t sensitivity_scratch_len(const soptx_mesh_s &m);
+}  // namespace soptx

@@ -1,0 +1,248 @@
+// Reference element of the library: local node lattice and the exact reference
+// integrals  M[k][l][a][b] = int_ref d_k phi_a  d_l phi_b.
+//
+// This is the "symbolic" half of the paper's symbolic fast assembly (Sec. 3.2.2,
+// Sec. 5.5): the element-independent integrals are computed exactly, once, in
+// rational arithmetic, and only rounded to double at the end.  Per element, the
+// device contracts them with the element's inverse Jacobian (kernels.cu).
+//
+//  * Simplices (P_k): the basis function of the node with barycentric lattice
+//    index alpha (sum = k) is  prod_v prod_{s < alpha_v} (k lam_v - s)/(s + 1),
+//    a polynomial in the barycentric coordinates lam_0..lam_d; d/dxi_m =
+//    d/dlam_m - d/dlam_0; and  int_ref lam^beta = prod(beta_v!) / (|beta| + d)!.
+//  * Tensor cells (Q_k): products of 1D Lagrange polynomials on the equispaced
+//    nodes i/k of [0,1]; the integral factorises into 1D integrals of
+//    l_i l_j, l_i' l_j and l_i' l_j'.
+#include <algorithm>
+#include <cstdlib>
+#include <map>
+#include <numeric>
+
+#include "internal.h"
+
+namespace soptx {
+namespace {
+
+// Exact rational with 128-bit numerator / denominator, always reduced.
+struct Q {
+    __int128 n = 0, d = 1;
+    Q() = default;
+    Q(long long v) : n(v), d(1) {}
+    Q(__int128 a, __int128 b) : n(a), d(b) { norm(); }
+    static __int128 g(__int128 a, __int128 b)
+    {
+        if (a < 0) a = -a;
+        if (b < 0) b = -b;
+        while (b) {
+            __int128 t = a % b;
+            a = b;
+            b = t;
+        }
+        return a ? a : 1;
+    }
+    void norm()
+    {
+        if (d < 0) { n = -n; d = -d; }
+        __int128 q = g(n, d);
+        n /= q;
+        d /= q;
+    }
+    Q operator+(const Q &o) const { return Q(n * o.d + o.n * d, d * o.d); }
+    Q operator-(const Q &o) const { return Q(n * o.d - o.n * d, d * o.d); }
+    Q operator*(const Q &o) const { return Q(n * o.n, d * o.d); }
+    Q operator/(const Q &o) const { return Q(n * o.d, d * o.n); }
+    bool zero() const { return n == 0; }
+    double to_double() const { return (double)((long double)n / (long double)d); }
+};
+
+// Polynomial in up to 4 variables: exponent tuple -> coefficient.
+using Mono = std::array<int, 4>;
+using Poly = std::map<Mono, Q>;
+
+Poly pmul(const Poly &a, const Poly &b)
+{
+    Poly r;
+    for (auto &x : a)
+        for (auto &y : b) {
+            Mono m;
+            for (int i = 0; i < 4; i++) m[i] = x.first[i] + y.first[i];
+            r[m] = r[m] + x.second * y.second;
+        }
+    for (auto it = r.begin(); it != r.end();) it = it->second.zero() ? r.erase(it) : std::next(it);
+    return r;
+}
+
+Poly pdiff(const Poly &a, int var)
+{
+    Poly r;
+    for (auto &x : a) {
+        if (x.first[var] == 0) continue;
+        Mono m = x.first;
+        Q c = x.second * Q((long long)m[var]);
+        m[var] -= 1;
+        r[m] = r[m] + c;
+    }
+    return r;
+}
+
+Poly psub(const Poly &a, const Poly &b)
+{
+    Poly r = a;
+    for (auto &y : b) r[y.first] = r[y.first] - y.second;
+    return r;
+}
+
+long long fact(int n)
+{
+    long long f = 1;
+    for (int i = 2; i <= n; i++) f *= i;
+    return f;
+}
+
+// int over the unit simplex of prod lam_v^beta_v (Dirichlet integral)
+Q simplex_integral(const Poly &p, int dim)
+{
+    Q s(0);
+    for (auto &x : p) {
+        long long num = 1;
+        int tot = 0;
+        for (int v = 0; v <= dim; v++) {
+            num *= fact(x.first[v]);
+            tot += x.first[v];
+        }
+        s = s + x.second * Q((__int128)num, (__int128)fact(tot + dim));
+    }
+    return s;
+}
+
+}  // namespace
+
+bool build_ref_element(int cell, int order, RefElement &ref, std::string &err)
+{
+    if (order < 1 || order > 3) {
+        err = "order must be 1, 2 or 3";
+        return false;
+    }
+    const int k = order, dim = cell_dim(cell);
+    ref.cell = cell;
+    ref.order = order;
+    ref.dim = dim;
+    ref.lat.clear();
+    if (is_simplex(cell)) {
+        // barycentric multi-indices: vertices first (vertex v carries lam_v = k),
+        // then the rest in lexicographic order of (lam_1, ..., lam_d)
+        std::vector<std::array<int, 4>> rest;
+        for (int v = 0; v <= dim; v++) {
+            std::array<int, 4> L{0, 0, 0, 0};
+            if (v == 0) L[3] = k; else L[v - 1] = k;
+            ref.lat.push_back(L);
+        }
+        for (int c = 0; c <= (dim == 3 ? k : 0); c++)
+            for (int b = 0; b <= k; b++)
+                for (int a = 0; a <= k; a++) {
+                    int s = a + b + c;
+                    if (s > k) continue;
+                    std::array<int, 4> L{a, b, c, k - s};
+                    int nz = (a > 0) + (b > 0) + (c > 0) + (k - s > 0);
+                    if (nz == 1) continue;   // a vertex, already listed
+                    rest.push_back(L);
+                }
+        ref.lat.insert(ref.lat.end(), rest.begin(), rest.end());
+    } else {
+        for (int c = 0; c <= (dim == 3 ? k : 0); c++)
+            for (int b = 0; b <= k; b++)
+                for (int a = 0; a <= k; a++) ref.lat.push_back({a, b, c, 0});
+    }
+    const int nb = (int)ref.lat.size();
+    ref.nb = nb;
+    ref.M.assign((size_t)dim * dim * nb * nb, 0.0);
+
+    if (is_simplex(cell)) {
+        // basis polynomials in lam_0..lam_dim (variable index v); lam_0 <-> lat[3]
+        std::vector<Poly> phi(nb);
+        for (int a = 0; a < nb; a++) {
+            int alpha[4] = {ref.lat[a][3], ref.lat[a][0], ref.lat[a][1], ref.lat[a][2]};
+            Poly p;
+            p[Mono{0, 0, 0, 0}] = Q(1);
+            for (int v = 0; v <= dim; v++)
+                for (int s = 0; s < alpha[v]; s++) {
+                    Poly f;   // (k lam_v - s) / (s + 1)
+                    Mono mv{0, 0, 0, 0};
+                    mv[v] = 1;
+                    f[mv] = Q((__int128)k, (__int128)(s + 1));
+                    if (s) f[Mono{0, 0, 0, 0}] = Q((__int128)-s, (__int128)(s + 1));
+                    p = pmul(p, f);
+                }
+            phi[a] = p;
+        }
+        std::vector<std::vector<Poly>> grad(nb, std::vector<Poly>(dim));
+        for (int a = 0; a < nb; a++) {
+            Poly d0 = pdiff(phi[a], 0);
+            for (int m = 0; m < dim; m++) grad[a][m] = psub(pdiff(phi[a], m + 1), d0);
+        }
+        for (int kk = 0; kk < dim; kk++)
+            for (int l = 0; l < dim; l++)
+                for (int a = 0; a < nb; a++)
+                    for (int b = 0; b < nb; b++) {
+                        Q v = simplex_integral(pmul(grad[a][kk], grad[b][l]), dim);
+                        ref.M[(((size_t)kk * dim + l) * nb + a) * nb + b] = v.to_double();
+                    }
+    } else {
+        // 1D Lagrange polynomials on t_i = i/k, as coefficient vectors
+        std::vector<std::vector<Q>> ell(k + 1);
+        for (int i = 0; i <= k; i++) {
+            std::vector<Q> c{Q(1)};
+            Q den(1);
+            for (int j = 0; j <= k; j++) {
+                if (j == i) continue;
+                // multiply by (t - j/k)
+                std::vector<Q> nc(c.size() + 1, Q(0));
+                for (size_t q = 0; q < c.size(); q++) {
+                    nc[q + 1] = nc[q + 1] + c[q];
+                    nc[q] = nc[q] - c[q] * Q((__int128)j, (__int128)k);
+                }
+                c = nc;
+                den = den * Q((__int128)(i - j), (__int128)k);
+            }
+            for (auto &x : c) x = x / den;
+            ell[i] = c;
+        }
+        auto deriv = [](const std::vector<Q> &c) {
+            std::vector<Q> r;
+            for (size_t q = 1; q < c.size(); q++) r.push_back(c[q] * Q((long long)q));
+            if (r.empty()) r.push_back(Q(0));
+            return r;
+        };
+        auto integ = [](const std::vector<Q> &a, const std::vector<Q> &b) {
+            Q s(0);
+            for (size_t p = 0; p < a.size(); p++)
+                for (size_t q = 0; q < b.size(); q++)
+                    s = s + a[p] * b[q] * Q((__int128)1, (__int128)(p + q + 1));
+            return s;
+        };
+        std::vector<std::vector<Q>> I0(k + 1, std::vector<Q>(k + 1)), I1 = I0, I2 = I0;
+        for (int i = 0; i <= k; i++)
+            for (int j = 0; j <= k; j++) {
+                I0[i][j] = integ(ell[i], ell[j]);
+                I1[i][j] = integ(deriv(ell[i]), ell[j]);        // derivative on the first
+                I2[i][j] = integ(deriv(ell[i]), deriv(ell[j]));
+            }
+        for (int kk = 0; kk < dim; kk++)
+            for (int l = 0; l < dim; l++)
+                for (int a = 0; a < nb; a++)
+                    for (int b = 0; b < nb; b++) {
+                        Q v(1);
+                        for (int m = 0; m < dim; m++) {
+                            int ia = ref.lat[a][m], ib = ref.lat[b][m];
+                            if (m == kk && m == l) v = v * I2[ia][ib];
+                            else if (m == kk) v = v * I1[ia][ib];
+                            else if (m == l) v = v * I1[ib][ia];
+                            else v = v * I0[ia][ib];
+                        }
+                        ref.M[(((size_t)kk * dim + l) * nb + a) * nb + b] = v.to_double();
+                    }
+    }
+    return true;
+}
+
+}  // namespace soptx

@@ -1,0 +1,53 @@
+"""Shared test helpers: small meshes and oracle comparisons."""
+import numpy as np
+
+import oracle
+from paper_2505_02438_gb300 import workloads as W
+
+# FP64 form: |K_gpu - K_ref| <= TOL64 * sum_e |E_e K_e^0[a,b]| per CSR entry,
+# |dc_gpu - dc_ref| <= TOL64 * |E'_e| sum_ab |u_a K_ab u_b| per cell.
+TOL64 = 1e-12
+# FP32 element matrices (FP64 accumulation): the element entries carry a
+# relative error of a few FP32 ulps (2^-24 ~ 6e-8) from the contraction.
+TOL32 = 2e-6
+
+
+def relabel(coords, cells, seed):
+    perm = np.random.default_rng(seed).permutation(len(coords))
+    out = np.empty_like(coords)
+    out[perm] = coords
+    return out, perm[cells].astype(np.int32)
+
+
+def small_cases():
+    """(name, cell, order, coords, cells) covering every cell type and order,
+    several tiles and ragged tails."""
+    g = lambda s: np.random.default_rng(s)
+    cases = []
+    c, cl = W.structured_quad(60, 20)
+    cases.append(("q4_60x20_lattice", "quad", 1, c, cl))
+    c, cl = W.structured_hex(13, 5, 4)
+    cases.append(("hex_q1_13x5x4_lattice", "hex", 1, c, cl))
+    c, cl = relabel(*W.structured_hex(6, 3, 2), 3)
+    cases.append(("hex_q1_relabelled_uniform", "hex", 1, c, cl))
+    c, cl = W.structured_quad(7, 5)
+    cases.append(("quad_q2_7x5", "quad", 2, c, cl))
+    c, cl = W.structured_quad(5, 3)
+    cases.append(("quad_q3_5x3", "quad", 3, c, cl))
+    c, cl = W.structured_hex(4, 3, 2)
+    cases.append(("hex_q2_4x3x2", "hex", 2, c, cl))
+    c, cl = W.structured_hex(2, 2, 1)
+    cases.append(("hex_q3_2x2x1", "hex", 3, c, cl))
+    for k in (1, 2, 3):
+        c, cl = W.triangle_grid(17, 9, 0.2, g(k))
+        cases.append(("tri_p%d_17x9_jitter" % k, "tri", k, c, cl))
+    for k in (1, 2, 3):
+        c, cl = W.kuhn_tets(5, 3, 2, 0.15, g(10 + k))
+        cases.append(("tet_p%d_5x3x2_jitter" % k, "tet", k, c, cl))
+    return cases
+
+
+def oracle_csr(cell, k, coords, cells, mat, rho, rows=None):
+    rp, ci, v, ndof = oracle.assemble(cell, k, coords, cells, mat, rho, rows=rows)
+    _, _, va, _ = oracle.assemble(cell, k, coords, cells, mat, rho, rows=rows, absval=True)
+    return rp, ci, v, va, ndof

@@ -1,0 +1,119 @@
+"""The C ABI without a GPU: the in-tree library loads, exports every symbol the
+public headers declare, and its host-side numbering / CSR pattern equals the
+oracle's, bit for bit."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from helpers import relabel, small_cases
+from paper_2505_02438_gb300 import build, workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def native():
+    build.build_library()
+    from paper_2505_02438_gb300 import _native
+    return _native
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"\b(soptx_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol(native):
+    L = ctypes.CDLL(native.LIB_PATH)
+    names = declared_symbols()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    # the binding declares a signature for each of them
+    assert set(names) <= set(native.SIGNATURES), set(names) - set(native.SIGNATURES)
+
+
+def test_version_and_error_string(native):
+    assert b"sm_103a" in native.lib().soptx_version()
+    assert isinstance(native.lib().soptx_last_error(), bytes)
+
+
+@pytest.mark.parametrize("name,cell,k,coords,cells", small_cases(), ids=[c[0] for c in small_cases()])
+def test_host_pattern_equals_oracle(native, name, cell, k, coords, cells):
+    from paper_2505_02438_gb300.api import host_plan
+    pl = host_plan(cell, k, coords, cells)
+    rp, ci, v, ndof = oracle.assemble(cell, k, coords, cells, (1, 1e-9, .3, 3, 0), np.ones(len(cells)))
+    assert pl["ndof"] == ndof
+    assert np.array_equal(pl["indptr"], rp)
+    assert np.array_equal(pl["indices"], ci)
+    cn, nn = oracle.number(cell, k, len(coords), cells)
+    for a, b in zip(pl["cell_nodes"], cn):
+        assert sorted(a) == sorted(b)
+
+
+@pytest.mark.parametrize("cell,k", [("tri", 3), ("tet", 2), ("tet", 3), ("quad", 2), ("hex", 2), ("hex", 3)])
+def test_host_pattern_relabelled_vertices(native, cell, k):
+    from paper_2505_02438_gb300.api import host_plan
+    g = np.random.default_rng(5)
+    mk = {"tri": lambda: W.triangle_grid(5, 4, 0.2, g), "tet": lambda: W.kuhn_tets(3, 2, 2, 0.1, g),
+          "quad": lambda: W.structured_quad(4, 3), "hex": lambda: W.structured_hex(2, 2, 2)}[cell]
+    coords, cells = relabel(*mk(), 11)
+    pl = host_plan(cell, k, coords, cells)
+    rp, ci, v, ndof = oracle.assemble(cell, k, coords, cells, (1, 1e-9, .3, 3, 0), np.ones(len(cells)))
+    assert np.array_equal(pl["indptr"], rp) and np.array_equal(pl["indices"], ci)
+
+
+def test_paths_selected():
+    from paper_2505_02438_gb300.api import host_plan
+    assert host_plan("hex", 1, *W.structured_hex(4, 3, 2))["path"] == "lattice"
+    assert host_plan("quad", 1, *W.structured_quad(4, 3))["path"] == "lattice"
+    assert host_plan("hex", 1, *relabel(*W.structured_hex(4, 3, 2), 1))["path"] == "uniform"
+    assert host_plan("hex", 2, *W.structured_hex(4, 3, 2))["path"] == "uniform"
+    assert host_plan("tri", 1, *W.triangle_grid(4, 3, 0.2, np.random.default_rng(0)))["path"] == "cached"
+
+
+def test_empty_mesh_plan():
+    from paper_2505_02438_gb300.api import host_plan
+    pl = host_plan("tri", 2, np.zeros((3, 2)), np.zeros((0, 3), np.int32))
+    assert pl["ndof"] == 6 and pl["nnz"] == 0 and np.all(pl["indptr"] == 0)
+
+
+@pytest.mark.parametrize("bad,msg", [
+    (lambda c, cl: (c, np.where(cl == 0, 10 ** 6, cl)), "out of range"),
+    (lambda c, cl: (c, np.concatenate([cl[:, :1], cl[:, :1], cl[:, 2:]], 1)), "repeats a vertex"),
+    (lambda c, cl: (np.where(np.arange(len(c))[:, None] == 5, c * 1.1 + 0.3, c), cl), "not a parallelogram"),
+])
+def test_invalid_meshes_rejected(bad, msg):
+    from paper_2505_02438_gb300 import _native as N
+    from paper_2505_02438_gb300.api import host_plan
+    coords, cells = bad(*W.structured_quad(4, 3))
+    with pytest.raises(N.SoptxError) as ei:
+        host_plan("quad", 1, coords, cells)
+    assert ei.value.code == 1 and msg in str(ei.value)
+
+
+def test_degenerate_simplex_rejected():
+    from paper_2505_02438_gb300 import _native as N
+    from paper_2505_02438_gb300.api import host_plan
+    coords = np.array([[0, 0], [1, 0], [2, 0.0]])
+    with pytest.raises(N.SoptxError, match="degenerate"):
+        host_plan("tri", 1, coords, np.array([[0, 1, 2]], np.int32))
+
+
+def test_wrong_dimension_and_order_rejected():
+    from paper_2505_02438_gb300 import _native as N
+    from paper_2505_02438_gb300.api import host_plan
+    c, cl = W.structured_quad(2, 2)
+    with pytest.raises(N.SoptxError, match="order"):
+        host_plan("quad", 4, c, cl)
+    with pytest.raises(N.SoptxError, match="dim"):
+        host_plan("hex", 1, c, cl)
