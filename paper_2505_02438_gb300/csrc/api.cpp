@@ -32,7 +32,7 @@ cudaError_t dev_alloc(void **p, size_t bytes)
 static void free_device(DeviceMesh &d)
 {
     void *ptrs[] = {d.indptr, d.indices, d.cell_node, d.node_off, d.inc_ptr, d.inc,
-                    d.pos, d.geo, d.M, d.K, d.scratch};
+                    d.pos, d.geo, d.M, d.K, d.scratch, d.Edf, d.kappa, d.K0, d.sectors};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     d = DeviceMesh{};
@@ -171,13 +171,38 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
         else B += (int64_t)bytes;
     }
     if (s == SOPTX_OK) {
-        d.scratch_len = std::max<int64_t>(sensitivity_scratch_len(*m), 1);
+        d.scratch_len = std::max<int64_t>(std::max<int64_t>(sensitivity_scratch_len(*m), lattice_sens_grid(h.nc)), 1);
         cudaError_t e = dev_alloc((void **)&d.scratch, d.scratch_len * sizeof(double));
         if (e != cudaSuccess) { cudaGetLastError(); s = cuda_status(e, "scratch"); }
         else B += d.scratch_len * (int64_t)sizeof(double);
     }
     if (s == SOPTX_OK) s = cuda_status(launch_element_matrices(*m, n_elem_mats, st), "element matrices kernel");
     if (s == SOPTX_OK) s = cuda_status(cudaStreamSynchronize(st), "mesh setup");
+    if (s == SOPTX_OK && m->path == SOPTX_PATH_LATTICE) {
+        // the lattice kernels read one FP64 K^0, its reference blocks as float
+        // pairs, and per-call element moduli
+        const size_t n2 = (size_t)h.ldof * h.ldof;
+        std::vector<double> K0(n2);
+        if (prec == SOPTX_ELEM_FP32) {
+            std::vector<float> Kf(n2);
+            s = cuda_status(cudaMemcpy(Kf.data(), d.K, n2 * sizeof(float), cudaMemcpyDeviceToHost), "K0");
+            for (size_t q = 0; q < n2; q++) K0[q] = Kf[q];
+        } else {
+            s = cuda_status(cudaMemcpy(K0.data(), d.K, n2 * sizeof(double), cudaMemcpyDeviceToHost), "K0");
+        }
+        std::vector<float2> kappa;
+        build_lattice_kappa(h.dim, K0, kappa);
+        if (s == SOPTX_OK) s = upload(&d.K0, K0, st, B, "K0");
+        if (s == SOPTX_OK) s = upload(&d.kappa, kappa, st, B, "kappa");
+        std::vector<float2> sectors;
+        if (s == SOPTX_OK && build_lattice_sectors(h.dim, K0, sectors)) s = upload(&d.sectors, sectors, st, B, "sectors");
+        if (s == SOPTX_OK) {
+            cudaError_t e = dev_alloc((void **)&d.Edf, (size_t)std::max<int64_t>(h.nc, 1) * sizeof(float2));
+            if (e != cudaSuccess) { cudaGetLastError(); s = cuda_status(e, "element moduli"); }
+            else B += std::max<int64_t>(h.nc, 1) * (int64_t)sizeof(float2);
+        }
+        if (s == SOPTX_OK) s = cuda_status(cudaStreamSynchronize(st), "mesh setup");
+    }
     if (s != SOPTX_OK) {
         std::string msg = g_last_error;
         cudaStreamSynchronize(st);

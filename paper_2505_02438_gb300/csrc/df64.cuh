@@ -1,0 +1,132 @@
+// Float-float ("df64") arithmetic for FP64-accurate results on the FP32 pipes.
+//
+// GB300 runs FP64 at 1/64 of its FP32 rate, so FP64-accurate sums and
+// products are formed from pairs of floats (h, l), value h + l, with the
+// error-free transformations of Knuth (TwoSum), Dekker (FastTwoSum) and the
+// FMA-based TwoProd.  A normalised pair carries about 48 significand bits.
+// Every helper uses the _rn intrinsics so the compiler cannot contract or
+// reorder the compensated operations.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace soptx {
+
+struct df {
+    float h, l;
+};
+
+__device__ __forceinline__ df df_make(float h, float l) { return df{h, l}; }
+
+// a + b = s + e exactly (Knuth TwoSum)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// a + b = s + e exactly when |a| >= |b| or a == 0 (Dekker FastTwoSum)
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// Sum of two pairs; the error is below about 2^-46 (|a| + |b|).
+__device__ __forceinline__ df df_add(df a, df b)
+{
+    float s, e;
+    two_sum(a.h, b.h, s, e);
+    float t = __fadd_rn(__fadd_rn(a.l, b.l), e);
+    df r;
+    fast_two_sum(s, t, r.h, r.l);
+    return r;
+}
+
+__device__ __forceinline__ df df_neg(df a) { return df{-a.h, -a.l}; }
+
+// Unnormalised product (h, l) of two pairs: h = round(a.h b.h) and l gathers
+// the rounding error of that product (exact, by FMA) and the cross terms.
+__device__ __forceinline__ df df_mul_raw(df a, df b)
+{
+    float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return df{p, e};
+}
+
+__device__ __forceinline__ df df_mul(df a, df b)
+{
+    df r = df_mul_raw(a, b);
+    df o;
+    fast_two_sum(r.h, r.l, o.h, o.l);
+    return o;
+}
+
+// Split a double into a normalised pair (FP64 pipe; used outside hot loops).
+__device__ __forceinline__ df df_from_double(double x)
+{
+    float h = __double2float_rn(x);
+    float l = __double2float_rn(x - (double)h);
+    return df{h, l};
+}
+
+// Out-of-line rare paths: keeping them as real calls stops the compiler from
+// if-converting them into FP64-pipe work on every element of a hot loop.
+__device__ __noinline__ df df_from_double_slow(double x) { return df_from_double(x); }
+__device__ __noinline__ double df_to_double_slow(float h, float l) { return (double)h + (double)l; }
+
+// Split a double into a pair with integer operations (no FP64 pipe): h keeps
+// the leading 24 significand bits (truncated), l the remaining 29 bits
+// rounded to 24.  |x - (h + l)| <= 2^-47 |x|.  Magnitudes outside
+// [2^-74, 2^127] and zero take the FP64 pipe.
+__device__ __forceinline__ df df_split(double x)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const uint32_t E = (hi >> 20) & 0x7ffu;
+    if (E < 949u || E > 1150u) return df_from_double_slow(x);
+    const uint32_t sign = hi & 0x80000000u;
+    const uint32_t hb = sign | ((E - 896u) << 23) | ((hi & 0x000fffffu) << 3) | (lo >> 29);
+    const float scale = __uint_as_float(((E - 948u) << 23) | sign);   // +-2^(E - 1075)
+    const float l = __fmul_rn(__uint2float_rn(lo & 0x1fffffffu), scale);
+    return df{__uint_as_float(hb), l};
+}
+
+// FP64 value of p + e, where p = round(a b) and e carries the product's
+// rounding error and cross terms (|e| <= 8 ulp(p)), built from the bit
+// patterns with integer operations: the double of p is exact (widen the
+// exponent, shift the mantissa); e is scaled so that one unit is 2^6 ulps of
+// that double, rounded to an integer (cvt.rni), and added to the 64-bit
+// pattern.  The result is within 2^-46 |p| of p + e.  Below a power of two the
+// lower binade has half the ulp, hence the doubled step.  Magnitudes under
+// 2^-81 (or zero) take the FP64 pipe out of line.
+__device__ __forceinline__ double df_to_double(float p, float e)
+{
+    const uint32_t hb = __float_as_uint(p);
+    const uint32_t sign = hb & 0x80000000u;
+    const uint32_t mag = hb & 0x7fffffffu;
+    if (mag < (46u << 23)) return df_to_double_slow(p, e);
+    const uint32_t hi = sign | ((mag >> 3) + 0x38000000u);
+    const uint32_t lo = mag << 29;
+    // scale = 2^(46 - E) with p's sign, E the unbiased exponent of p
+    const uint32_t sbits = ((300u << 23) - (mag & 0x7f800000u)) | sign;
+    int32_t ci = __float2int_rn(__fmul_rn(e, __uint_as_float(sbits)));
+    if ((mag & 0x007fffffu) == 0u && ci < 0) ci *= 2;       // just below a power of two
+    const uint64_t bits = (((uint64_t)hi << 32) | lo) + (uint64_t)((int64_t)ci * 64);
+    return __longlong_as_double((long long)bits);
+}
+
+// Sum without the final renormalisation (s, e): enough when the result only
+// feeds further pair arithmetic.
+__device__ __forceinline__ df df_add_lazy(df a, df b)
+{
+    float s, e;
+    two_sum(a.h, b.h, s, e);
+    return df{s, __fadd_rn(__fadd_rn(a.l, b.l), e)};
+}
+
+}  // namespace soptx

@@ -80,6 +80,11 @@ struct DeviceMesh {
     void *K = nullptr;             // uniform: [ldof][ldof]; cached: [nc][ldof][ldof]
     double *scratch = nullptr;     // partial sums
     int64_t scratch_len = 0;
+    // order-1 box lattice path
+    float2 *Edf = nullptr;         // [nc] element moduli as float pairs
+    float2 *kappa = nullptr;       // [3^d][d][d] reference blocks as float pairs
+    double *K0 = nullptr;          // [ldof][ldof] unit-modulus matrix in FP64
+    float2 *sectors = nullptr;     // [2^d][d][d] Walsh-sector blocks of K^0 (nullptr: no split)
 };
 
 struct Material {
@@ -110,4 +115,11 @@ cudaError_t launch_sensitivity(const soptx_mesh_s &m, const double *rho, const d
 cudaError_t launch_Ku(const soptx_mesh_s &m, const double *rho, const double *u, const double *gout,
                       double *out, cudaStream_t st);
 int64_t sensitivity_scratch_len(const soptx_mesh_s &m);
+cudaError_t launch_lattice_assemble(const soptx_mesh_s &m, const double *rho, double *vals, cudaStream_t st);
+void build_lattice_kappa(int dim, const std::vector<double> &K0, std::vector<float2> &kappa);
+bool build_lattice_sectors(int dim, const std::vector<double> &K0, std::vector<float2> &B);
+cudaError_t launch_lattice_sensitivity(const soptx_mesh_s &m, const double *rho, const double *u, double *out,
+                                       double *c, const double *gscale, cudaStream_t st);
+int lattice_sens_grid(int64_t nc);
+__global__ void k_reduce_partials(int n, const double *__restrict__ partial, double *__restrict__ c);
 }  // namespace soptx

@@ -255,7 +255,8 @@ static cudaError_t assemble_t(const soptx_mesh_s &m, const double *rho, double *
 
 cudaError_t launch_assemble(const soptx_mesh_s &m, const double *rho, double *vals, cudaStream_t st)
 {
-    if (m.h.nn == 0) return cudaSuccess;
+    if (m.h.nn == 0 || m.h.nnz == 0) return cudaSuccess;
+    if (m.path == SOPTX_PATH_LATTICE) return launch_lattice_assemble(m, rho, vals, st);
     const bool f32 = m.prec == SOPTX_ELEM_FP32;
     if (m.h.dim == 2) return f32 ? assemble_t<2, float>(m, rho, vals, st) : assemble_t<2, double>(m, rho, vals, st);
     return f32 ? assemble_t<3, float>(m, rho, vals, st) : assemble_t<3, double>(m, rho, vals, st);
@@ -285,6 +286,7 @@ cudaError_t launch_sensitivity(const soptx_mesh_s &m, const double *rho, const d
         if (c) return cudaMemsetAsync(c, 0, sizeof(double), st);
         return cudaSuccess;
     }
+    if (m.path == SOPTX_PATH_LATTICE && m.d.sectors) return launch_lattice_sensitivity(m, rho, u, dc, c, gscale, st);
     const bool f32 = m.prec == SOPTX_ELEM_FP32;
     if (m.h.dim == 2)
         return f32 ? sens_t<2, float>(m, rho, u, dc, c, gscale, st) : sens_t<2, double>(m, rho, u, dc, c, gscale, st);

@@ -1,0 +1,565 @@
+// Assembly on an order-1 box lattice (Q1 quads / hexes on a structured grid
+// of identical axis-aligned boxes), FP64-accurate on the FP32 pipes.
+//
+// For node n and a neighbour m = n + delta, the cells shared by n and m are
+// the 2^z cells around n on the side(s) delta selects (z = number of zero
+// components of delta).  A box is symmetric under the reflection across its
+// mid-plane normal to axis k, which swaps the corners along k and flips the
+// k-th displacement component, so every shared cell contributes the SAME
+// unit-modulus block entry up to a sign:
+//     K[(n,i),(m,j)] = kappa_delta[i][j] * sum_{cells c} sigma_c(i,j) E(rho_c),
+// with kappa_delta the block of the cell on the high side of n along the
+// zero axes and sigma_c = -1 exactly when c lies on the low side along an odd
+// number of zero axes that belong to {i, j} (i != j).  The signed sums are
+// separable per axis (low L, high H, H+L, H-L), so all 4^d of them come from
+// the 2^d moduli around n in d stages of one float-float add per lane.
+//
+// Each warp owns one node (3D) or three nodes (2D), one lane per neighbour
+// offset delta, and writes the node's d rows (d * d * deg(n) contiguous CSR
+// values) with coalesced stores.  The element moduli arrive from k_simp_df
+// as float pairs; a node touching a modulus outside [2^-60, 2^60] (flagged by
+// a NaN low word) is done in plain FP64 instead.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+
+#include "df64.cuh"
+#include "internal.h"
+#include "kernels_common.cuh"
+
+namespace soptx {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__global__ void k_simp_df(int64_t nc, const double *__restrict__ rho, SimpParams sp, float2 *__restrict__ Edf)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc; e += (int64_t)gridDim.x * blockDim.x) {
+        const double E = simp_E(sp, rho[e]);
+        const double a = fabs(E);
+        float2 out;
+        if (E == 0.0) {
+            out = make_float2(0.f, 0.f);
+        } else if (!(a >= 0x1p-60 && a <= 0x1p60)) {
+            out = make_float2((float)E, __int_as_float(0x7fc00000));   // flag: do this node in FP64
+        } else {
+            const df v = df_from_double(E);
+            out = make_float2(v.h, v.l);
+        }
+        Edf[e] = out;
+    }
+}
+
+__device__ __forceinline__ df shfl_df(df v, int src)
+{
+    return df{__shfl_sync(kFull, v.h, src), __shfl_sync(kFull, v.l, src)};
+}
+
+// o: 0 -> L, 1 -> H, 2 -> H + L, 3 -> H - L.  `lsel` = (o == 0) and
+// `coef` = 0, 1 or -1 (the factor on L) are per-lane constants.
+__device__ __forceinline__ df combine(bool lsel, float coef, df L, df H)
+{
+    const df lhs = lsel ? L : H;
+    return df_add(lhs, df{__fmul_rn(coef, L.h), __fmul_rn(coef, L.l)});
+}
+__device__ __forceinline__ float opt_coef(int o) { return o == 2 ? 1.f : (o == 3 ? -1.f : 0.f); }
+
+__device__ __forceinline__ int axis_opt(int delta, bool in_class)
+{
+    return delta < 0 ? 0 : (delta > 0 ? 1 : (in_class ? 3 : 2));
+}
+
+// Plain-FP64 version of one node's rows (used for out-of-range moduli).
+template <int D>
+__device__ __noinline__ void lattice_node_fp64(int nx, int ny, int nz, int ix, int iy, int iz, int dl, bool valid,
+                                               int mi, int rowlen, double *base, const double *__restrict__ K0,
+                                               const double *__restrict__ rho, SimpParams sp)
+{
+    if (!valid) return;
+    const int N[3] = {nx, ny, nz}, idx[3] = {ix, iy, iz};
+    const int delta[3] = {dl % 3 - 1, (dl / 3) % 3 - 1, dl / 9 - 1};
+    const int ldof = D * (1 << D);
+    for (int i = 0; i < D; i++)
+        for (int j = 0; j < D; j++) {
+            double acc = 0.0;
+            for (int c = 0; c < (1 << D); c++) {      // ascending cell order
+                int a = 0, b = 0, eidx = 0, stride = 1;
+                bool ok = true;
+                for (int m = 0; m < D; m++) {
+                    const int cm = (c >> m) & 1;
+                    const int am = 1 - cm, bm = am + delta[m];
+                    const int em = idx[m] - 1 + cm;
+                    if (bm < 0 || bm > 1 || em < 0 || em >= N[m]) ok = false;
+                    a |= am << m;
+                    b |= bm << m;
+                    eidx += em * stride;
+                    stride *= N[m];
+                }
+                if (!ok) continue;
+                acc += simp_E(sp, rho[eidx]) * K0[(D * a + i) * ldof + D * b + j];
+            }
+            base[i * rowlen + D * mi + j] = acc;
+        }
+}
+
+// Node chunks per warp: consecutive nodes, so the lattice index is decoded once
+// per chunk and then stepped; the next node's moduli are fetched before the
+// current node is processed.
+constexpr int kChunk = 16;
+// Sign classes (0 = i == j, 1 = {0,1}, 2 = {0,2}, 3 = {1,2}) whose entries are
+// formed by one FP64 multiply each; 2 puts 5 of the 9 entries on the FP64 pipe.
+#ifndef SOPTX_LATTICE_FP64_CLASSES
+#define SOPTX_LATTICE_FP64_CLASSES 2
+#endif
+constexpr int kFp64Classes = SOPTX_LATTICE_FP64_CLASSES < 1 ? 1 : SOPTX_LATTICE_FP64_CLASSES;
+
+struct NodeIter {
+    int idx[3];
+    __device__ void decode(uint32_t n, int nx, int ny)
+    {
+        idx[0] = (int)(n % (uint32_t)(nx + 1));
+        const uint32_t r = n / (uint32_t)(nx + 1);
+        idx[1] = (int)(r % (uint32_t)(ny + 1));
+        idx[2] = (int)(r / (uint32_t)(ny + 1));
+    }
+    __device__ void step(int nx, int ny)
+    {
+        if (++idx[0] > nx) {
+            idx[0] = 0;
+            if (++idx[1] > ny) {
+                idx[1] = 0;
+                ++idx[2];
+            }
+        }
+    }
+};
+
+__device__ __forceinline__ float2 load_corner(const float2 *__restrict__ Edf, const int idx[3], int lane, int nx,
+                                              int ny, int nz)
+{
+    float2 v = make_float2(0.f, 0.f);
+    if (lane < 8) {
+        const int ex = idx[0] - 1 + (lane & 1), ey = idx[1] - 1 + ((lane >> 1) & 1), ez = idx[2] - 1 + (lane >> 2);
+        if (ex >= 0 && ex < nx && ey >= 0 && ey < ny && ez >= 0 && ez < nz)
+            v = __ldg(&Edf[((int64_t)ez * ny + ey) * nx + ex]);
+    }
+    return v;
+}
+
+#ifndef SOPTX_LATTICE_MINBLOCKS
+#define SOPTX_LATTICE_MINBLOCKS 4
+#endif
+template <int WPB>
+__global__ void __launch_bounds__(WPB * 32, SOPTX_LATTICE_MINBLOCKS)
+k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restrict__ node_off,
+                    const float2 *__restrict__ Edf, const float2 *__restrict__ kappa_g,
+                    const double *__restrict__ K0, const double *__restrict__ rho, SimpParams sp,
+                    double *__restrict__ vals)
+{
+    const int lane = threadIdx.x & 31;
+    const int dl = lane < 27 ? lane : 26;
+    const int dx = dl % 3 - 1, dy = (dl / 3) % 3 - 1, dz = dl / 9 - 1;
+    // table entries t = ox + 4 oy + 16 oz of the four sign classes of (i, j)
+    int tq[4];
+    tq[0] = axis_opt(dx, false) + 4 * axis_opt(dy, false) + 16 * axis_opt(dz, false);   // i == j
+    tq[1] = axis_opt(dx, true) + 4 * axis_opt(dy, true) + 16 * axis_opt(dz, false);     // {0, 1}
+    tq[2] = axis_opt(dx, true) + 4 * axis_opt(dy, false) + 16 * axis_opt(dz, true);     // {0, 2}
+    tq[3] = axis_opt(dx, false) + 4 * axis_opt(dy, true) + 16 * axis_opt(dz, true);     // {1, 2}
+    __shared__ float2 kap_s[27 * 9];
+    __shared__ double kapd_s[27 * 9];
+    __shared__ double stage_s[WPB][27 * 9];     // one node's d rows, written back coalesced
+    double *stage = stage_s[threadIdx.x >> 5];
+    for (int t = threadIdx.x; t < 27 * 9; t += blockDim.x) {
+        kap_s[t] = kappa_g[t];
+        kapd_s[t] = (double)kappa_g[t].x + (double)kappa_g[t].y;
+    }
+    __syncthreads();
+    // stage constants
+    const int ox = lane & 3, oy = (lane >> 2) & 3;
+    const int yzx = (lane >> 2) & 3;            // stage X: (cy, cz) of lanes 0..15
+    const int czy = (lane >> 4) & 1;            // stage Y: cz of lane
+    const int oz0 = (lane < 16) ? 0 : 1, oz1 = oz0 + 2;
+    const float cx_ = opt_coef(ox), cy_ = opt_coef(oy), cz0_ = opt_coef(oz0), cz1_ = opt_coef(oz1);
+    const int N[3] = {nx, ny, nz};
+
+    const int64_t nchunks = (nn + kChunk - 1) / kChunk;
+    const int64_t warps = (int64_t)gridDim.x * WPB;
+    for (int64_t ch = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5); ch < nchunks; ch += warps) {
+        const int64_t n_begin = ch * kChunk;
+        const int64_t n_end = min(n_begin + (int64_t)kChunk, nn);
+        NodeIter it;
+        it.decode((uint32_t)n_begin, nx, ny);
+        float2 cur = load_corner(Edf, it.idx, lane, nx, ny, nz);
+        int64_t off = node_off[n_begin];
+        for (int64_t n = n_begin; n < n_end; n++) {
+            const int idx[3] = {it.idx[0], it.idx[1], it.idx[2]};
+            // prefetch the next node's corner modulus and CSR offset
+            it.step(nx, ny);
+            float2 nxt = make_float2(0.f, 0.f);
+            int64_t off_next = 0;
+            if (n + 1 < n_end) {
+                nxt = load_corner(Edf, it.idx, lane, nx, ny, nz);
+                off_next = node_off[n + 1];
+            }
+            const df Ec = df{cur.x, cur.y};
+            const bool bad = lane < 8 && isnan(cur.y);
+            const bool interior = idx[0] > 0 && idx[0] < nx && idx[1] > 0 && idx[1] < ny && idx[2] > 0 && idx[2] < nz;
+            bool valid;
+            int mi, rowlen;
+            if (interior) {
+                valid = lane < 27;
+                mi = lane;
+                rowlen = 81;
+            } else {
+                int lo[3], cnt[3];
+                for (int m = 0; m < 3; m++) {
+                    lo[m] = idx[m] > 0 ? -1 : 0;
+                    cnt[m] = (idx[m] < N[m] ? 1 : 0) - lo[m] + 1;
+                }
+                valid = lane < 27 && dx >= lo[0] && dx < lo[0] + cnt[0] && dy >= lo[1] && dy < lo[1] + cnt[1] &&
+                        dz >= lo[2] && dz < lo[2] + cnt[2];
+                mi = (dx - lo[0]) + cnt[0] * ((dy - lo[1]) + cnt[1] * (dz - lo[2]));
+                rowlen = 3 * cnt[0] * cnt[1] * cnt[2];
+            }
+            double *base = vals + 9 * off;
+            if (__any_sync(kFull, bad)) {
+                lattice_node_fp64<3>(nx, ny, nz, idx[0], idx[1], idx[2], dl, valid, mi, rowlen, base, K0, rho, sp);
+            } else {
+                // stage X: lanes 0..15 -> (ox, cy, cz)
+                const df xL = shfl_df(Ec, 2 * yzx), xH = shfl_df(Ec, 2 * yzx + 1);
+                const df X = combine(ox == 0, cx_, xL, xH);
+                // stage Y: lanes 0..31 -> (ox, oy, cz)
+                const df yL = shfl_df(X, ox + 4 * (2 * czy)), yH = shfl_df(X, ox + 4 * (1 + 2 * czy));
+                const df Y = combine(oy == 0, cy_, yL, yH);
+                // stage Z: lane holds entries lane (A) and lane + 32 (B)
+                const df zL = shfl_df(Y, lane & 15), zH = shfl_df(Y, (lane & 15) + 16);
+                const df A = combine(oz0 == 0, cz0_, zL, zH), B = combine(false, cz1_, zL, zH);
+                df T[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const df a = shfl_df(A, tq[q] & 31), b = shfl_df(B, tq[q] & 31);
+                    T[q] = tq[q] >= 32 ? b : a;
+                }
+                if (valid) {
+                    // Two routes to an FP64 value, balancing the FP32/integer
+                    // pipes against the otherwise idle FP64 pipe: classes below
+                    // kFp64Classes convert T once and take one DMUL per entry;
+                    // the others multiply in float pairs and convert each entry.
+                    double Td[kFp64Classes];
+#pragma unroll
+                    for (int q = 0; q < kFp64Classes; q++) Td[q] = df_to_double(T[q].h, T[q].l);
+#pragma unroll
+                    for (int i = 0; i < 3; i++) {
+                        double *row = stage + i * rowlen + 3 * mi;
+#pragma unroll
+                        for (int j = 0; j < 3; j++) {
+                            const int q = (i == j) ? 0 : (i + j == 1 ? 1 : (i + j == 2 ? 2 : 3));
+                            if (q < kFp64Classes) {
+                                row[j] = kapd_s[dl * 9 + i * 3 + j] * Td[q < kFp64Classes ? q : 0];
+                            } else {
+                                const float2 kv = kap_s[dl * 9 + i * 3 + j];
+                                const df v = df_mul_raw(df{kv.x, kv.y}, T[q]);
+                                row[j] = df_to_double(v.h, v.l);
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+                const int blk = 3 * rowlen;
+                for (int t = lane; t < blk; t += 32) __stcs(base + t, stage[t]);
+                __syncwarp();
+            }
+            cur = nxt;
+            off = off_next;
+        }
+    }
+}
+
+// 2D: three nodes per warp, lanes 9g .. 9g+8 serve node g, one lane per offset.
+template <int WPB>
+__global__ void __launch_bounds__(WPB * 32)
+k_lattice_assemble2(int nx, int ny, int64_t nn, const int64_t *__restrict__ node_off,
+                    const float2 *__restrict__ Edf, const float2 *__restrict__ kappa_g,
+                    const double *__restrict__ K0, const double *__restrict__ rho, SimpParams sp,
+                    double *__restrict__ vals)
+{
+    __shared__ float2 kap_s[9 * 4];
+    __shared__ double stage_s[WPB][3 * 9 * 4];   // three nodes' rows, written back coalesced
+    for (int t = threadIdx.x; t < 9 * 4; t += blockDim.x) kap_s[t] = kappa_g[t];
+    __syncthreads();
+    double *stage = stage_s[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int g = lane < 27 ? lane / 9 : 2;
+    const int dl = lane < 27 ? lane % 9 : 8;
+    const int dx = dl % 3 - 1, dy = dl / 3 - 1;
+    df kap[4];
+    for (int q = 0; q < 4; q++) kap[q] = df{kap_s[dl * 4 + q].x, kap_s[dl * 4 + q].y};
+    const int N[3] = {nx, ny, 1};
+    const int64_t warps = (int64_t)gridDim.x * WPB;
+    for (int64_t n0 = ((int64_t)blockIdx.x * WPB + (threadIdx.x >> 5)) * 3; n0 < nn; n0 += warps * 3) {
+        const int64_t n = n0 + g;
+        const bool live = lane < 27 && n < nn;
+        int idx[3] = {0, 0, 0};
+        if (live) {
+            idx[0] = (int)(n % (nx + 1));
+            idx[1] = (int)(n / (nx + 1));
+        }
+        df E[4];
+        bool bad = false;
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            E[c] = df{0.f, 0.f};
+            const int ex = idx[0] - 1 + (c & 1), ey = idx[1] - 1 + (c >> 1);
+            if (live && ex >= 0 && ex < nx && ey >= 0 && ey < ny) {
+                const float2 v = Edf[(int64_t)ey * nx + ex];
+                E[c] = df{v.x, v.y};
+                bad |= isnan(v.y);
+            }
+        }
+        int lo[2], cnt[2];
+        for (int m = 0; m < 2; m++) {
+            lo[m] = idx[m] > 0 ? -1 : 0;
+            cnt[m] = (idx[m] < N[m] ? 1 : 0) - lo[m] + 1;
+        }
+        const bool valid = live && dx >= lo[0] && dx < lo[0] + cnt[0] && dy >= lo[1] && dy < lo[1] + cnt[1];
+        const int mi = (dx - lo[0]) + cnt[0] * (dy - lo[1]);
+        const int rowlen = 2 * cnt[0] * cnt[1];
+        double *base = live ? vals + 4 * node_off[n] : vals;
+        if (__any_sync(kFull, bad)) {
+            // the whole warp takes the FP64 route for its (up to) three nodes
+            lattice_node_fp64<2>(nx, ny, 1, idx[0], idx[1], 0, dl, valid, mi, rowlen, base, K0, rho, sp);
+            continue;
+        }
+        // signed sums over the shared cells: diagonal class and the {0,1} class
+        df Td = df{0.f, 0.f}, Tp = df{0.f, 0.f};
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const int cx = c & 1, cy = c >> 1;
+            // cell c is shared with the neighbour iff the neighbour's corner stays in {0, 1}
+            const bool shared = (1 - cx + dx >= 0) && (1 - cx + dx <= 1) && (1 - cy + dy >= 0) && (1 - cy + dy <= 1);
+            if (!shared) continue;
+            const bool flip = ((dx == 0 && cx == 0) != (dy == 0 && cy == 0));
+            Td = df_add(Td, E[c]);
+            Tp = df_add(Tp, flip ? df_neg(E[c]) : E[c]);
+        }
+        // the (up to) three nodes' blocks are consecutive in the CSR values
+        const int64_t n_last = min(n0 + 2, nn - 1);
+        const int64_t off0 = node_off[n0];
+        const int span = (int)(4 * (node_off[n_last + 1] - off0));
+        const int sbase = live ? (int)(4 * (node_off[n] - off0)) : 0;
+        if (valid) {
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                double *row = stage + sbase + i * rowlen + 2 * mi;
+#pragma unroll
+                for (int j = 0; j < 2; j++) {
+                    const df v = df_mul_raw(kap[i * 2 + j], i == j ? Td : Tp);
+                    row[j] = df_to_double(v.h, v.l);
+                }
+            }
+        }
+        __syncwarp();
+        for (int t = lane; t < span; t += 32) __stcs(vals + 4 * off0 + t, stage[t]);
+        __syncwarp();
+    }
+}
+
+// Sensitivity on the box lattice.  The reflections of a box across its
+// mid-planes commute with K^0, so in the Walsh basis of each displacement
+// component, f_t(a) = (-1)^(t.a) over the 2^d corners a, K^0 splits into 2^d
+// independent d x d blocks: sector c couples the modes t = c xor e_i of the
+// components i.  With w_{t,i} = sum_a f_t(a) u_{a,i} (a fast Walsh transform),
+//     u_e^T K^0 u_e = sum_c sum_ij w_{c^e_i, i} B_c[i][j] w_{c^e_j, j},
+// B_c[i][j] = f_{c^e_i}^T K^0_{ij} f_{c^e_j} / 4^d, each term of the outer sum
+// a non-negative energy.  One thread per cell, float-pair arithmetic.
+template <int D>
+__global__ void __launch_bounds__(128, 3)
+k_lattice_sens(int nx, int ny, int nz, int64_t nc, const double *__restrict__ rho, const double *__restrict__ u,
+               SimpParams sp, const float2 *__restrict__ Bg, const double *__restrict__ gscale,
+               double *__restrict__ out, double *__restrict__ partial)
+{
+    constexpr int NCR = 1 << D;
+    __shared__ float2 Bs[NCR * D * D];
+    __shared__ double wsum[8];
+    for (int t = threadIdx.x; t < NCR * D * D; t += blockDim.x) Bs[t] = Bg[t];
+    __syncthreads();
+    const double g = gscale ? *gscale : -1.0;
+    double mine = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc; e += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t ue = (uint32_t)e;
+        const int ex = (int)(ue % (uint32_t)nx);
+        const uint32_t r = ue / (uint32_t)nx;
+        const int ey = D == 3 ? (int)(r % (uint32_t)ny) : (int)r;
+        const int ez = D == 3 ? (int)(r / (uint32_t)ny) : 0;
+        df w[NCR][D];
+#pragma unroll
+        for (int a = 0; a < NCR; a++) {
+            const int64_t node = (int64_t)(ex + (a & 1)) +
+                                 (int64_t)(nx + 1) * ((ey + ((a >> 1) & 1)) + (int64_t)(ny + 1) * (ez + (a >> 2)));
+#pragma unroll
+            for (int i = 0; i < D; i++) w[a][i] = df_split(u[D * node + i]);
+        }
+        // in-place Walsh transform along each axis
+#pragma unroll
+        for (int m = 0; m < D; m++)
+#pragma unroll
+            for (int a = 0; a < NCR; a++)
+                if (!(a & (1 << m)))
+#pragma unroll
+                    for (int i = 0; i < D; i++) {
+                        const df x = w[a][i], y = w[a | (1 << m)][i];
+                        w[a][i] = df_add_lazy(x, y);
+                        w[a | (1 << m)][i] = df_add_lazy(x, df_neg(y));
+                    }
+        // compensated sum of the sector energies: S + C
+        float S = 0.f, C = 0.f;
+#pragma unroll
+        for (int c = 0; c < NCR; c++) {
+            df x[D];
+#pragma unroll
+            for (int i = 0; i < D; i++) x[i] = w[c ^ (1 << i)][i];
+#pragma unroll
+            for (int i = 0; i < D; i++)
+#pragma unroll
+                for (int j = i; j < D; j++) {
+                    const float2 bb = Bs[(c * D + i) * D + j];     // off-diagonal entries pre-doubled
+                    const df t = df_mul_raw(df_mul_raw(x[i], x[j]), df{bb.x, bb.y});
+                    float err;
+                    two_sum(S, t.h, S, err);
+                    C = __fadd_rn(C, __fadd_rn(t.l, err));
+                }
+        }
+        df s;
+        two_sum(S, C, s.h, s.l);
+        const double sd = df_to_double(s.h, s.l);
+        const double re = rho[e];
+        out[e] = g * simp_dE(sp, re) * sd;
+        mine += simp_E(sp, re) * sd;
+    }
+    if (partial) {
+        mine = warp_sum(mine);
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (lane == 0) wsum[warp] = mine;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w2 = 0; w2 < (int)(blockDim.x >> 5); w2++) t += wsum[w2];
+            partial[blockIdx.x] = t;
+        }
+    }
+}
+
+}  // namespace
+
+constexpr int kSensThreads = 128;
+int lattice_sens_grid(int64_t nc)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>((nc + kSensThreads - 1) / kSensThreads, 152 * 12));
+}
+
+cudaError_t launch_lattice_sensitivity(const soptx_mesh_s &m, const double *rho, const double *u, double *out,
+                                       double *c, const double *gscale, cudaStream_t st)
+{
+    const auto &h = m.h;
+    const int grid = lattice_sens_grid(h.nc);
+    double *part = c ? m.d.scratch : nullptr;
+    if (h.dim == 3)
+        k_lattice_sens<3><<<grid, kSensThreads, 0, st>>>(h.lat_n[0], h.lat_n[1], h.lat_n[2], h.nc, rho, u, simp_params(m.mat),
+                                                (const float2 *)m.d.sectors, gscale, out, part);
+    else
+        k_lattice_sens<2><<<grid, kSensThreads, 0, st>>>(h.lat_n[0], h.lat_n[1], 1, h.nc, rho, u, simp_params(m.mat),
+                                                (const float2 *)m.d.sectors, gscale, out, part);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess || !c) return err;
+    k_reduce_partials<<<1, 256, 0, st>>>(grid, m.d.scratch, c);
+    return cudaGetLastError();
+}
+
+// Sector blocks B_c[i][j] of a box element's K^0 (see k_lattice_sens), the
+// off-diagonal ones doubled (only i <= j is summed); returns
+// false when K^0 does not split into the 2^d sectors (then the general
+// sensitivity kernel is used).
+bool build_lattice_sectors(int dim, const std::vector<double> &K0, std::vector<float2> &B)
+{
+    const int ncr = 1 << dim, ldof = dim * ncr;
+    auto f = [](int t, int a) { return (__builtin_popcount(t & a) & 1) ? -1.0 : 1.0; };
+    double fmax = 0.0, offmax = 0.0;
+    std::vector<double> F((size_t)ncr * dim * ncr * dim);
+    for (int t = 0; t < ncr; t++)
+        for (int i = 0; i < dim; i++)
+            for (int t2 = 0; t2 < ncr; t2++)
+                for (int j = 0; j < dim; j++) {
+                    double s = 0.0;
+                    for (int a = 0; a < ncr; a++)
+                        for (int b = 0; b < ncr; b++) s += f(t, a) * K0[(size_t)(dim * a + i) * ldof + dim * b + j] * f(t2, b);
+                    F[(((size_t)t * dim + i) * ncr + t2) * dim + j] = s;
+                    fmax = std::max(fmax, std::fabs(s));
+                    if ((t ^ (1 << i)) != (t2 ^ (1 << j))) offmax = std::max(offmax, std::fabs(s));
+                }
+    if (!(offmax <= 1e-13 * fmax)) return false;
+    const double norm = 1.0 / ((double)ncr * ncr);
+    B.assign((size_t)ncr * dim * dim, make_float2(0.f, 0.f));
+    for (int c = 0; c < ncr; c++)
+        for (int i = 0; i < dim; i++)
+            for (int j = 0; j < dim; j++) {
+                const double x = (i == j ? 1.0 : 2.0) * norm *
+                                 F[(((size_t)(c ^ (1 << i)) * dim + i) * ncr + (c ^ (1 << j))) * dim + j];
+                const float hh = (float)x;
+                B[((size_t)c * dim + i) * dim + j] = make_float2(hh, (float)(x - (double)hh));
+            }
+    return true;
+}
+
+cudaError_t launch_lattice_assemble(const soptx_mesh_s &m, const double *rho, double *vals, cudaStream_t st)
+{
+    const auto &h = m.h;
+    const SimpParams sp = simp_params(m.mat);
+    const int eb = 256;
+    const int egrid = (int)std::min<int64_t>((h.nc + eb - 1) / eb, 152 * 8);
+    k_simp_df<<<std::max(egrid, 1), eb, 0, st>>>(h.nc, rho, sp, (float2 *)m.d.Edf);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    constexpr int WPB = 8;
+    if (h.dim == 3) {
+        const int64_t chunks = (h.nn + kChunk - 1) / kChunk;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((chunks + WPB - 1) / WPB, 152 * 4));
+        k_lattice_assemble3<WPB><<<grid, WPB * 32, 0, st>>>(h.lat_n[0], h.lat_n[1], h.lat_n[2], h.nn, m.d.node_off,
+                                                            (const float2 *)m.d.Edf, (const float2 *)m.d.kappa,
+                                                            m.d.K0, rho, sp, vals);
+    } else {
+        const int64_t groups = (h.nn + 2) / 3;
+        const int grid = (int)std::min<int64_t>((groups + WPB - 1) / WPB, 152 * 8);
+        k_lattice_assemble2<WPB><<<grid, WPB * 32, 0, st>>>(h.lat_n[0], h.lat_n[1], h.nn, m.d.node_off,
+                                                            (const float2 *)m.d.Edf, (const float2 *)m.d.kappa,
+                                                            m.d.K0, rho, sp, vals);
+    }
+    return cudaGetLastError();
+}
+
+// kappa_delta[i][j] = K0[(a*, i), (b*, j)] for every offset delta (x fastest),
+// a*, b* the corners of n and n + delta in the reference cell (high side on
+// zero axes).  Stored as float pairs.
+void build_lattice_kappa(int dim, const std::vector<double> &K0, std::vector<float2> &kappa)
+{
+    const int nd = dim == 3 ? 27 : 9, ldof = dim * (1 << dim);
+    kappa.assign((size_t)nd * dim * dim, make_float2(0.f, 0.f));
+    for (int dl = 0; dl < nd; dl++) {
+        int a = 0, b = 0, r = dl;
+        for (int m = 0; m < dim; m++) {
+            const int delta = r % 3 - 1;
+            r /= 3;
+            const int am = delta < 0 ? 1 : 0, bm = am + delta;
+            a |= am << m;
+            b |= bm << m;
+        }
+        for (int i = 0; i < dim; i++)
+            for (int j = 0; j < dim; j++) {
+                const double x = K0[(size_t)(dim * a + i) * ldof + dim * b + j];
+                const float hh = (float)x;
+                const float ll = (float)(x - (double)hh);
+                kappa[(size_t)dl * dim * dim + i * dim + j] = make_float2(hh, ll);
+            }
+    }
+}
+
+}  // namespace soptx

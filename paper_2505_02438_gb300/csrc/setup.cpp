@@ -136,8 +136,16 @@ bool geometry(HostMesh &hm, const double *coords, const int32_t *cv, std::string
         double *g = &hm.geo[(size_t)e * ng];
         for (int q = 0; q < d * d; q++) g[q] = G[q];
         g[d * d] = std::fabs(det);
-        if (e == 0) std::memcpy(J0, J, sizeof(J));
-        else if (hm.uniform && std::memcmp(J0, J, sizeof(double) * d * d) != 0) hm.uniform = false;
+        // uniform: every Jacobian equals the first to within rounding of the
+        // coordinates (1e-14 of its largest entry), so one K^0 serves all cells
+        if (e == 0) {
+            std::memcpy(J0, J, sizeof(J));
+        } else if (hm.uniform) {
+            double j0max = 0.0;
+            for (int q = 0; q < d * d; q++) j0max = std::max(j0max, std::fabs(J0[q]));
+            for (int q = 0; q < d * d; q++)
+                if (std::fabs(J[q] - J0[q]) > 1e-14 * j0max) hm.uniform = false;
+        }
     }
     return true;
 }

@@ -133,3 +133,32 @@ def test_allocation_failure_rolls_back(P):
             N.lib().soptx_debug_fail_alloc_after(0)
     m = P.Mesh("tet", 2, c, cl)          # the library is still usable
     assert m.nnz > 0
+
+
+@pytest.mark.parametrize("cell,mk", [("hex", lambda: W.structured_hex(5, 4, 3)), ("quad", lambda: W.structured_quad(9, 7))])
+def test_lattice_out_of_range_moduli_take_fp64_route(P, cell, mk):
+    """With Emin = 0, tiny densities give moduli below the float-pair range;
+    those nodes are assembled in plain FP64 and must still match."""
+    c, cl = mk()
+    mat = (1.0, 0.0, 0.3, 3.0, 0)
+    m = P.Mesh(cell, 1, c, cl, *mat)
+    assert m.path == "lattice"
+    g = np.random.default_rng(8)
+    rho = g.uniform(0.001, 1.0, len(cl))
+    rho[::5] = 1e-9          # E = 1e-27
+    rho[1::7] = 0.0          # E = 0 exactly
+    vals = m.assemble_K(to_dev(rho)).cpu().numpy()
+    rp, ci, v, va, _ = oracle_csr(cell, 1, c, cl, mat, rho)
+    assert np.all(np.abs(vals - v) <= TOL64 * va + 1e-300)
+
+
+def test_lattice_anisotropic_boxes(P):
+    """Box cells with different edge lengths per axis and a shifted origin."""
+    c, cl = W.structured_hex(6, 4, 3)
+    c = c * np.array([0.5, 1.25, 2.0]) + np.array([3.0, -1.0, 0.25])
+    m, *_ = check_assembly(P, "hex", 1, c, cl, "fp64")
+    assert m.path == "lattice"
+    c, cl = W.structured_quad(8, 5)
+    c = c * np.array([2.0, 0.3])
+    m, *_ = check_assembly(P, "quad", 1, c, cl, "fp64")
+    assert m.path == "lattice"
