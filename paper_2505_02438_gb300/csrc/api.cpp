@@ -32,7 +32,8 @@ cudaError_t dev_alloc(void **p, size_t bytes)
 static void free_device(DeviceMesh &d)
 {
     void *ptrs[] = {d.indptr, d.indices, d.cell_node, d.node_off, d.inc_ptr, d.inc,
-                    d.pos, d.geo, d.M, d.K, d.scratch, d.Edf, d.kappa, d.K0, d.sectors};
+                    d.pos, d.geo, d.M, d.K, d.scratch, d.Edf, d.kappa, d.K0, d.sectors, d.udf, d.part,
+                    d.inc_e, d.inc_a};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     d = DeviceMesh{};
@@ -153,6 +154,8 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
     UP(d.node_off, h.node_off, "node_off");
     UP(d.inc_ptr, h.inc_ptr, "inc_ptr");
     UP(d.inc, h.inc, "inc");
+    UP(d.inc_e, h.inc_e, "inc_e");
+    UP(d.inc_a, h.inc_a, "inc_a");
     UP(d.pos, h.pos, "pos");
     UP(d.M, ref.M, "reference integrals");
 #undef UP
@@ -164,7 +167,7 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
     }
     const int64_t n_elem_mats = (m->path == SOPTX_PATH_CACHED) ? h.nc : (h.nc > 0 ? 1 : 0);
     if (s == SOPTX_OK) {
-        size_t esz = (prec == SOPTX_ELEM_FP32) ? 4 : 8;
+        size_t esz = (prec == SOPTX_ELEM_FP32) ? 4 : 8;   // float, or a float pair
         size_t bytes = (size_t)std::max<int64_t>(n_elem_mats, 1) * h.ldof * h.ldof * esz;
         cudaError_t e = dev_alloc(&d.K, bytes);
         if (e != cudaSuccess) { cudaGetLastError(); s = cuda_status(e, "element matrices"); }
@@ -178,6 +181,18 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
     }
     if (s == SOPTX_OK) s = cuda_status(launch_element_matrices(*m, n_elem_mats, st), "element matrices kernel");
     if (s == SOPTX_OK) s = cuda_status(cudaStreamSynchronize(st), "mesh setup");
+    if (s == SOPTX_OK && m->path != SOPTX_PATH_LATTICE) {
+        // per-call float-pair moduli and displacements, per-(cell, node) partials
+        void *p1 = nullptr, *p2 = nullptr, *p3 = nullptr;
+        cudaError_t e = dev_alloc(&p1, (size_t)std::max<int64_t>(h.nc, 1) * sizeof(float2));
+        if (e == cudaSuccess) e = dev_alloc(&p2, (size_t)std::max<int64_t>(h.ndof, 1) * sizeof(float2));
+        if (e == cudaSuccess) e = dev_alloc(&p3, (size_t)std::max<int64_t>(h.nc * h.nb, 1) * sizeof(double));
+        d.Edf = (float2 *)p1;
+        d.udf = (float2 *)p2;
+        d.part = (double *)p3;
+        if (e != cudaSuccess) { cudaGetLastError(); s = cuda_status(e, "general-path scratch"); }
+        else B += std::max<int64_t>(h.nc, 1) * 8 + std::max<int64_t>(h.ndof, 1) * 8 + std::max<int64_t>(h.nc * h.nb, 1) * 8;
+    }
     if (s == SOPTX_OK && m->path == SOPTX_PATH_LATTICE) {
         // the lattice kernels read one FP64 K^0, its reference blocks as float
         // pairs, and per-call element moduli
@@ -188,7 +203,9 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
             s = cuda_status(cudaMemcpy(Kf.data(), d.K, n2 * sizeof(float), cudaMemcpyDeviceToHost), "K0");
             for (size_t q = 0; q < n2; q++) K0[q] = Kf[q];
         } else {
-            s = cuda_status(cudaMemcpy(K0.data(), d.K, n2 * sizeof(double), cudaMemcpyDeviceToHost), "K0");
+            std::vector<float2> Kp(n2);
+            s = cuda_status(cudaMemcpy(Kp.data(), d.K, n2 * sizeof(float2), cudaMemcpyDeviceToHost), "K0");
+            for (size_t q = 0; q < n2; q++) K0[q] = (double)Kp[q].x + (double)Kp[q].y;
         }
         std::vector<float2> kappa;
         build_lattice_kappa(h.dim, K0, kappa);
@@ -214,6 +231,8 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
     // host copies that the kernels do not need any more
     std::vector<uint16_t>().swap(h.pos);
     std::vector<int32_t>().swap(h.inc);
+    std::vector<int32_t>().swap(h.inc_e);
+    std::vector<uint8_t>().swap(h.inc_a);
     *out = m;
     return SOPTX_OK;
 }
@@ -337,9 +356,11 @@ soptx_status soptx_sensitivity(soptx_mesh m, const double *d_rho, const double *
 soptx_status soptx_assemble_and_sensitivity(soptx_mesh m, const double *d_rho, const double *d_u, double *d_vals,
                                             double *d_dc, double *d_c, void *stream)
 {
-    soptx_status s = soptx_assemble_K(m, d_rho, d_vals, stream);
-    if (s != SOPTX_OK) return s;
-    return soptx_sensitivity(m, d_rho, d_u, d_dc, d_c, stream);
+    if (!m) SOPTX_FAIL(SOPTX_EINVAL, "mesh is NULL");
+    if ((!d_vals && m->h.nnz > 0) || (m->h.nc > 0 && (!d_rho || !d_u || !d_dc)))
+        SOPTX_FAIL(SOPTX_EINVAL, "d_rho / d_u / d_vals / d_dc is NULL");
+    return cuda_status(launch_step(*m, d_rho, d_u, d_vals, d_dc, d_c, (cudaStream_t)stream),
+                       "soptx_assemble_and_sensitivity");
 }
 
 soptx_status soptx_compliance_vjp(soptx_mesh m, const double *d_rho, const double *d_u, const double *d_gout,

@@ -76,8 +76,8 @@ __device__ __forceinline__ df df_from_double(double x)
 
 // Out-of-line rare paths: keeping them as real calls stops the compiler from
 // if-converting them into FP64-pipe work on every element of a hot loop.
-__device__ __noinline__ df df_from_double_slow(double x) { return df_from_double(x); }
-__device__ __noinline__ double df_to_double_slow(float h, float l) { return (double)h + (double)l; }
+static __device__ __noinline__ df df_from_double_slow(double x) { return df_from_double(x); }
+static __device__ __noinline__ double df_to_double_slow(float h, float l) { return (double)h + (double)l; }
 
 // Split a double into a pair with integer operations (no FP64 pipe): h keeps
 // the leading 24 significand bits (truncated), l the remaining 29 bits

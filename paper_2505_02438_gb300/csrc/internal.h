@@ -54,6 +54,8 @@ struct HostMesh {
     std::vector<int32_t> nbr;           // [node_off[nn]] sorted neighbour nodes
     std::vector<int32_t> inc_ptr;       // [nn+1]
     std::vector<int32_t> inc;           // [ninc] e * nb + a, ascending e per node
+    std::vector<int32_t> inc_e;         // [ninc] e
+    std::vector<uint8_t> inc_a;         // [ninc] a
     std::vector<uint16_t> pos;          // [ninc][nb] column block of node b in row n
     std::vector<double> geo;            // [nc][dim*dim + 1]: G = J^-1 (row-major), |det J|
     bool uniform = false;               // every cell has the same Jacobian
@@ -74,6 +76,8 @@ struct DeviceMesh {
     int64_t *node_off = nullptr;   // [nn+1]
     int32_t *inc_ptr = nullptr;    // [nn+1]
     int32_t *inc = nullptr;        // [ninc]
+    int32_t *inc_e = nullptr;      // [ninc] cell of each incidence
+    uint8_t *inc_a = nullptr;      // [ninc] local node of each incidence
     uint16_t *pos = nullptr;       // [ninc][nb]
     double *geo = nullptr;         // [nc][dim*dim+1]
     double *M = nullptr;           // reference integrals [dim][dim][nb][nb]
@@ -85,6 +89,9 @@ struct DeviceMesh {
     float2 *kappa = nullptr;       // [3^d][d][d] reference blocks as float pairs
     double *K0 = nullptr;          // [ldof][ldof] unit-modulus matrix in FP64
     float2 *sectors = nullptr;     // [2^d][d][d] Walsh-sector blocks of K^0 (nullptr: no split)
+    // general path
+    float2 *udf = nullptr;         // [ndof] u as float pairs
+    double *part = nullptr;        // [nc][nb] per-(cell, node) partials of u_e^T K_e^0 u_e
 };
 
 struct Material {
@@ -121,5 +128,10 @@ bool build_lattice_sectors(int dim, const std::vector<double> &K0, std::vector<f
 cudaError_t launch_lattice_sensitivity(const soptx_mesh_s &m, const double *rho, const double *u, double *out,
                                        double *c, const double *gscale, cudaStream_t st);
 int lattice_sens_grid(int64_t nc);
+cudaError_t launch_gather(const soptx_mesh_s &m, const double *rho, const double *u, double *vals, double *dc,
+                          double *c, const double *gscale, cudaStream_t st);
+int gather_finalize_grid(int64_t nc);
+cudaError_t launch_step(const soptx_mesh_s &m, const double *rho, const double *u, double *vals, double *dc,
+                        double *c, cudaStream_t st);
 __global__ void k_reduce_partials(int n, const double *__restrict__ partial, double *__restrict__ c);
 }  // namespace soptx

@@ -42,4 +42,20 @@ __device__ __forceinline__ double warp_sum(double v)
 struct Material;
 SimpParams simp_params(const Material &m);
 
+// Element-matrix entries: float pairs (FP64 element matrices, value h + l) or
+// plain floats (FP32 element matrices).
+template <typename KT> struct KLoad;
+template <> struct KLoad<float2> {
+    static __device__ __forceinline__ float2 raw(const float2 *p) { return __ldcs(p); }
+    static __device__ __forceinline__ double get64(const float2 *p)
+    {
+        const float2 v = *p;
+        return (double)v.x + (double)v.y;
+    }
+};
+template <> struct KLoad<float> {
+    static __device__ __forceinline__ float2 raw(const float *p) { return make_float2(__ldcs(p), 0.f); }
+    static __device__ __forceinline__ double get64(const float *p) { return (double)*p; }
+};
+
 }  // namespace soptx

@@ -355,6 +355,12 @@ bool setup_host_mesh(int dim, int cell, int order, int64_t nv, const double *coo
                 int32_t n = hm.cell_node[(size_t)e * nb + a];
                 hm.inc[fill[n]++] = (int32_t)(e * nb + a);
             }
+        hm.inc_e.resize(hm.ninc);
+        hm.inc_a.resize(hm.ninc);
+        for (int64_t q = 0; q < hm.ninc; q++) {
+            hm.inc_e[q] = hm.inc[q] / nb;
+            hm.inc_a[q] = (uint8_t)(hm.inc[q] % nb);
+        }
     }
 
     // ---- node adjacency (sorted neighbour nodes) and the position map
