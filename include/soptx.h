@@ -173,6 +173,35 @@ soptx_status soptx_compliance_vjp(soptx_mesh mesh, const double *d_rho, const do
                                   const double *d_gout, double *d_grad_rho, double *d_grad_u,
                                   void *stream);
 
+/*
+ * Allocation-free sensitivities on a box lattice.  The paper has no
+ * counterpart to this call: it exists for callers that must not allocate
+ * device memory -- code running under another framework's memory pool or
+ * allocator hooks, or in a process whose GPU memory is reserved up front --
+ * and therefore cannot create a mesh either (soptx_mesh_create allocates).
+ *
+ * The lattice is described by its sizes alone: cells_per_axis[dim] cells of
+ * edge lengths cell_size[dim] (host arrays), vertices, cells and corners in
+ * lexicographic order with x fastest, dofs node-interleaved -- the same layout
+ * and results as a mesh that soptx_mesh_create puts on its box-lattice path.
+ *   d_rho [n_cells], d_u [ndof], d_dc [n_cells]: device float64, caller-owned;
+ *   d_c: device float64 [1] or NULL.
+ * Computes d_dc[e] = -E'(rho_e) u_e^T K^0 u_e and *d_c = sum_e E(rho_e) u_e^T K^0 u_e.
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  Its only
+ * scratch, one partial sum of c per 1024 cells, is a fixed 64 KiB __device__
+ * array inside the library that every GPU loading the library keeps until the
+ * process exits; hence the limit: n_cells <= 8,388,608, larger lattices return
+ * SOPTX_EINVAL.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  All calls share the array, so calls that overlap
+ * on the device race on it; every call overwrites the slots it uses.
+ */
+soptx_status soptx_lattice_sensitivity_noalloc(int dim, const int32_t *cells_per_axis,
+                                               const double *cell_size, const soptx_material *mat,
+                                               const double *d_rho, const double *d_u, double *d_dc,
+                                               double *d_c, void *stream);
+
 /* Frees the mesh's device memory (synchronises the device first). */
 soptx_status soptx_mesh_destroy(soptx_mesh mesh);
 

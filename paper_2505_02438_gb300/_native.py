@@ -42,6 +42,7 @@ SIGNATURES = {
     "soptx_compliance_vjp": (i32, [P, P, P, P, P, P, P]),
     "soptx_mesh_destroy": (i32, [P]),
     "soptx_host_plan": (i32, [i32, i32, i32, i64, P, i64, P, Pi64, Pi64, Pi32, Pi32, P, P, P]),
+    "soptx_lattice_sensitivity_noalloc": (i32, [i32, P, P, ctypes.POINTER(Material), P, P, P, P, P]),
     "soptx_last_error": (ctypes.c_char_p, []),
     "soptx_version": (ctypes.c_char_p, []),
     "soptx_debug_fail_alloc_after": (None, [i64]),
