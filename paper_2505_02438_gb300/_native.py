@@ -27,6 +27,31 @@ class Material(ctypes.Structure):
                 ("p", ctypes.c_double), ("plane_strain", ctypes.c_int32)]
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_cap_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32), ("n_streams", ctypes.c_int32),
+                ("max_queue", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("job", ctypes.c_uint64), ("dim", ctypes.c_int32), ("cell", ctypes.c_int32),
+                ("order", ctypes.c_int32), ("n_vertices", ctypes.c_int64), ("coords", ctypes.c_void_p),
+                ("n_cells", ctypes.c_int64), ("cell_vertices", ctypes.c_void_p), ("mat", Material),
+                ("prec", ctypes.c_int32), ("d_rho", ctypes.c_void_p), ("d_u", ctypes.c_void_p),
+                ("d_vals", ctypes.c_void_p), ("d_dc", ctypes.c_void_p), ("d_c", ctypes.c_void_p)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("queue_us", ctypes.c_double), ("latency_us", ctypes.c_double),
+                ("gpu_us", ctypes.c_double), ("nnz", ctypes.c_int64), ("mesh_was_resident", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("evictions", ctypes.c_int64), ("mesh_setups", ctypes.c_int64), ("resident_bytes", ctypes.c_int64),
+                ("peak_resident_bytes", ctypes.c_int64), ("resident_meshes", ctypes.c_int32),
+                ("in_flight", ctypes.c_int32), ("queued", ctypes.c_int32)]
+
+
 SIGNATURES = {
     "soptx_mesh_create": (i32, [i32, i32, i32, i64, P, i64, P, ctypes.POINTER(Material), i32, P, PP]),
     "soptx_mesh_info": (i32, [P, Pi64, Pi64, Pi64, Pi32]),
@@ -43,6 +68,12 @@ SIGNATURES = {
     "soptx_mesh_destroy": (i32, [P]),
     "soptx_host_plan": (i32, [i32, i32, i32, i64, P, i64, P, Pi64, Pi64, Pi32, Pi32, P, P, P]),
     "soptx_lattice_sensitivity_noalloc": (i32, [i32, P, P, ctypes.POINTER(Material), P, P, P, P, P]),
+    "soptx_server_create": (i32, [ctypes.POINTER(ServerOpts), PP]),
+    "soptx_serve_submit": (i32, [P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "soptx_serve_wait": (i32, [P, ctypes.c_uint64, i64, ctypes.POINTER(Result)]),
+    "soptx_serve_poll": (i32, [P, ctypes.c_uint64, Pi32]),
+    "soptx_server_stats_get": (i32, [P, ctypes.POINTER(ServerStats)]),
+    "soptx_server_destroy": (i32, [P]),
     "soptx_last_error": (ctypes.c_char_p, []),
     "soptx_version": (ctypes.c_char_p, []),
     "soptx_debug_fail_alloc_after": (None, [i64]),

@@ -62,9 +62,9 @@ class Mesh:
         self.device_bytes = nbytes.value
 
     @classmethod
-    def from_workload(cls, wl, elem_prec="fp64", stream=None):
+    def from_workload(cls, wl, elem_prec=None, stream=None):
         return cls(wl.cell, wl.order, wl.coords, wl.cells, wl.E0, wl.Emin, wl.nu, wl.p, wl.plane_strain,
-                   elem_prec, stream)
+                   elem_prec or wl.elem_prec, stream)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

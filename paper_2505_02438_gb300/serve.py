@@ -1,0 +1,89 @@
+"""Python handle on the continuous-batching server of include/soptx_serve.h.
+
+The server keeps each design job's mesh resident, admits requests in arrival
+order as slots and HBM budget allow, and overlaps their kernels on a stream
+pool; this module only marshals requests and results."""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+
+class Server:
+    def __init__(self, hbm_cap_bytes=120 << 30, max_slots=16, n_streams=8, max_queue=4096, device=None):
+        dev = torch.cuda.current_device() if device is None else int(device)
+        self.device = torch.device("cuda", dev)
+        opts = N.ServerOpts(int(hbm_cap_bytes), int(max_slots), int(n_streams), int(max_queue), dev)
+        h = ctypes.c_void_p()
+        N.check(N.lib().soptx_server_create(ctypes.byref(opts), ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, job, wl, rho, u, vals=None, dc=None, c=None):
+        """Queue one iteration of design `job` (mesh and material from the
+        workload `wl`); returns a ticket.  Outputs are allocated if not given."""
+        coords = np.ascontiguousarray(wl.coords, np.float64)
+        cells = np.ascontiguousarray(wl.cells, np.int32)
+        nc = cells.shape[0]
+        if dc is None:
+            dc = torch.empty(nc, dtype=torch.float64, device=self.device)
+        if c is None:
+            c = torch.empty(1, dtype=torch.float64, device=self.device)
+        r = N.Request()
+        r.job = int(job)
+        r.dim = coords.shape[1]
+        r.cell = N.CELL[wl.cell]
+        r.order = int(wl.order)
+        r.n_vertices = coords.shape[0]
+        r.coords = coords.ctypes.data_as(ctypes.c_void_p)
+        r.n_cells = nc
+        r.cell_vertices = cells.ctypes.data_as(ctypes.c_void_p)
+        r.mat = N.Material(wl.E0, wl.Emin, wl.nu, wl.p, int(wl.plane_strain))
+        r.prec = N.PREC[getattr(wl, "elem_prec", "fp64")]
+        r.d_rho = ctypes.c_void_p(rho.data_ptr())
+        r.d_u = ctypes.c_void_p(u.data_ptr())
+        r.d_vals = ctypes.c_void_p(vals.data_ptr()) if vals is not None else None
+        r.d_dc = ctypes.c_void_p(dc.data_ptr())
+        r.d_c = ctypes.c_void_p(c.data_ptr())
+        t = ctypes.c_uint64()
+        N.check(N.lib().soptx_serve_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        self._keep[t.value] = (coords, cells, rho, u, vals, dc, c)
+        return t.value
+
+    def outputs(self, ticket):
+        coords, cells, rho, u, vals, dc, c = self._keep[ticket]
+        return vals, dc, c
+
+    def wait(self, ticket, timeout_us=-1):
+        res = N.Result()
+        N.check(N.lib().soptx_serve_wait(self._h, ctypes.c_uint64(ticket), int(timeout_us), ctypes.byref(res)))
+        out = dict(status=res.status, queue_us=res.queue_us, latency_us=res.latency_us, gpu_us=res.gpu_us,
+                   nnz=res.nnz, mesh_was_resident=bool(res.mesh_was_resident))
+        vals, dc, c = self.outputs(ticket)
+        out.update(vals=vals, dc=dc, c=c)
+        del self._keep[ticket]
+        return out
+
+    def poll(self, ticket):
+        d = ctypes.c_int32()
+        N.check(N.lib().soptx_serve_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(d)))
+        return bool(d.value)
+
+    def stats(self):
+        st = N.ServerStats()
+        N.check(N.lib().soptx_server_stats_get(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in N.ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            N.lib().soptx_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

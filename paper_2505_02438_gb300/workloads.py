@@ -135,6 +135,7 @@ class Workload:
     plane_strain: int = 0
     rho: np.ndarray = None
     seed_base: int = 0
+    elem_prec: str = "fp64"
     extra: dict = field(default_factory=dict)
 
     @property
@@ -197,3 +198,35 @@ def standard(i, scale=1.0):
     if i == 4:
         return jittered_tet(s(60), s(20), s(20))
     raise ValueError("workload %r has no single mesh" % i)
+
+
+def serving_stream(n_jobs=64, iters=8, wl=5, scale=1.0):
+    """The serving workload: n_jobs design jobs x iters requests.  Each job is a
+    mesh family drawn uniformly from {Q4 plane stress, hex Q1, Kuhn P2 tets}
+    with a size from t ~ U(0, 1) (Q4 from 60x20 to 800x400, hex from 30x10x10
+    to 120x40x40, tet cubes from 6x2x2 to 60x20x20, each axis shrunk by
+    `scale`), and FP64 or FP32 element matrices with probability 1/2.
+    Returns a list of jobs: dict(job, workload, elem_prec)."""
+    g = rng(wl, 4)
+    jobs = []
+    for j in range(n_jobs):
+        fam = int(g.integers(0, 3))
+        t = float(g.uniform(0.0, 1.0))
+        prec = "fp64" if g.uniform() < 0.5 else "fp32"
+        s = lambda n: max(1, int(round(n * scale)))
+        if fam == 0:
+            w = mbb_q4(s(60 * (800 / 60) ** t), s(20 * (400 / 20) ** t), wl=100 + j)
+        elif fam == 1:
+            f = 4 ** t
+            w = cantilever_hex(s(30 * f), s(10 * f), s(10 * f), wl=100 + j)
+        else:
+            f = 10 ** t
+            w = jittered_tet(s(6 * f), s(2 * f), s(2 * f), wl=100 + j)
+        w.elem_prec = prec
+        jobs.append(dict(job=j, workload=w, elem_prec=prec))
+    return jobs
+
+
+def poisson_arrivals(n, rate_per_s, wl=5):
+    """Arrival times (seconds) of n requests at the given Poisson rate."""
+    return np.cumsum(rng(wl, 3).exponential(1.0 / rate_per_s, size=n))

@@ -1,0 +1,97 @@
+"""The serving pattern: continuous batching of many design jobs on one GPU.
+Each result must be the same alone and in the mix; admission must respect the
+HBM cap (evicting idle meshes); the error paths must report, not hang."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2505_02438_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def inputs(m, job, it):
+    g = np.random.default_rng(1000 * job + it)
+    rho = torch.as_tensor(g.uniform(0.001, 1.0, m.n_cells), device="cuda")
+    u = torch.as_tensor(g.standard_normal(m.ndof), device="cuda")
+    return rho, u
+
+
+def run_mix(lib, jobs, iters, **server_kw):
+    from paper_2505_02438_gb300.serve import Server
+    meshes = {j["job"]: lib.Mesh.from_workload(j["workload"]) for j in jobs}
+    srv = Server(**server_kw)
+    tickets = []
+    for it in range(iters):
+        for j in jobs:
+            m = meshes[j["job"]]
+            rho, u = inputs(m, j["job"], it)
+            vals = torch.empty(m.nnz, dtype=torch.float64, device="cuda")
+            tickets.append((j["job"], it, rho, u, srv.submit(j["job"], j["workload"], rho, u, vals=vals)))
+    results = [(job, it, rho, u, srv.wait(t)) for job, it, rho, u, t in tickets]
+    stats = srv.stats()
+    srv.close()
+    return meshes, results, stats
+
+
+def check_same_as_alone(meshes, results):
+    for job, it, rho, u, r in results:
+        assert r["status"] == 0, (job, it, r["status"])
+        vals, dc, c = meshes[job].step(rho, u)
+        # the same deterministic kernels: identical bits alone and in the mix
+        assert torch.equal(vals, r["vals"]) and torch.equal(dc, r["dc"]) and torch.equal(c, r["c"]), (job, it)
+
+
+def test_mix_matches_alone(lib):
+    jobs = W.serving_stream(n_jobs=10, scale=0.2)
+    meshes, results, stats = run_mix(lib, jobs, iters=3, max_slots=6, n_streams=4)
+    check_same_as_alone(meshes, results)
+    assert stats["completed"] == 30 and stats["failed"] == 0
+    assert stats["mesh_setups"] == 10 and stats["evictions"] == 0
+    assert sum(not r["mesh_was_resident"] for *_, r in results) == 10
+
+
+def test_lowered_cap_evicts_idle_meshes(lib):
+    jobs = W.serving_stream(n_jobs=8, scale=0.2)
+    sizes = [lib.Mesh.from_workload(j["workload"]).device_bytes for j in jobs]
+    cap = int(1.2 * max(sizes))
+    meshes, results, stats = run_mix(lib, jobs, iters=2, hbm_cap_bytes=cap, max_slots=4, n_streams=2)
+    check_same_as_alone(meshes, results)
+    assert stats["evictions"] > 0
+    assert stats["peak_resident_bytes"] <= cap
+
+
+def test_error_paths(lib):
+    from paper_2505_02438_gb300 import _native as N
+    from paper_2505_02438_gb300.serve import Server
+    wl = W.cantilever_hex(40, 20, 20)
+    m = lib.Mesh.from_workload(wl)
+    rho, u = inputs(m, 0, 0)
+    # a mesh larger than the cap fails with ENOMEM
+    srv = Server(hbm_cap_bytes=1 << 20)
+    t = srv.submit(1, wl, rho, u)
+    assert srv.wait(t)["status"] == 2
+    with pytest.raises(N.SoptxError) as ei:
+        srv.wait(12345)
+    assert ei.value.code == 6
+    srv.close()
+    # a bounded wait that runs out reports ETIMEOUT and leaves the ticket valid
+    srv = Server(max_queue=1)
+    t = srv.submit(2, wl, rho, u)
+    with pytest.raises(N.SoptxError) as ei:
+        srv.wait(t, timeout_us=0)
+    assert ei.value.code == 5
+    # the queue holds one pending request while the first mesh is being set up
+    busy = 0
+    extra = []
+    for k in range(3):
+        try:
+            extra.append(srv.submit(3 + k, wl, rho, u))
+        except N.SoptxError as e:
+            assert e.code == 4
+            busy += 1
+    assert srv.wait(t)["status"] == 0
+    for x in extra:
+        assert srv.wait(x)["status"] == 0
+    assert busy >= 1
+    srv.close()
