@@ -3,15 +3,16 @@
 //
 //  k_prep          : E(rho_e) per cell and, when u is given, u per dof, as
 //                    float pairs (FP64 math once per item).
-//  k_gather_fused  : one warp owns the d rows of one node; it walks the node's
-//                    incident cells in ascending order and for each reads the
-//                    node's row block of K_e^0 once, adding E_e K_e^0 into the
-//                    rows' CSR values (float-pair accumulators in shared
-//                    memory, so every value is summed in ascending cell
-//                    order, no atomics) and, when u is given, forming the
-//                    cell's partial  sum_i u_(a,i) sum_(b,j) K_e[(a,i),(b,j)] u_(b,j)
-//                    for this node a.  The rows leave through coalesced
-//                    streaming stores.
+//  k_gather_nodes  : a group of lanes owns the d rows of one node; it walks
+//                    the node's incident cells in ascending order and for
+//                    each reads the node's row block of K_e^0 once, adding
+//                    E_e K_e^0 into the rows' CSR values (float-pair
+//                    accumulators in shared memory, so every value is summed
+//                    in ascending cell order, no atomics) and, when u is
+//                    given, forming the cell's partial
+//                    sum_i u_(a,i) sum_(b,j) K_e[(a,i),(b,j)] u_(b,j)  for
+//                    this node a.  The rows leave through coalesced streaming
+//                    stores.
 //  k_sens_finalize : s_e = sum of the cell's node partials (fixed order),
 //                    dc_e = -E'(rho_e) s_e and block partials of E_e s_e.
 // Nodes touching a modulus outside [2^-60, 2^60] are redone in plain FP64.
@@ -27,7 +28,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kGW = 8;   // warps per CTA
-constexpr int kMaxRounds = (kMaxNb * 9 + 31) / 32;   // 32-entry rounds of a node's row block
 
 __global__ void k_prep(int64_t nc, const double *__restrict__ rho, SimpParams sp, float2 *__restrict__ Edf,
                        int64_t ndof, const double *__restrict__ u, float2 *__restrict__ udf)
@@ -52,200 +52,275 @@ __global__ void k_prep(int64_t nc, const double *__restrict__ rho, SimpParams sp
         }
 }
 
-// Plain-FP64 rows of one node (a modulus outside the float-pair range).
-template <int D, typename KT>
-__device__ __noinline__ void gather_node_fp64(int lane, int nb, int ldof, int deg, int32_t q0, int32_t q1,
-                                              const int32_t *__restrict__ inc, const uint16_t *__restrict__ pos,
-                                              const KT *__restrict__ K, int64_t kstride,
-                                              const double *__restrict__ rho, SimpParams sp, double *out)
+// Arguments of the node-group gather.
+template <typename KT>
+struct GatherArgs {
+    int64_t nn;
+    int nb, max_deg, nck;
+    const int64_t *__restrict__ node_off;
+    const int32_t *__restrict__ inc_ptr;
+    const int32_t *__restrict__ inc_e;
+    const uint8_t *__restrict__ inc_a;
+    const uint16_t *__restrict__ pos;
+    const int32_t *__restrict__ cell_node;
+    const int32_t *__restrict__ indices;
+    const KT *__restrict__ K;
+    int64_t kstride;
+    const float2 *__restrict__ Edf;
+    const float2 *__restrict__ udf;
+    const double *__restrict__ rho;
+    SimpParams sp;
+    double *__restrict__ vals;
+    double *__restrict__ part;
+};
+
+// E * k as an unnormalised pair: float pairs (FP64 element matrices) or a
+// float (FP32 element matrices, one rounding-free TwoProd and one FMA).
+__device__ __forceinline__ df mul_k(df E, float2 k) { return df_mul_raw(E, df{k.x, k.y}); }
+__device__ __forceinline__ df mul_kf(df E, float k)
 {
-    for (int t = lane; t < D * D * deg; t += 32) out[t] = 0.0;
-    __syncwarp();
-    for (int32_t q = q0; q < q1; q++) {
-        const int32_t ea = inc[q];
-        const int64_t e = ea / nb;
-        const int a = ea - (int)e * nb;
-        const double E = simp_E(sp, rho[e]);
-        const KT *Ke = K + e * kstride;
-        for (int t = lane; t < nb * D * D; t += 32) {
-            const int b = t / (D * D), i = (t / D) % D, j = t % D;
-            out[i * (D * deg) + D * pos[(int64_t)q * nb + b] + j] += E * KLoad<KT>::get64(Ke + (D * a + i) * ldof + D * b + j);
-        }
-        __syncwarp();
-    }
+    const float p = __fmul_rn(E.h, k);
+    return df{p, __fmaf_rn(E.l, k, __fmaf_rn(E.h, k, -p))};
+}
+template <typename KT> struct KEntry;
+template <> struct KEntry<float2> {
+    using T = float2;
+    static __device__ __forceinline__ T load(const float2 *p) { return __ldcs(p); }
+    static __device__ __forceinline__ T zero() { return make_float2(0.f, 0.f); }
+    static __device__ __forceinline__ df mul(df a, T k) { return mul_k(a, k); }
+};
+template <> struct KEntry<float> {
+    using T = float;
+    static __device__ __forceinline__ T load(const float *p) { return __ldcs(p); }
+    static __device__ __forceinline__ T zero() { return 0.f; }
+    static __device__ __forceinline__ df mul(df a, T k) { return mul_kf(a, k); }
+};
+
+// Accumulate x into the unnormalised pair (s, c).
+__device__ __forceinline__ void acc_add(float &s, float &c, df x)
+{
+    float t, err;
+    two_sum(s, x.h, t, err);
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(x.l, err));
 }
 
-template <int D, typename KT, bool SENS>
-__global__ void __launch_bounds__(kGW * 32)
-k_gather_fused(int64_t nn, int nb, int max_deg, const int64_t *__restrict__ node_off,
-               const int32_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc,
-               const int32_t *__restrict__ inc_e, const uint8_t *__restrict__ inc_a,
-               const uint16_t *__restrict__ pos, const int32_t *__restrict__ cell_node,
-               const KT *__restrict__ K, int64_t kstride, const float2 *__restrict__ Edf,
-               const float2 *__restrict__ udf, const double *__restrict__ rho, SimpParams sp,
-               double *__restrict__ vals, double *__restrict__ part)
+// Plain-FP64 redo of one node by the whole warp (a modulus outside the
+// float-pair range): rows into acc (as doubles), and the node's partials.
+template <int D, typename KT>
+__device__ __noinline__ void gather_node_fp64_warp(const GatherArgs<KT> &A, bool sens, int lane, int64_t n, int deg,
+                                                   int32_t q0, int32_t cnt, double *acc)
 {
-    extern __shared__ float smem_f[];
-    __shared__ int tab_koff[kMaxRounds * 32], tab_bij[kMaxRounds * 32];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ldof = D * nb;
+    const int nb = A.nb, ldof = D * nb, rowlen = D * deg;
     const int per = nb * D * D;
-    const int rounds = (per + 31) / 32;
-    // entry t of a node's row block: (b, i, j) = (t / d^2, (t / d) % d, t % d)
-    for (int t = threadIdx.x; t < rounds * 32; t += blockDim.x) {
-        const int tt = t < per ? t : 0;
-        const int b = tt / (D * D), i = (tt / D) % D, j = tt % D;
-        tab_koff[t] = i * ldof + D * b + j;
-        tab_bij[t] = b | (i << 8) | (j << 16);
-    }
-    __syncthreads();
-    float *acc_h = smem_f + (size_t)warp * 2 * D * D * max_deg;
-    float *acc_l = acc_h + D * D * max_deg;
-    double *acc_d = reinterpret_cast<double *>(acc_h);   // FP64 route reuses the same space
-    for (int64_t n = (int64_t)blockIdx.x * kGW + warp; n < nn; n += (int64_t)gridDim.x * kGW) {
-        const int64_t off = node_off[n];
-        const int deg = (int)(node_off[n + 1] - off);
-        const int blk = D * D * deg;
-        const int32_t q0 = inc_ptr[n], q1 = inc_ptr[n + 1];
-        double *out = vals + (int64_t)D * D * off;
-        // any incident modulus outside the float-pair range?
-        bool bad = false;
-        for (int32_t q = q0 + lane; q < q1; q += 32) bad |= isnan(Edf[inc[q] / nb].y);
-        if (__any_sync(kFull, bad)) {
-            if (vals) {
-                gather_node_fp64<D, KT>(lane, nb, ldof, deg, q0, q1, inc, pos, K, kstride, rho, sp, acc_d);
-                __syncwarp();
-                for (int t = lane; t < blk; t += 32) __stcs(out + t, acc_d[t]);
-                __syncwarp();
-            }
-            if (SENS) {
-                for (int32_t q = q0; q < q1; q++) {
-                    const int32_t ea = inc[q];
-                    const int64_t e = ea / nb;
-                    const int a = ea - (int)e * nb;
-                    const KT *Ke = K + e * kstride;
-                    double s = 0.0;
-                    for (int t = lane; t < nb * D * D; t += 32) {
-                        const int b = t / (D * D), i = (t / D) % D, j = t % D;
-                        const float2 ua = udf[(int64_t)D * n + i], ub = udf[(int64_t)D * cell_node[e * nb + b] + j];
-                        s += ((double)ua.x + ua.y) * KLoad<KT>::get64(Ke + (D * a + i) * ldof + D * b + j) *
-                             ((double)ub.x + ub.y);
-                    }
-                    s = warp_sum(s);
-                    if (lane == 0) part[ea] = s;
-                }
-            }
-            continue;
-        }
-        if (vals) {
-            for (int t = lane; t < blk; t += 32) {
-                acc_h[t] = 0.f;
-                acc_l[t] = 0.f;
+    for (int t = lane; t < D * rowlen; t += 32) acc[t] = 0.0;
+    __syncwarp();
+    for (int32_t q = q0; q < q0 + cnt; q++) {
+        const int64_t e = A.inc_e[q];
+        const int a = A.inc_a[q];
+        const double E = simp_E(A.sp, A.rho[e]);
+        const KT *Ke = A.K + e * A.kstride;
+        double s = 0.0;
+        for (int t = lane; t < per; t += 32) {
+            const int b = t / (D * D), i = (t / D) % D, j = t % D;
+            const double k = KLoad<KT>::get64(Ke + (D * a + i) * ldof + D * b + j);
+            if (A.vals) acc[i * rowlen + D * A.pos[(int64_t)q * nb + b] + j] += E * k;
+            if (sens) {
+                const float2 ua = A.udf[(int64_t)D * n + i], ub = A.udf[(int64_t)D * A.cell_node[e * nb + b] + j];
+                s += ((double)ua.x + ua.y) * k * ((double)ub.x + ub.y);
             }
         }
         __syncwarp();
-        // Flattened (incidence, round) items: round r of incidence q covers the
-        // entries t = 32 r + lane of the node's row block of K_e (offsets from
-        // the per-block table).  The next item's loads are issued before the
-        // current item is accumulated.
-        const int n_items = (q1 - q0) * rounds;
-        struct Inc {
-            const KT *kb;
-            const int32_t *cn;
-            const uint16_t *ps;
+        if (sens) {
+            s = warp_sum(s);
+            if (lane == 0) A.part[e * nb + a] = s;
+        }
+    }
+    __syncwarp();
+    if (A.vals) {
+        double *out = A.vals + (int64_t)D * D * A.node_off[n];
+        for (int t = lane; t < D * rowlen; t += 32) __stcs(out + t, acc[t]);
+    }
+    __syncwarp();
+}
+
+// General path, any mesh.  A warp serves NPW nodes at once, GL = 32 / NPW
+// lanes per node.  Lane ll of a group owns row i = ll / LPR of the node's d
+// rows and the columns c, c + LPR, c + 2 LPR, ... (c = ll % LPR) of each
+// incident cell's row block K_e^0[(a, i), :], so its entries of one cell are
+// R rounds apart, and in each round the lanes of a row read consecutive
+// entries.  Entry (b, j) of cell e lands in column block pos(e, b) of the
+// node's rows, i.e. at offset s = d pos + j of row i; the displacement it
+// meets, u_(b,j), is entry s of the node's neighbour displacements, staged
+// in shared memory once per node from the CSR column indices.  For every
+// incident cell (ascending) a lane adds E_e k into the node's row
+// accumulators (float pairs in shared memory; no two lanes of a group hold
+// the same slot within one cell, so there is no race and the order is fixed)
+// and, with u, sums k u_(b,j) for its row; the group then forms the cell's
+// partial  sum_i u_(a,i) (K_e u_e)_(a,i)  by a fixed-order butterfly.  The
+// next cell's entries and positions are loaded while the current one is
+// accumulated (its index two cells ahead).  Rows longer than R LPR columns
+// take nck chunks (CH).
+template <int D, typename KT, bool SENS, int NPW, int R, bool CH>
+__global__ void __launch_bounds__(kGW * 32, 2) k_gather_nodes(const GatherArgs<KT> A)
+{
+    using KE = KEntry<KT>;
+    using KV = typename KE::T;
+    constexpr int GL = 32 / NPW;
+    constexpr int LPR = GL / D;
+    extern __shared__ float2 smem_s[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    const int g = lane / GL, ll = lane % GL;
+    const int irow = ll / LPR, c = ll - irow * LPR;
+    const bool act = irow < D;
+    const int i = act ? irow : 0;
+    const int nb = A.nb, ldof = D * nb, nck = CH ? A.nck : 1;
+    const int gslot = warp * NPW + g;
+    const int acc_len = D * D * A.max_deg, un_len = SENS ? D * A.max_deg : 0;
+    float2 *acc = smem_s + (size_t)gslot * acc_len;
+    float2 *un = smem_s + (size_t)wpb * NPW * acc_len + (size_t)gslot * un_len;
+    const int64_t step = (int64_t)gridDim.x * wpb * NPW;
+    for (int64_t n0 = ((int64_t)blockIdx.x * wpb + warp) * NPW; n0 < A.nn; n0 += step) {
+        const int64_t n = n0 + g;
+        const bool has = n < A.nn;
+        int64_t off = 0;
+        int deg = 0;
+        int32_t q0 = 0, cnt = 0;
+        if (has) {
+            off = A.node_off[n];
+            deg = (int)(A.node_off[n + 1] - off);
+            q0 = A.inc_ptr[n];
+            cnt = A.inc_ptr[n + 1] - q0;
+        }
+        const int rowlen = D * deg, blk = D * rowlen;
+        if (A.vals)
+            for (int t = ll; t < blk; t += GL) acc[t] = make_float2(0.f, 0.f);
+        df uni = df{0.f, 0.f};
+        if (SENS) {
+            // displacements of the node's neighbour dofs, in CSR column order
+            const int32_t *cols = A.indices + (int64_t)D * D * off;
+            for (int t = ll; t < rowlen; t += GL) un[t] = A.udf[cols[t]];
+            if (has && act) {
+                const float2 v = A.udf[(int64_t)D * n + i];
+                uni = df{v.x, v.y};
+            }
+        }
+        const int items = cnt * nck;
+        int imax = items;
+#pragma unroll
+        for (int o = GL; o < 32; o <<= 1) imax = max(imax, __shfl_xor_sync(kFull, imax, o));
+        __syncwarp();
+
+        // item = (incidence t, chunk kc): the lane's R entries of it
+        struct Item {
+            KV k[R];
+            int p[R];
             float2 E;
             int32_t ea;
         };
-        auto fetch_inc = [&](int32_t q) {
-            Inc c;
-            const int32_t e = inc_e[q];
-            const int a = inc_a[q];
-            c.ea = e * nb + a;
-            c.kb = K + (int64_t)e * kstride + (int64_t)(D * a) * ldof;
-            c.cn = cell_node + (int64_t)e * nb;
-            c.ps = pos + (int64_t)q * nb;
-            c.E = Edf[e];
-            return c;
-        };
-        struct Item {
-            float2 k, ub, ua;
-            int slot;
-        };
-        auto fetch = [&](const Inc &c, int r) {
-            Item it;
-            const int t = 32 * r + lane;
-            const int koff = tab_koff[t], bij = tab_bij[t];
-            const int bb = bij & 0xff, ii = (bij >> 8) & 0xff, jj = bij >> 16;
-            const bool live = t < per;
-            it.k = live ? KLoad<KT>::raw(c.kb + koff) : make_float2(0.f, 0.f);
-            it.slot = (vals && live) ? ii * (D * deg) + D * c.ps[bb] + jj : 0;
-            it.ub = (SENS && live) ? udf[(int64_t)D * c.cn[bb] + jj] : make_float2(0.f, 0.f);
-            it.ua = (SENS && live) ? udf[(int64_t)D * n + ii] : make_float2(0.f, 0.f);
-            return it;
-        };
-        float S = 0.f, C = 0.f;     // this lane's share of the current cell's node partial
-        int32_t q = q0;
-        int r = 0;
-        Inc ccur = n_items > 0 ? fetch_inc(q0) : Inc{};
-        Item cur = n_items > 0 ? fetch(ccur, 0) : Item{};
-        Inc cnxt = ccur;
-        for (int item = 0; item < n_items; item++) {
-            int32_t qn = q;
-            int rn = r + 1;
-            if (rn == rounds) {
-                rn = 0;
-                qn++;
-                if (qn < q1) cnxt = fetch_inc(qn);
-            }
-            Item nxt;
-            if (item + 1 < n_items) nxt = fetch(cnxt, rn);
-            if (32 * r + lane < per) {
-                const df kv = df{cur.k.x, cur.k.y};
-                if (vals) {
-                    const df pr = df_mul_raw(df{ccur.E.x, ccur.E.y}, kv);
-                    float s, err;
-                    two_sum(acc_h[cur.slot], pr.h, s, err);
-                    acc_h[cur.slot] = s;
-                    acc_l[cur.slot] = __fadd_rn(acc_l[cur.slot], __fadd_rn(pr.l, err));
-                }
-                if (SENS) {
-                    const df t1 = df_mul_raw(df_mul_raw(kv, df{cur.ub.x, cur.ub.y}), df{cur.ua.x, cur.ua.y});
-                    float s, err;
-                    two_sum(S, t1.h, s, err);
-                    S = s;
-                    C = __fadd_rn(C, __fadd_rn(t1.l, err));
-                }
-            }
-            if (rn == 0) {   // last round of this cell
-                __syncwarp();
-                if (SENS) {
-                    // fixed-order butterfly of the lanes' (S, C) pairs
+        auto fetch = [&](int it, int32_t e, int a, Item &d) {
+            const bool on = it < items;
+            const int t = !on ? 0 : (CH ? it / nck : it), kc = (!on || !CH) ? 0 : it - t * nck;
+            d.E = on ? A.Edf[e] : make_float2(0.f, 0.f);
+            d.ea = e * nb + a;
+            const KT *kr = A.K + (int64_t)e * A.kstride + (int64_t)(D * a + i) * ldof + c + LPR * R * kc;
+            const uint16_t *ps = A.pos + (int64_t)(q0 + t) * nb;
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        const float So = __shfl_xor_sync(kFull, S, o), Co = __shfl_xor_sync(kFull, C, o);
-                        float s, err;
-                        two_sum(S, So, s, err);
-                        S = s;
-                        C = __fadd_rn(__fadd_rn(C, Co), err);
-                    }
-                    if (lane == 0) {
-                        float h, l;
-                        two_sum(S, C, h, l);
-                        part[ccur.ea] = df_to_double(h, l);
-                    }
-                    S = 0.f;
-                    C = 0.f;
-                }
-                ccur = cnxt;
+            for (int r = 0; r < R; r++) {
+                const int col = c + LPR * (R * kc + r);
+                const bool lv = on && act && col < ldof;
+                const int b = col / D, j = col - D * b;
+                d.k[r] = lv ? KE::load(kr + LPR * r) : KE::zero();
+                d.p[r] = lv ? D * ps[b] + j : -1;
             }
-            q = qn;
-            r = rn;
-            cur = nxt;
+        };
+        auto fetch_ea = [&](int it, int32_t &e, int &a) {
+            const int t = CH ? it / nck : it;
+            e = it < items ? A.inc_e[q0 + t] : 0;
+            a = it < items ? A.inc_a[q0 + t] : 0;
+        };
+        int32_t e1, e2;
+        int a1, a2;
+        fetch_ea(0, e1, a1);
+        fetch_ea(1, e2, a2);
+        Item nxt;
+        fetch(0, e1, a1, nxt);
+        bool bad = false;
+        float S = 0.f, C = 0.f;
+        for (int it = 0; it < imax; it++) {
+            const Item cur = nxt;
+            e1 = e2;
+            a1 = a2;
+            fetch_ea(it + 2, e2, a2);
+            fetch(it + 1, e1, a1, nxt);
+            if (it < items) {
+                bad |= isnan(cur.E.y);
+                const df E = df{cur.E.x, cur.E.y};
+                float2 *arow = acc + i * rowlen;
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    const int s = cur.p[r];
+                    if (s < 0) continue;
+                    if (A.vals) {
+                        float2 v = arow[s];
+                        acc_add(v.x, v.y, KE::mul(E, cur.k[r]));
+                        arow[s] = v;
+                    }
+                    if (SENS) {
+                        const float2 ub = un[s];
+                        acc_add(S, C, KE::mul(df{ub.x, ub.y}, cur.k[r]));
+                    }
+                }
+            }
+            __syncwarp();
+            if (SENS && (!CH || it % nck == nck - 1)) {
+                // the group's fixed-order butterfly of  u_(a,i) * (lane's share of (K_e u_e)_(a,i))
+                float Sp, Cp;
+                {
+                    float h, l;
+                    two_sum(S, C, h, l);
+                    const df v = df_mul_raw(uni, df{h, l});
+                    Sp = v.h;
+                    Cp = v.l;
+                }
+#pragma unroll
+                for (int o = GL / 2; o > 0; o >>= 1) {
+                    const float So = __shfl_xor_sync(kFull, Sp, o), Co = __shfl_xor_sync(kFull, Cp, o);
+                    float s, err;
+                    two_sum(Sp, So, s, err);
+                    Sp = s;
+                    Cp = __fadd_rn(__fadd_rn(Cp, Co), err);
+                }
+                if (ll == 0 && it < items) {
+                    float h, l;
+                    two_sum(Sp, Cp, h, l);
+                    A.part[cur.ea] = df_to_double(h, l);
+                }
+                S = 0.f;
+                C = 0.f;
+            }
         }
-        if (vals) {
-            for (int t = lane; t < blk; t += 32) {
+        // a group whose node met an out-of-range modulus is redone in FP64 by the whole warp
+        const unsigned badm = __ballot_sync(kFull, bad);
+        constexpr unsigned kGroup = GL == 32 ? kFull : ((1u << GL) - 1u);
+        if (badm) {
+#pragma unroll 1
+            for (int gg = 0; gg < NPW; gg++) {
+                if (!(badm & (kGroup << (gg * GL)))) continue;
+                const int src = gg * GL;
+                const int64_t ng = __shfl_sync(kFull, n, src);
+                const int dg = __shfl_sync(kFull, deg, src);
+                const int32_t qg = __shfl_sync(kFull, q0, src), cg = __shfl_sync(kFull, cnt, src);
+                gather_node_fp64_warp<D, KT>(A, SENS, lane, ng, dg, qg, cg,
+                                             reinterpret_cast<double *>(smem_s + (size_t)(warp * NPW + gg) * acc_len));
+            }
+        }
+        if (A.vals && !(badm & (kGroup << (g * GL)))) {
+            double *out = A.vals + (int64_t)D * D * off;
+            for (int t = ll; t < blk; t += GL) {
+                const float2 v = acc[t];
                 float h, l;
-                two_sum(acc_h[t], acc_l[t], h, l);
+                two_sum(v.x, v.y, h, l);
                 __stcs(out + t, df_to_double(h, l));
             }
         }
@@ -253,154 +328,179 @@ k_gather_fused(int64_t nn, int nb, int max_deg, const int64_t *__restrict__ node
     }
 }
 
-// Same computation with the R rounds of a node's row block unrolled: each
-// lane's entry offsets live in registers and the next incidence's entries are
-// loaded into register arrays while the current one is accumulated.
-template <int D, typename KT, bool SENS, int R>
-__global__ void __launch_bounds__(kGW * 32)
-k_gather_unrolled(int64_t nn, int nb, int max_deg, const int64_t *__restrict__ node_off,
-                  const int32_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc,
-                  const int32_t *__restrict__ inc_e, const uint8_t *__restrict__ inc_a,
-                  const uint16_t *__restrict__ pos, const int32_t *__restrict__ cell_node,
-                  const KT *__restrict__ K, int64_t kstride, const float2 *__restrict__ Edf,
-                  const float2 *__restrict__ udf, const double *__restrict__ rho, SimpParams sp,
-                  double *__restrict__ vals, double *__restrict__ part)
+// The same gather for the cell types whose row blocks tile exactly into
+// the group's lanes (d nb = LPR R): P2 tetrahedra and P3 triangles.  Every
+// lane-round constant is fixed at compile time or per lane; the positions of
+// a cell's nodes arrive once per cell (lane b of the group loads pos(e, b))
+// and reach the lanes that need them by shuffles; the item loop is unrolled
+// by two so the prefetched item never has to be copied.
+template <int D, int NB, typename KT, bool SENS, int NPW, int R>
+__global__ void __launch_bounds__(kGW * 32, 2) k_gather_rows(const GatherArgs<KT> A)
 {
-    extern __shared__ float smem_f[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ldof = D * nb;
-    const int per = nb * D * D;
-    int koff[R], bq[R], iq[R], jq[R];
-    bool live[R];
+    using KE = KEntry<KT>;
+    using KV = typename KE::T;
+    constexpr int GL = 32 / NPW, LPR = GL / D, LDOF = D * NB, NPOS = (NB + GL - 1) / GL;
+    static_assert(LPR * R == LDOF, "the rounds must tile the row block");
+    static_assert(NPOS <= 2, "at most two positions per lane");
+    extern __shared__ float2 smem_s[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    const int g = lane / GL, ll = lane % GL;
+    const int irow = ll / LPR, c = ll - irow * LPR;
+    const bool act = irow < D;
+    const int i = act ? irow : 0;
+    int srcl[R], jr[R];
+    bool hi[R];
 #pragma unroll
     for (int r = 0; r < R; r++) {
-        const int t = 32 * r + lane;
-        live[r] = t < per;
-        const int tt = live[r] ? t : 0;
-        bq[r] = tt / (D * D);
-        iq[r] = (tt / D) % D;
-        jq[r] = tt % D;
-        koff[r] = iq[r] * ldof + D * bq[r] + jq[r];
+        const int col = c + LPR * r, b = col / D;
+        jr[r] = col - D * b;
+        srcl[r] = g * GL + b % GL;
+        hi[r] = b >= GL;
     }
-    float *acc_h = smem_f + (size_t)warp * 2 * D * D * max_deg;
-    float *acc_l = acc_h + D * D * max_deg;
-    double *acc_d = reinterpret_cast<double *>(acc_h);
-    for (int64_t n = (int64_t)blockIdx.x * kGW + warp; n < nn; n += (int64_t)gridDim.x * kGW) {
-        const int64_t off = node_off[n];
-        const int deg = (int)(node_off[n + 1] - off);
-        const int blk = D * D * deg;
-        const int32_t q0 = inc_ptr[n], q1 = inc_ptr[n + 1];
-        double *out = vals + (int64_t)D * D * off;
-        bool bad = false;
-        for (int32_t q = q0 + lane; q < q1; q += 32) bad |= isnan(Edf[inc_e[q]].y);
-        if (__any_sync(kFull, bad)) {
-            if (vals) {
-                gather_node_fp64<D, KT>(lane, nb, ldof, deg, q0, q1, inc, pos, K, kstride, rho, sp, acc_d);
-                __syncwarp();
-                for (int t = lane; t < blk; t += 32) __stcs(out + t, acc_d[t]);
-                __syncwarp();
-            }
-            if (SENS) {
-                for (int32_t q = q0; q < q1; q++) {
-                    const int64_t e = inc_e[q];
-                    const int a = inc_a[q];
-                    const KT *Ke = K + e * kstride;
-                    double s = 0.0;
-                    for (int t = lane; t < per; t += 32) {
-                        const int b = t / (D * D), i = (t / D) % D, j = t % D;
-                        const float2 ua = udf[(int64_t)D * n + i], ub = udf[(int64_t)D * cell_node[e * nb + b] + j];
-                        s += ((double)ua.x + ua.y) * KLoad<KT>::get64(Ke + (D * a + i) * ldof + D * b + j) *
-                             ((double)ub.x + ub.y);
-                    }
-                    s = warp_sum(s);
-                    if (lane == 0) part[e * nb + a] = s;
-                }
-            }
-            continue;
+    const int gslot = warp * NPW + g;
+    const int acc_len = D * D * A.max_deg, un_len = SENS ? D * A.max_deg : 0;
+    float2 *acc = smem_s + (size_t)gslot * acc_len;
+    float2 *un = smem_s + (size_t)wpb * NPW * acc_len + (size_t)gslot * un_len;
+    const int64_t step = (int64_t)gridDim.x * wpb * NPW;
+    for (int64_t n0 = ((int64_t)blockIdx.x * wpb + warp) * NPW; n0 < A.nn; n0 += step) {
+        const int64_t n = n0 + g;
+        const bool has = n < A.nn;
+        int64_t off = 0;
+        int deg = 0;
+        int32_t q0 = 0, cnt = 0;
+        if (has) {
+            off = A.node_off[n];
+            deg = (int)(A.node_off[n + 1] - off);
+            q0 = A.inc_ptr[n];
+            cnt = A.inc_ptr[n + 1] - q0;
         }
-        if (vals)
-            for (int t = lane; t < blk; t += 32) {
-                acc_h[t] = 0.f;
-                acc_l[t] = 0.f;
+        const int rowlen = D * deg, blk = D * rowlen;
+        if (A.vals)
+            for (int t = ll; t < blk; t += GL) acc[t] = make_float2(0.f, 0.f);
+        df uni = df{0.f, 0.f};
+        if (SENS) {
+            const int32_t *cols = A.indices + (int64_t)D * D * off;
+            for (int t = ll; t < rowlen; t += GL) un[t] = A.udf[cols[t]];
+            if (has && act) {
+                const float2 v = A.udf[(int64_t)D * n + i];
+                uni = df{v.x, v.y};
             }
-        float2 ua[R];
-        if (SENS)
+        }
+        int imax = cnt;
 #pragma unroll
-            for (int r = 0; r < R; r++) ua[r] = udf[(int64_t)D * n + iq[r]];
+        for (int o = GL; o < 32; o <<= 1) imax = max(imax, __shfl_xor_sync(kFull, imax, o));
         __syncwarp();
-        // prefetched next incidence
-        float2 kN[R], ubN[R], EN = make_float2(0.f, 0.f);
-        int slotN[R];
-        int32_t eaN = 0;
-        auto load = [&](int32_t q) {
-            const int32_t e = inc_e[q];
-            const int a = inc_a[q];
-            eaN = e * nb + a;
-            EN = Edf[e];
-            const KT *kb = K + (int64_t)e * kstride + (int64_t)(D * a) * ldof;
-            const int32_t *cn = cell_node + (int64_t)e * nb;
-            const uint16_t *ps = pos + (int64_t)q * nb;
-#pragma unroll
-            for (int r = 0; r < R; r++) {
-                kN[r] = live[r] ? KLoad<KT>::raw(kb + koff[r]) : make_float2(0.f, 0.f);
-                if (vals) slotN[r] = live[r] ? iq[r] * (D * deg) + D * ps[bq[r]] + jq[r] : 0;
-                if (SENS) ubN[r] = live[r] ? udf[(int64_t)D * cn[bq[r]] + jq[r]] : make_float2(0.f, 0.f);
-            }
+
+        struct Item {
+            KV k[R];
+            int pv[NPOS];
+            float2 E;
+            int32_t ea;
         };
-        if (q0 < q1) load(q0);
-        for (int32_t q = q0; q < q1; q++) {
-            float2 kc[R], ubc[R];
-            int slotc[R];
+        auto fetch = [&](int it, int32_t e, int a, Item &d) {
+            const bool on = it < cnt;
+            d.E = on ? A.Edf[e] : make_float2(0.f, 0.f);
+            d.ea = e * NB + a;
+            const KT *kr = A.K + (int64_t)e * A.kstride + (int64_t)(D * a + i) * LDOF + c;
+#pragma unroll
+            for (int r = 0; r < R; r++) d.k[r] = (on && act) ? KE::load(kr + LPR * r) : KE::zero();
+            const uint16_t *ps = A.pos + (int64_t)(q0 + it) * NB;
+#pragma unroll
+            for (int q = 0; q < NPOS; q++) d.pv[q] = (on && ll + q * GL < NB) ? (int)ps[ll + q * GL] : 0;
+        };
+        int32_t e1 = 0, e2 = 0;
+        int a1 = 0, a2 = 0;
+        auto fetch_ea = [&](int it, int32_t &e, int &a) {
+            e = it < cnt ? A.inc_e[q0 + it] : 0;
+            a = it < cnt ? A.inc_a[q0 + it] : 0;
+        };
+        bool bad = false;
+        auto body = [&](const Item &cur, Item &nxt, int it) {
+            e1 = e2;
+            a1 = a2;
+            fetch_ea(it + 2, e2, a2);
+            fetch(it + 1, e1, a1, nxt);
+            int s[R];
 #pragma unroll
             for (int r = 0; r < R; r++) {
-                kc[r] = kN[r];
-                ubc[r] = ubN[r];
-                slotc[r] = slotN[r];
-            }
-            const float2 Ec = EN;
-            const int32_t eac = eaN;
-            if (q + 1 < q1) load(q + 1);
-            float S = 0.f, C = 0.f;
-#pragma unroll
-            for (int r = 0; r < R; r++) {
-                if (!live[r]) continue;
-                const df kv = df{kc[r].x, kc[r].y};
-                if (vals) {
-                    const df pr = df_mul_raw(df{Ec.x, Ec.y}, kv);
-                    float s2, err;
-                    two_sum(acc_h[slotc[r]], pr.h, s2, err);
-                    acc_h[slotc[r]] = s2;
-                    acc_l[slotc[r]] = __fadd_rn(acc_l[slotc[r]], __fadd_rn(pr.l, err));
+                int pb = __shfl_sync(kFull, cur.pv[0], srcl[r]);
+                if (NPOS == 2) {
+                    const int p1 = __shfl_sync(kFull, cur.pv[NPOS - 1], srcl[r]);
+                    pb = hi[r] ? p1 : pb;
                 }
-                if (SENS) {
-                    const df t1 = df_mul_raw(df_mul_raw(kv, df{ubc[r].x, ubc[r].y}), df{ua[r].x, ua[r].y});
-                    float s2, err;
-                    two_sum(S, t1.h, s2, err);
-                    S = s2;
-                    C = __fadd_rn(C, __fadd_rn(t1.l, err));
+                s[r] = D * pb + jr[r];
+            }
+            float S = 0.f, C = 0.f;
+            if (it < cnt && act) {
+                bad |= isnan(cur.E.y);
+                const df E = df{cur.E.x, cur.E.y};
+                float2 *arow = acc + i * rowlen;
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    if (A.vals) {
+                        float2 v = arow[s[r]];
+                        acc_add(v.x, v.y, KE::mul(E, cur.k[r]));
+                        arow[s[r]] = v;
+                    }
+                    if (SENS) {
+                        const float2 ub = un[s[r]];
+                        acc_add(S, C, KE::mul(df{ub.x, ub.y}, cur.k[r]));
+                    }
                 }
             }
             __syncwarp();
             if (SENS) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const float So = __shfl_xor_sync(kFull, S, o), Co = __shfl_xor_sync(kFull, C, o);
-                    float s2, err;
-                    two_sum(S, So, s2, err);
-                    S = s2;
-                    C = __fadd_rn(__fadd_rn(C, Co), err);
-                }
-                if (lane == 0) {
+                float Sp, Cp;
+                {
                     float h, l;
                     two_sum(S, C, h, l);
-                    part[eac] = df_to_double(h, l);
+                    const df v = df_mul_raw(uni, df{h, l});
+                    Sp = v.h;
+                    Cp = v.l;
+                }
+#pragma unroll
+                for (int o = GL / 2; o > 0; o >>= 1) {
+                    const float So = __shfl_xor_sync(kFull, Sp, o), Co = __shfl_xor_sync(kFull, Cp, o);
+                    float s2, err;
+                    two_sum(Sp, So, s2, err);
+                    Sp = s2;
+                    Cp = __fadd_rn(__fadd_rn(Cp, Co), err);
+                }
+                if (ll == 0 && it < cnt) {
+                    float h, l;
+                    two_sum(Sp, Cp, h, l);
+                    A.part[cur.ea] = df_to_double(h, l);
                 }
             }
+        };
+        fetch_ea(0, e1, a1);
+        fetch_ea(1, e2, a2);
+        Item I0, I1;
+        fetch(0, e1, a1, I0);
+        for (int it = 0; it < imax; it += 2) {
+            body(I0, I1, it);
+            if (it + 1 < imax) body(I1, I0, it + 1);
         }
-        if (vals) {
-            for (int t = lane; t < blk; t += 32) {
+        const unsigned badm = __ballot_sync(kFull, bad);
+        constexpr unsigned kGroup = GL == 32 ? kFull : ((1u << GL) - 1u);
+        if (badm) {
+#pragma unroll 1
+            for (int gg = 0; gg < NPW; gg++) {
+                if (!(badm & (kGroup << (gg * GL)))) continue;
+                const int src = gg * GL;
+                const int64_t ng = __shfl_sync(kFull, n, src);
+                const int dg = __shfl_sync(kFull, deg, src);
+                const int32_t qg = __shfl_sync(kFull, q0, src), cg = __shfl_sync(kFull, cnt, src);
+                gather_node_fp64_warp<D, KT>(A, SENS, lane, ng, dg, qg, cg,
+                                             reinterpret_cast<double *>(smem_s + (size_t)(warp * NPW + gg) * acc_len));
+            }
+        }
+        if (A.vals && !(badm & (kGroup << (g * GL)))) {
+            double *out = A.vals + (int64_t)D * D * off;
+            for (int t = ll; t < blk; t += GL) {
+                const float2 v = acc[t];
                 float h, l;
-                two_sum(acc_h[t], acc_l[t], h, l);
+                two_sum(v.x, v.y, h, l);
                 __stcs(out + t, df_to_double(h, l));
             }
         }
@@ -438,31 +538,63 @@ __global__ void k_sens_finalize(int64_t nc, int nb, const double *__restrict__ p
 
 int ggrid(int64_t items, int per) { return (int)std::max<int64_t>(1, std::min<int64_t>((items + per - 1) / per, 152 * 16)); }
 
+// Lane layout per mesh type: (nodes per warp, lanes per row, rounds per
+// chunk).  P2 tetrahedra (30 columns): 2 nodes x 3 rows x 5 lanes, 6 rounds;
+// P3 triangles (20 columns): 4 nodes x 2 rows x 4 lanes, 5 rounds; anything
+// else one node per warp, 10 (3D) or 16 (2D) lanes per row, chunks of 4 rounds.
+template <int D, typename KT, int NPW, typename Kern>
+cudaError_t gather_launch(const soptx_mesh_s &m, const double *rho, double *vals, bool sens, int R, Kern kern,
+                          cudaStream_t st)
+{
+    const auto &h = m.h;
+    GatherArgs<KT> A;
+    A.nn = h.nn;
+    A.nb = h.nb;
+    A.max_deg = h.max_deg;
+    const int lpr = 32 / NPW / D;
+    const int rounds = (h.ldof + lpr - 1) / lpr;
+    A.nck = (rounds + R - 1) / R;
+    A.node_off = m.d.node_off;
+    A.inc_ptr = m.d.inc_ptr;
+    A.inc_e = m.d.inc_e;
+    A.inc_a = m.d.inc_a;
+    A.pos = m.d.pos;
+    A.cell_node = m.d.cell_node;
+    A.indices = m.d.indices;
+    A.K = (const KT *)m.d.K;
+    A.kstride = m.path == SOPTX_PATH_CACHED ? (int64_t)h.ldof * h.ldof : 0;
+    A.Edf = m.d.Edf;
+    A.udf = m.d.udf;
+    A.rho = rho;
+    A.sp = simp_params(m.mat);
+    A.vals = vals;
+    A.part = sens ? m.d.part : nullptr;
+    const size_t per_warp = (size_t)NPW * (D * D + (sens ? D : 0)) * h.max_deg * sizeof(float2);
+    const int wpb = (int)std::max<size_t>(1, std::min<size_t>(kGW, (size_t)(200 * 1024) / per_warp));
+    const size_t smem = per_warp * wpb;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    const int64_t groups = (h.nn + NPW - 1) / NPW;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((groups + wpb - 1) / wpb, 152 * 16));
+    kern<<<grid, wpb * 32, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
 template <int D, typename KT>
 cudaError_t gather_t(const soptx_mesh_s &m, const double *rho, double *vals, bool sens, cudaStream_t st)
 {
-    const auto &h = m.h;
-    const size_t sm = (size_t)kGW * 2 * D * D * h.max_deg * sizeof(float);
-    const int rounds = (h.nb * D * D + 31) / 32;
-    auto kern = sens ? k_gather_fused<D, KT, true> : k_gather_fused<D, KT, false>;
-#define SOPTX_PICK(RR)                                                                                     \
-    if (rounds == RR) kern = sens ? k_gather_unrolled<D, KT, true, RR> : k_gather_unrolled<D, KT, false, RR>;
-    SOPTX_PICK(1)
-    SOPTX_PICK(2)
-    SOPTX_PICK(3)
-    SOPTX_PICK(4)
-    SOPTX_PICK(5)
-    SOPTX_PICK(6)
-#undef SOPTX_PICK
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (err != cudaSuccess) return err;
-    const KT *K = (const KT *)m.d.K;
-    const int64_t kstride = m.path == SOPTX_PATH_CACHED ? (int64_t)h.ldof * h.ldof : 0;
-    kern<<<ggrid(h.nn, kGW), kGW * 32, sm, st>>>(h.nn, h.nb, h.max_deg, m.d.node_off, m.d.inc_ptr, m.d.inc,
-                                                 m.d.inc_e, m.d.inc_a, m.d.pos,
-                                                 m.d.cell_node, K, kstride, m.d.Edf, m.d.udf, rho,
-                                                 simp_params(m.mat), vals, m.d.part);
-    return cudaGetLastError();
+    const int nb = m.h.nb;
+    if constexpr (D == 3) {
+        if (nb == 10)   // P2 tetrahedra: 2 nodes x 3 rows x 5 lanes, 6 rounds
+            return gather_launch<D, KT, 2>(m, rho, vals, sens, 6,
+                                           sens ? k_gather_rows<3, 10, KT, true, 2, 6> : k_gather_rows<3, 10, KT, false, 2, 6>, st);
+    } else {
+        if (nb == 10)   // P3 triangles: 4 nodes x 2 rows x 4 lanes, 5 rounds
+            return gather_launch<D, KT, 4>(m, rho, vals, sens, 5,
+                                           sens ? k_gather_rows<2, 10, KT, true, 4, 5> : k_gather_rows<2, 10, KT, false, 4, 5>, st);
+    }
+    return gather_launch<D, KT, 1>(m, rho, vals, sens, 4,
+                                   sens ? k_gather_nodes<D, KT, true, 1, 4, true> : k_gather_nodes<D, KT, false, 1, 4, true>, st);
 }
 
 }  // namespace
