@@ -55,6 +55,25 @@ __device__ __forceinline__ df shfl_df(df v, int src)
     return df{__shfl_sync(kFull, v.h, src), __shfl_sync(kFull, v.l, src)};
 }
 
+// Bulk shared -> global copies by the copy engine (cp.async.bulk, no tensor
+// map): both addresses 16-byte aligned, size a multiple of 16.  A warp
+// stages a node's rows in shared memory and one lane hands them to the copy
+// engine, so the stores do not queue behind the warps' shared-memory and
+// shuffle traffic in the load/store unit.
+__device__ __forceinline__ void bulk_store(double *gdst, const double *ssrc, uint32_t bytes)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(ssrc);
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(s), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// wait until at most one committed group is still reading its shared source
+__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+// wait until every committed group has completed
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// order this thread's generic-proxy shared-memory writes before later async-proxy reads
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // o: 0 -> L, 1 -> H, 2 -> H + L, 3 -> H - L.  `lsel` = (o == 0) and
 // `coef` = 0, 1 or -1 (the factor on L) are per-lane constants.
 __device__ __forceinline__ df combine(bool lsel, float coef, df L, df H)
@@ -167,8 +186,12 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restric
     tq[3] = axis_opt(dx, false) + 4 * axis_opt(dy, true) + 16 * axis_opt(dz, true);     // {1, 2}
     __shared__ float2 kap_s[27 * 9];
     __shared__ double kapd_s[27 * 9];
-    __shared__ double stage_s[WPB][27 * 9];     // one node's d rows, written back coalesced
-    double *stage = stage_s[threadIdx.x >> 5];
+    // two staging buffers per warp (a node's d rows), 16-byte aligned, one
+    // spare slot so that a value sits at the same 16-byte phase as its
+    // destination; the copy engine writes a buffer out while the warp fills
+    // the other one
+    __shared__ __align__(16) double stage_s[WPB][2][27 * 9 + 1];
+    int buf = 0;
     for (int t = threadIdx.x; t < 27 * 9; t += blockDim.x) {
         kap_s[t] = kappa_g[t];
         kapd_s[t] = (double)kappa_g[t].x + (double)kappa_g[t].y;
@@ -240,6 +263,13 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restric
                     const df a = shfl_df(A, tq[q] & 31), b = shfl_df(B, tq[q] & 31);
                     T[q] = tq[q] >= 32 ? b : a;
                 }
+                // the buffer about to be filled was handed to the copy engine two
+                // nodes ago: wait until that copy has read it
+                if (lane == 0) bulk_wait_read_1();
+                __syncwarp();
+                // value t of the node's block goes to slot ph + t, ph the 16-byte phase of base
+                const int ph = (int)((reinterpret_cast<uintptr_t>(base) >> 3) & 1);
+                double *stage = stage_s[threadIdx.x >> 5][buf];
                 if (valid) {
                     // Two routes to an FP64 value, balancing the FP32/integer
                     // pipes against the otherwise idle FP64 pipe: classes below
@@ -250,7 +280,7 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restric
                     for (int q = 0; q < kFp64Classes; q++) Td[q] = df_to_double(T[q].h, T[q].l);
 #pragma unroll
                     for (int i = 0; i < 3; i++) {
-                        double *row = stage + i * rowlen + 3 * mi;
+                        double *row = stage + ph + i * rowlen + 3 * mi;
 #pragma unroll
                         for (int j = 0; j < 3; j++) {
                             const int q = (i == j) ? 0 : (i + j == 1 ? 1 : (i + j == 2 ? 2 : 3));
@@ -264,15 +294,24 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restric
                         }
                     }
                 }
+                fence_proxy_async_smem();
                 __syncwarp();
+                // a value at an odd 8-byte phase at either end goes out by a plain store
                 const int blk = 3 * rowlen;
-                for (int t = lane; t < blk; t += 32) __stcs(base + t, stage[t]);
-                __syncwarp();
+                const int head = ph, mid = (blk - head) & ~1, tail = blk - head - mid;
+                if (lane == 0 && mid > 0) {
+                    bulk_store(base + head, stage + ph + head, (uint32_t)(8 * mid));
+                    bulk_commit();
+                }
+                if (lane == 1 && head) __stcs(base, stage[ph]);
+                if (lane == 2 && tail) __stcs(base + blk - 1, stage[ph + blk - 1]);
+                buf ^= 1;
             }
             cur = nxt;
             off = off_next;
         }
     }
+    if (lane == 0) bulk_wait_all();
 }
 
 // 2D: three nodes per warp, lanes 9g .. 9g+8 serve node g, one lane per offset.
