@@ -397,7 +397,8 @@ def run_ours(args, rank, world, local_rank):
     if fused:
         # one pass does both: its algorithmic bytes are the whole step's
         achieved = ab["step"] / asm_avg_s / 1e9
-        kernel_name, kernel_file, alg_launch = "k_gather_unrolled", "gather.cu", ab["step"]
+        kernel_name = "k_gather_rows" if mesh.nb == 10 else "k_gather_nodes"
+        kernel_file, alg_launch = "gather.cu", ab["step"]
     else:
         achieved = ab["assemble"] / asm_avg_s / 1e9
         kernel_name, kernel_file, alg_launch = "k_lattice_assemble3", "lattice.cu", ab["assemble"]
