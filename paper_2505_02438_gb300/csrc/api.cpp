@@ -33,7 +33,7 @@ static void free_device(DeviceMesh &d)
 {
     void *ptrs[] = {d.indptr, d.indices, d.cell_node, d.node_off, d.inc_ptr, d.inc,
                     d.pos, d.geo, d.M, d.K, d.scratch, d.Edf, d.kappa, d.K0, d.sectors, d.udf, d.part,
-                    d.inc_e, d.inc_a};
+                    d.inc_e, d.inc_a, d.counter};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     d = DeviceMesh{};
@@ -178,6 +178,12 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
         cudaError_t e = dev_alloc((void **)&d.scratch, d.scratch_len * sizeof(double));
         if (e != cudaSuccess) { cudaGetLastError(); s = cuda_status(e, "scratch"); }
         else B += d.scratch_len * (int64_t)sizeof(double);
+    }
+    if (s == SOPTX_OK) {
+        cudaError_t e = dev_alloc((void **)&d.counter, 16);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d.counter, 0, 16, st);
+        if (e != cudaSuccess) { cudaGetLastError(); s = cuda_status(e, "grid-sum ticket"); }
+        else B += 16;
     }
     if (s == SOPTX_OK) s = cuda_status(launch_element_matrices(*m, n_elem_mats, st), "element matrices kernel");
     if (s == SOPTX_OK) s = cuda_status(cudaStreamSynchronize(st), "mesh setup");

@@ -2,7 +2,7 @@
 // K^0 when every cell has the same Jacobian), FP64-accurate on the FP32 pipes.
 //
 //  k_prep          : E(rho_e) per cell and, when u is given, u per dof, as
-//                    float pairs (FP64 math once per item).
+//                    float pairs (integer operations and float-pair SIMP).
 //  k_gather_nodes  : a group of lanes owns the d rows of one node; it walks
 //                    the node's incident cells in ascending order and for
 //                    each reads the node's row block of K_e^0 once, adding
@@ -33,18 +33,7 @@ __global__ void k_prep(int64_t nc, const double *__restrict__ rho, SimpParams sp
                        int64_t ndof, const double *__restrict__ u, float2 *__restrict__ udf)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc; e += stride) {
-        const double E = simp_E(sp, rho[e]);
-        const double a = fabs(E);
-        float2 out;
-        if (E == 0.0) out = make_float2(0.f, 0.f);
-        else if (!(a >= 0x1p-60 && a <= 0x1p60)) out = make_float2((float)E, __int_as_float(0x7fc00000));
-        else {
-            const df v = df_from_double(E);
-            out = make_float2(v.h, v.l);
-        }
-        Edf[e] = out;
-    }
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc; e += stride) Edf[e] = simp_E_pair(sp, rho[e]);
     if (u)
         for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < ndof; r += stride) {
             const df v = df_split(u[r]);
@@ -509,12 +498,14 @@ __global__ void __launch_bounds__(kGW * 32, 2) k_gather_rows(const GatherArgs<KT
 }
 
 // One thread per cell: s_e = sum_a part[e][a] in node order.  out[e] =
-// g E'(rho_e) s_e with g = *gscale, or -1 (the compliance sensitivity).
-__global__ void k_sens_finalize(int64_t nc, int nb, const double *__restrict__ part, const double *__restrict__ rho,
-                                SimpParams sp, const double *__restrict__ gscale, double *__restrict__ out,
-                                double *__restrict__ partial)
+// g E'(rho_e) s_e with g = *gscale, or -1 (the compliance sensitivity).  With
+// c, also c = sum_e E_e s_e over the grid (fixed order, last block).
+__global__ void __launch_bounds__(256) k_sens_finalize(int64_t nc, int nb, const double *__restrict__ part,
+                                                       const double *__restrict__ rho, SimpParams sp,
+                                                       const double *__restrict__ gscale, double *__restrict__ out,
+                                                       double *__restrict__ partial, unsigned *__restrict__ counter,
+                                                       double *__restrict__ c)
 {
-    __shared__ double wsum[8];
     const double g = gscale ? *gscale : -1.0;
     double mine = 0.0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc; e += (int64_t)gridDim.x * blockDim.x) {
@@ -524,16 +515,7 @@ __global__ void k_sens_finalize(int64_t nc, int nb, const double *__restrict__ p
         if (out) out[e] = g * simp_dE(sp, r) * s;
         mine += simp_E(sp, r) * s;
     }
-    if (partial) {
-        mine = warp_sum(mine);
-        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = mine;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += wsum[w];
-            partial[blockIdx.x] = t;
-        }
-    }
+    if (c) grid_sum_last_block(mine, partial, counter, c);
 }
 
 int ggrid(int64_t items, int per) { return (int)std::max<int64_t>(1, std::min<int64_t>((items + per - 1) / per, 152 * 16)); }
@@ -619,11 +601,8 @@ cudaError_t launch_gather(const soptx_mesh_s &m, const double *rho, const double
     }
     if (!sens) return cudaSuccess;
     const int grid = gather_finalize_grid(h.nc);
-    k_sens_finalize<<<grid, 256, 0, st>>>(h.nc, h.nb, m.d.part, rho, simp_params(m.mat), gscale, dc,
-                                          c ? m.d.scratch : nullptr);
-    err = cudaGetLastError();
-    if (err != cudaSuccess || !c) return err;
-    k_reduce_partials<<<1, 256, 0, st>>>(grid, m.d.scratch, c);
+    k_sens_finalize<<<grid, 256, 0, st>>>(h.nc, h.nb, m.d.part, rho, simp_params(m.mat), gscale, dc, m.d.scratch,
+                                          m.d.counter, c);
     return cudaGetLastError();
 }
 

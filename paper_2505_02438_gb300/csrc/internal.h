@@ -84,6 +84,7 @@ struct DeviceMesh {
     void *K = nullptr;             // uniform: [ldof][ldof]; cached: [nc][ldof][ldof]
     double *scratch = nullptr;     // partial sums
     int64_t scratch_len = 0;
+    unsigned *counter = nullptr;   // last-block ticket of the grid sums (zero between calls)
     // order-1 box lattice path
     float2 *Edf = nullptr;         // [nc] element moduli as float pairs
     float2 *kappa = nullptr;       // [3^d][d][d] reference blocks as float pairs

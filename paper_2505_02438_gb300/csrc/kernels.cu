@@ -6,6 +6,7 @@
 //  k_Ku               : (K(rho) u) without forming K, for the u-gradient.
 // The hot kernels live in lattice.cu (box lattices) and gather.cu (any mesh).
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 
 #include "internal.h"
@@ -133,6 +134,14 @@ SimpParams simp_params(const Material &m)
     sp.dE = m.dE;
     sp.p = m.p;
     sp.p_int = m.p_int;
+    auto split = [](double x, float &h, float &l) {
+        h = (float)x;
+        l = (float)(x - (double)h);
+    };
+    split(m.dE, sp.dEh, sp.dEl);
+    split(m.Emin, sp.Eminh, sp.Eminl);
+    auto normal = [](double x) { return x == 0.0 || (std::fabs(x) >= 0x1p-100 && std::fabs(x) <= 0x1p100); };
+    sp.pair_ok = (m.p_int >= 1 && m.p_int <= 4 && normal(m.dE) && normal(m.Emin)) ? 1 : 0;
     return sp;
 }
 

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include "df64.cuh"
+
 namespace soptx {
 
 // Modified SIMP, Sec. 2.1:  E(rho) = Emin + rho^p (E0 - Emin),
@@ -10,6 +12,10 @@ namespace soptx {
 struct SimpParams {
     double Emin, dE, p;
     int p_int;
+    // float-pair copies of dE and Emin; pair_ok when p is an integer in 1..4
+    // and both are zero or normal floats in [2^-100, 2^100]
+    float dEh, dEl, Eminh, Eminl;
+    int pair_ok;
 };
 
 __device__ __forceinline__ double simp_pow(const SimpParams &sp, double r, int minus)
@@ -32,6 +38,28 @@ __device__ __forceinline__ double simp_dE(const SimpParams &sp, double r)
     return sp.p * simp_pow(sp, r, 1) * sp.dE;
 }
 
+// E(rho) as the float pair the assembly kernels read; a NaN low word flags a
+// modulus outside [2^-60, 2^60] (those nodes are redone in FP64).  For
+// integer p and rho in [2^-16, 2^16] the SIMP law is evaluated in float-pair
+// arithmetic on the FP32 pipes (relative error below 2^-42); otherwise in FP64.
+__device__ __forceinline__ float2 simp_E_pair(const SimpParams &sp, double r)
+{
+    if (sp.pair_ok && r >= 0x1p-16 && r <= 0x1p16) {
+        const df x = df_split(r);
+        df v = x;
+        for (int i = 1; i < sp.p_int; i++) v = df_mul(v, x);
+        const df E = df_add(df_mul(v, df{sp.dEh, sp.dEl}), df{sp.Eminh, sp.Eminl});
+        const float a = fabsf(E.h);
+        if (a >= 0x1p-60f && a <= 0x1p60f) return make_float2(E.h, E.l);
+    }
+    const double E = simp_E(sp, r);
+    const double a = fabs(E);
+    if (E == 0.0) return make_float2(0.f, 0.f);
+    if (!(a >= 0x1p-60 && a <= 0x1p60)) return make_float2((float)E, __int_as_float(0x7fc00000));
+    const df v = df_from_double(E);
+    return make_float2(v.h, v.l);
+}
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
@@ -41,6 +69,45 @@ __device__ __forceinline__ double warp_sum(double v)
 
 struct Material;
 SimpParams simp_params(const Material &m);
+
+// Sum of `mine` over the grid into *c, deterministically: each block writes its
+// partial (a fixed-order butterfly per warp, then the warps in order), the last block to finish (an
+// atomic ticket on *counter) adds all partials in index order and resets the
+// ticket for the next call.  blockDim.x must be a power of two <= 256, and
+// calls that share `partial` / `counter` must not overlap on the device.
+__device__ __forceinline__ void grid_sum_last_block(double mine, double *__restrict__ partial,
+                                                    unsigned *__restrict__ counter, double *__restrict__ c)
+{
+    __shared__ double red[256];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    if (lane == 0) red[warp] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < nw; w++) t += red[w];
+        partial[blockIdx.x] = t;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double t = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(partial + i);
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *c = red[0];
+        *counter = 0u;
+    }
+}
 
 // Element-matrix entries: float pairs (FP64 element matrices, value h + l) or
 // plain floats (FP32 element matrices).

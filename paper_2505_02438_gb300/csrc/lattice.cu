@@ -34,20 +34,8 @@ constexpr unsigned kFull = 0xffffffffu;
 
 __global__ void k_simp_df(int64_t nc, const double *__restrict__ rho, SimpParams sp, float2 *__restrict__ Edf)
 {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc; e += (int64_t)gridDim.x * blockDim.x) {
-        const double E = simp_E(sp, rho[e]);
-        const double a = fabs(E);
-        float2 out;
-        if (E == 0.0) {
-            out = make_float2(0.f, 0.f);
-        } else if (!(a >= 0x1p-60 && a <= 0x1p60)) {
-            out = make_float2((float)E, __int_as_float(0x7fc00000));   // flag: do this node in FP64
-        } else {
-            const df v = df_from_double(E);
-            out = make_float2(v.h, v.l);
-        }
-        Edf[e] = out;
-    }
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc; e += (int64_t)gridDim.x * blockDim.x)
+        Edf[e] = simp_E_pair(sp, rho[e]);
 }
 
 __device__ __forceinline__ df shfl_df(df v, int src)
@@ -415,11 +403,11 @@ template <int D>
 __global__ void __launch_bounds__(128, 3)
 k_lattice_sens(int nx, int ny, int nz, int64_t nc, const double *__restrict__ rho, const double *__restrict__ u,
                SimpParams sp, const float2 *__restrict__ Bg, const double *__restrict__ gscale,
-               double *__restrict__ out, double *__restrict__ partial)
+               double *__restrict__ out, double *__restrict__ partial, unsigned *__restrict__ counter,
+               double *__restrict__ c)
 {
     constexpr int NCR = 1 << D;
     __shared__ float2 Bs[NCR * D * D];
-    __shared__ double wsum[8];
     for (int t = threadIdx.x; t < NCR * D * D; t += blockDim.x) Bs[t] = Bg[t];
     __syncthreads();
     const double g = gscale ? *gscale : -1.0;
@@ -475,17 +463,7 @@ k_lattice_sens(int nx, int ny, int nz, int64_t nc, const double *__restrict__ rh
         out[e] = g * simp_dE(sp, re) * sd;
         mine += simp_E(sp, re) * sd;
     }
-    if (partial) {
-        mine = warp_sum(mine);
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        if (lane == 0) wsum[warp] = mine;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int w2 = 0; w2 < (int)(blockDim.x >> 5); w2++) t += wsum[w2];
-            partial[blockIdx.x] = t;
-        }
-    }
+    if (c) grid_sum_last_block(mine, partial, counter, c);
 }
 
 }  // namespace
@@ -501,16 +479,14 @@ cudaError_t launch_lattice_sensitivity(const soptx_mesh_s &m, const double *rho,
 {
     const auto &h = m.h;
     const int grid = lattice_sens_grid(h.nc);
-    double *part = c ? m.d.scratch : nullptr;
     if (h.dim == 3)
-        k_lattice_sens<3><<<grid, kSensThreads, 0, st>>>(h.lat_n[0], h.lat_n[1], h.lat_n[2], h.nc, rho, u, simp_params(m.mat),
-                                                (const float2 *)m.d.sectors, gscale, out, part);
+        k_lattice_sens<3><<<grid, kSensThreads, 0, st>>>(h.lat_n[0], h.lat_n[1], h.lat_n[2], h.nc, rho, u,
+                                                         simp_params(m.mat), (const float2 *)m.d.sectors, gscale, out,
+                                                         m.d.scratch, m.d.counter, c);
     else
         k_lattice_sens<2><<<grid, kSensThreads, 0, st>>>(h.lat_n[0], h.lat_n[1], 1, h.nc, rho, u, simp_params(m.mat),
-                                                (const float2 *)m.d.sectors, gscale, out, part);
-    cudaError_t err = cudaGetLastError();
-    if (err != cudaSuccess || !c) return err;
-    k_reduce_partials<<<1, 256, 0, st>>>(grid, m.d.scratch, c);
+                                                         (const float2 *)m.d.sectors, gscale, out, m.d.scratch,
+                                                         m.d.counter, c);
     return cudaGetLastError();
 }
 
