@@ -119,6 +119,22 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def max_over_ranks(values, world, device=None):
+    """Element-wise maximum of a list of floats over all ranks (the slowest
+    rank sets the whole job's time); identity on one rank."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def job_rate(units_per_rank, world, steps, ms_total):
+    """Whole-job throughput: the units every rank processed over the max-over-ranks time."""
+    return world * units_per_rank * steps / (ms_total / 1e3)
+
+
 def traffic_record(kernel_file, kernel_name):
     """dram bytes per launch of `kernel_name` from the committed ncu summary,
     valid only while the kernel source is unchanged (its sha256 matches)."""
@@ -357,10 +373,7 @@ def run_ours(args, rank, world, local_rank):
     asm_ms = sum(e[0].elapsed_time(e[1]) for e in ev)
     sens_ms = sum(e[1].elapsed_time(e[2]) for e in ev)
     step_ms = asm_ms + sens_ms
-    t = torch.tensor([step_ms, asm_ms, sens_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    step_ms, asm_ms, sens_ms = [float(x) for x in t.cpu()]
+    step_ms, asm_ms, sens_ms = max_over_ranks([step_ms, asm_ms, sens_ms], world, dev)
     clocks = sampler.summary()
 
     # end to end: pinned host inputs -> device, step, dc and c back to the host
@@ -384,10 +397,7 @@ def run_ours(args, rank, world, local_rank):
         e1.record(stream)
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
-    te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-    e2e_ms = float(te.item())
+    e2e_ms = max_over_ranks([e2e_ms], world, dev)[0]
 
     if rank != 0:
         return
@@ -403,7 +413,7 @@ def run_ours(args, rank, world, local_rank):
         achieved = ab["assemble"] / asm_avg_s / 1e9
         kernel_name, kernel_file, alg_launch = "k_lattice_assemble3", "lattice.cu", ab["assemble"]
     traffic = traffic_record(kernel_file, kernel_name)
-    value = world * nnz * K / (step_ms / 1e3) / 1e9
+    value = job_rate(nnz, world, K, step_ms) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "GNNZ/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": step_ms / K, "higher_is_better": True, "scaling": "weak",
@@ -412,14 +422,14 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD_DESC[args.workload], "path": mesh.path, "nnz": nnz, "ndof": ndof,
                    "n_cells": nc, "elem_prec": args.elem_prec, "l2": "flushed (256 MiB write) between steps",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "sens_elems_per_s": world * nc * K / (step_ms / 1e3),
+        "sens_elems_per_s": job_rate(nc, world, K, step_ms),
         "assemble_ms": asm_ms / K, "sensitivity_ms": sens_ms / K, "fused_step": fused, "setup_s": setup_s,
         "step_alg_bytes": ab["step"], "step_hbm_frac": ab["step"] / (step_ms / K / 1e3) / 1e9 / peak,
         "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "alg_bytes_per_launch": alg_launch},
         "clocks": clocks,
-        "e2e": {"value": world * nnz * n_e2e / (e2e_ms / 1e3) / 1e9, "unit": "GNNZ/s",
+        "e2e": {"value": job_rate(nnz, world, n_e2e, e2e_ms) / 1e9, "unit": "GNNZ/s",
                 "h2d_bytes_per_step": 8 * (nc + ndof), "d2h_bytes_per_step": 8 * (nc + 1),
                 "steps": n_e2e},
         "gpu_launches": 4 * K,   # prep/SIMP, assembly (+ fused sensitivity), sensitivity or finalize, reduction of c
