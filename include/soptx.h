@@ -228,6 +228,12 @@ const char *soptx_version(void);
  * (n >= 1) fails as if the device were out of memory; n <= 0 disables. */
 void soptx_debug_fail_alloc_after(int64_t n);
 
+/* Test hook for the lattice path: while enabled (nonzero), meshes created
+ * from now on skip the Walsh-sector split of the box element, so their
+ * sensitivities take the general gather kernels (the route a box whose
+ * element matrix does not split would take). */
+void soptx_debug_lattice_no_sectors(int32_t enable);
+
 #ifdef __cplusplus
 }
 #endif

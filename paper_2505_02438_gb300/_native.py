@@ -77,6 +77,7 @@ SIGNATURES = {
     "soptx_last_error": (ctypes.c_char_p, []),
     "soptx_version": (ctypes.c_char_p, []),
     "soptx_debug_fail_alloc_after": (None, [i64]),
+    "soptx_debug_lattice_no_sectors": (None, [i32]),
 }
 
 _lib = None

@@ -11,6 +11,7 @@ namespace soptx {
 
 static thread_local std::string g_last_error;
 static std::atomic<int64_t> g_fail_after{0};
+static std::atomic<int> g_no_sectors{0};
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
@@ -95,6 +96,7 @@ extern "C" {
 const char *soptx_last_error(void) { return g_last_error.c_str(); }
 const char *soptx_version(void) { return "soptx-gb300 0.1 (sm_103a)"; }
 void soptx_debug_fail_alloc_after(int64_t n) { g_fail_after.store(n > 0 ? n : 0); }
+void soptx_debug_lattice_no_sectors(int32_t enable) { g_no_sectors.store(enable ? 1 : 0); }
 
 soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_vertices, const double *coords,
                                int64_t n_cells, const int32_t *cell_vertices, const soptx_material *mat,
@@ -187,18 +189,6 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
     }
     if (s == SOPTX_OK) s = cuda_status(launch_element_matrices(*m, n_elem_mats, st), "element matrices kernel");
     if (s == SOPTX_OK) s = cuda_status(cudaStreamSynchronize(st), "mesh setup");
-    if (s == SOPTX_OK && m->path != SOPTX_PATH_LATTICE) {
-        // per-call float-pair moduli and displacements, per-(cell, node) partials
-        void *p1 = nullptr, *p2 = nullptr, *p3 = nullptr;
-        cudaError_t e = dev_alloc(&p1, (size_t)std::max<int64_t>(h.nc, 1) * sizeof(float2));
-        if (e == cudaSuccess) e = dev_alloc(&p2, (size_t)std::max<int64_t>(h.ndof, 1) * sizeof(float2));
-        if (e == cudaSuccess) e = dev_alloc(&p3, (size_t)std::max<int64_t>(h.nc * h.nb, 1) * sizeof(double));
-        d.Edf = (float2 *)p1;
-        d.udf = (float2 *)p2;
-        d.part = (double *)p3;
-        if (e != cudaSuccess) { cudaGetLastError(); s = cuda_status(e, "general-path scratch"); }
-        else B += std::max<int64_t>(h.nc, 1) * 8 + std::max<int64_t>(h.ndof, 1) * 8 + std::max<int64_t>(h.nc * h.nb, 1) * 8;
-    }
     if (s == SOPTX_OK && m->path == SOPTX_PATH_LATTICE) {
         // the lattice kernels read one FP64 K^0, its reference blocks as float
         // pairs, and per-call element moduli
@@ -218,13 +208,31 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
         if (s == SOPTX_OK) s = upload(&d.K0, K0, st, B, "K0");
         if (s == SOPTX_OK) s = upload(&d.kappa, kappa, st, B, "kappa");
         std::vector<float2> sectors;
-        if (s == SOPTX_OK && build_lattice_sectors(h.dim, K0, sectors)) s = upload(&d.sectors, sectors, st, B, "sectors");
+        // FP32 element matrices carry their rounding into K^0: zeros hold to about 2^-24 there
+        const double zero_tol = prec == SOPTX_ELEM_FP32 ? 1e-5 : 1e-13;
+        if (s == SOPTX_OK && !g_no_sectors.load() && build_lattice_sectors(h.dim, K0, zero_tol, sectors))
+            s = upload(&d.sectors, sectors, st, B, "sectors");
         if (s == SOPTX_OK) {
             cudaError_t e = dev_alloc((void **)&d.Edf, (size_t)std::max<int64_t>(h.nc, 1) * sizeof(float2));
             if (e != cudaSuccess) { cudaGetLastError(); s = cuda_status(e, "element moduli"); }
             else B += std::max<int64_t>(h.nc, 1) * (int64_t)sizeof(float2);
         }
         if (s == SOPTX_OK) s = cuda_status(cudaStreamSynchronize(st), "mesh setup");
+    }
+    if (s == SOPTX_OK && (m->path != SOPTX_PATH_LATTICE || !d.sectors)) {
+        // per-call float-pair moduli and displacements, per-(cell, node) partials
+        // of the general path (also the sensitivity of a lattice whose element
+        // matrix does not split into Walsh sectors)
+        void *p1 = nullptr, *p2 = nullptr, *p3 = nullptr;
+        cudaError_t e = d.Edf ? cudaSuccess : dev_alloc(&p1, (size_t)std::max<int64_t>(h.nc, 1) * sizeof(float2));
+        if (e == cudaSuccess) e = dev_alloc(&p2, (size_t)std::max<int64_t>(h.ndof, 1) * sizeof(float2));
+        if (e == cudaSuccess) e = dev_alloc(&p3, (size_t)std::max<int64_t>(h.nc * h.nb, 1) * sizeof(double));
+        if (!d.Edf) d.Edf = (float2 *)p1;
+        d.udf = (float2 *)p2;
+        d.part = (double *)p3;
+        if (e != cudaSuccess) { cudaGetLastError(); s = cuda_status(e, "general-path scratch"); }
+        else B += (p1 ? std::max<int64_t>(h.nc, 1) * 8 : 0) + std::max<int64_t>(h.ndof, 1) * 8 +
+                  std::max<int64_t>(h.nc * h.nb, 1) * 8;
     }
     if (s != SOPTX_OK) {
         std::string msg = g_last_error;

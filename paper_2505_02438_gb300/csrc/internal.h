@@ -125,7 +125,7 @@ cudaError_t launch_Ku(const soptx_mesh_s &m, const double *rho, const double *u,
 int64_t sensitivity_scratch_len(const soptx_mesh_s &m);
 cudaError_t launch_lattice_assemble(const soptx_mesh_s &m, const double *rho, double *vals, cudaStream_t st);
 void build_lattice_kappa(int dim, const std::vector<double> &K0, std::vector<float2> &kappa);
-bool build_lattice_sectors(int dim, const std::vector<double> &K0, std::vector<float2> &B);
+bool build_lattice_sectors(int dim, const std::vector<double> &K0, double zero_tol, std::vector<float2> &B);
 cudaError_t launch_lattice_sensitivity(const soptx_mesh_s &m, const double *rho, const double *u, double *out,
                                        double *c, const double *gscale, cudaStream_t st);
 int lattice_sens_grid(int64_t nc);

@@ -391,6 +391,16 @@ k_lattice_assemble2(int nx, int ny, int64_t nn, const int64_t *__restrict__ node
     }
 }
 
+// Entries of the sector blocks that vanish on every box: a row or column
+// whose Walsh mode is the rigid translation (c xor e_i = 0), and the coupling
+// of components i != j whose axes lie on different sides of the sector
+// (bit i of c != bit j of c), which the box's reflection symmetry cancels.
+// The host checks them (build_lattice_sectors) before this path is taken.
+__host__ __device__ constexpr bool sector_zero(int c, int i, int j)
+{
+    return (c ^ (1 << i)) == 0 || (c ^ (1 << j)) == 0 || (i != j && ((c >> i) & 1) != ((c >> j) & 1));
+}
+
 // Sensitivity on the box lattice.  The reflections of a box across its
 // mid-planes commute with K^0, so in the Walsh basis of each displacement
 // component, f_t(a) = (-1)^(t.a) over the 2^d corners a, K^0 splits into 2^d
@@ -400,7 +410,7 @@ k_lattice_assemble2(int nx, int ny, int64_t nn, const int64_t *__restrict__ node
 // B_c[i][j] = f_{c^e_i}^T K^0_{ij} f_{c^e_j} / 4^d, each term of the outer sum
 // a non-negative energy.  One thread per cell, float-pair arithmetic.
 template <int D>
-__global__ void __launch_bounds__(128, 3)
+__global__ void __launch_bounds__(128, 4)
 k_lattice_sens(int nx, int ny, int nz, int64_t nc, const double *__restrict__ rho, const double *__restrict__ u,
                SimpParams sp, const float2 *__restrict__ Bg, const double *__restrict__ gscale,
                double *__restrict__ out, double *__restrict__ partial, unsigned *__restrict__ counter,
@@ -449,6 +459,7 @@ k_lattice_sens(int nx, int ny, int nz, int64_t nc, const double *__restrict__ rh
             for (int i = 0; i < D; i++)
 #pragma unroll
                 for (int j = i; j < D; j++) {
+                    if (sector_zero(c, i, j)) continue;
                     const float2 bb = Bs[(c * D + i) * D + j];     // off-diagonal entries pre-doubled
                     const df t = df_mul_raw(df_mul_raw(x[i], x[j]), df{bb.x, bb.y});
                     float err;
@@ -491,10 +502,12 @@ cudaError_t launch_lattice_sensitivity(const soptx_mesh_s &m, const double *rho,
 }
 
 // Sector blocks B_c[i][j] of a box element's K^0 (see k_lattice_sens), the
-// off-diagonal ones doubled (only i <= j is summed); returns
+// off-diagonal ones doubled (only i <= j is summed), the entries that vanish
+// on every box (sector_zero) checked against zero_tol relative to the largest
+// sector entry; returns
 // false when K^0 does not split into the 2^d sectors (then the general
 // sensitivity kernel is used).
-bool build_lattice_sectors(int dim, const std::vector<double> &K0, std::vector<float2> &B)
+bool build_lattice_sectors(int dim, const std::vector<double> &K0, double zero_tol, std::vector<float2> &B)
 {
     const int ncr = 1 << dim, ldof = dim * ncr;
     auto f = [](int t, int a) { return (__builtin_popcount(t & a) & 1) ? -1.0 : 1.0; };
@@ -513,6 +526,13 @@ bool build_lattice_sectors(int dim, const std::vector<double> &K0, std::vector<f
                 }
     if (!(offmax <= 1e-13 * fmax)) return false;
     const double norm = 1.0 / ((double)ncr * ncr);
+    // the entries the kernel skips must vanish (to the rounding of K^0: zero_tol)
+    for (int c = 0; c < ncr; c++)
+        for (int i = 0; i < dim; i++)
+            for (int j = 0; j < dim; j++)
+                if (sector_zero(c, i, j) &&
+                    !(std::fabs(F[(((size_t)(c ^ (1 << i)) * dim + i) * ncr + (c ^ (1 << j))) * dim + j]) <= zero_tol * fmax))
+                    return false;
     B.assign((size_t)ncr * dim * dim, make_float2(0.f, 0.f));
     for (int c = 0; c < ncr; c++)
         for (int i = 0; i < dim; i++)

@@ -162,3 +162,18 @@ def test_lattice_anisotropic_boxes(P):
     c = c * np.array([2.0, 0.3])
     m, *_ = check_assembly(P, "quad", 1, c, cl, "fp64")
     assert m.path == "lattice"
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("cell,mk", [("hex", lambda: W.structured_hex(6, 5, 4)), ("quad", lambda: W.structured_quad(11, 7))])
+def test_lattice_without_sectors_uses_general_sensitivity(P, cell, mk, prec):
+    """A box lattice whose element matrix is not split into Walsh sectors
+    computes its sensitivities with the general gather kernels."""
+    from paper_2505_02438_gb300 import _native as N
+    coords, cells = mk()
+    N.lib().soptx_debug_lattice_no_sectors(1)
+    try:
+        m, *_ = check_assembly(P, cell, 1, coords, cells, prec)
+    finally:
+        N.lib().soptx_debug_lattice_no_sectors(0)
+    assert m.path == "lattice"
