@@ -93,6 +93,20 @@ def _jitter(coords, shape, amount, g):
     return coords
 
 
+def quad_grid(nx, ny, jitter=0.0, g=None):
+    """Quads of an nx x ny grid, interior vertices jittered (then the cells are
+    general bilinear quadrilaterals, not parallelograms)."""
+    coords, cells = structured_quad(nx, ny)
+    return _jitter(coords, (nx, ny), jitter, g), cells
+
+
+def hex_grid(nx, ny, nz, jitter=0.0, g=None):
+    """Hexahedra of an nx x ny x nz grid, interior vertices jittered (general
+    trilinear hexahedra)."""
+    coords, cells = structured_hex(nx, ny, nz)
+    return _jitter(coords, (nx, ny, nz), jitter, g), cells
+
+
 def triangle_grid(nx, ny, jitter=0.0, g=None):
     shape = (nx, ny)
     o = _cell_origins(shape)
@@ -184,6 +198,20 @@ def jittered_tet(nx=60, ny=20, nz=20, order=2, jitter=0.15, wl=4):
     rho = _rho_uniform(len(cells), rng(wl, 1))
     return Workload("tet_p%d_%dx%dx%d" % (order, nx, ny, nz), "tet", order, coords, cells,
                     rho=rho, seed_base=wl)
+
+
+def jittered_quad(nx=60, ny=20, order=1, jitter=0.2, wl=6):
+    """Bilinear quadrilaterals (interior vertices jittered), plane stress."""
+    coords, cells = quad_grid(nx, ny, jitter, rng(wl, 0))
+    rho = _rho_uniform(len(cells), rng(wl, 1))
+    return Workload("quadj_q%d_%dx%d" % (order, nx, ny), "quad", order, coords, cells, rho=rho, seed_base=wl)
+
+
+def jittered_hex(nx=120, ny=40, nz=40, order=1, jitter=0.15, wl=7):
+    """Trilinear hexahedra of the cantilever box, interior vertices jittered."""
+    coords, cells = hex_grid(nx, ny, nz, jitter, rng(wl, 0))
+    rho = _rho_uniform(len(cells), rng(wl, 1))
+    return Workload("hexj_q%d_%dx%dx%d" % (order, nx, ny, nz), "hex", order, coords, cells, rho=rho, seed_base=wl)
 
 
 def standard(i, scale=1.0):

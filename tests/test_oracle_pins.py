@@ -227,6 +227,29 @@ def test_element_matrix_symmetric_psd_rigid_null_space(cell, k):
         assert np.abs(K @ R.T).max() < 1e-12 * scale * max(1.0, np.abs(R).max())
 
 
+@pytest.mark.parametrize("cell,k", [(c, k) for c in ("quad", "hex") for k in (1, 2, 3)])
+def test_distorted_tensor_cell_symmetric_psd_rigid_null_space(cell, k):
+    """General (non-affine) bilinear / trilinear cells: K_e^0 is still
+    symmetric PSD with exactly the rigid-body null space (a rigid motion has
+    zero strain at every quadrature point), and moving the corners changes it
+    (it is not the parallelogram's matrix)."""
+    rng = np.random.default_rng(300 + k)
+    d = W.DIM[cell]
+    nrig = 3 if d == 2 else 6
+    for _ in range(2):
+        xa = affine_cell(cell, rng)
+        xv = xa + 0.12 * rng.standard_normal(xa.shape)
+        K = oracle.element_matrix(cell, k, xv, 0.3)
+        scale = np.abs(K).max()
+        np.testing.assert_allclose(K, K.T, atol=1e-14 * scale)
+        ev = np.linalg.eigvalsh(K)
+        assert ev[0] > -1e-12 * scale
+        assert np.sum(ev < 1e-10 * scale) == nrig
+        R = rigid_modes(local_node_positions(cell, k, xv))
+        assert np.abs(K @ R.T).max() < 1e-12 * scale * max(1.0, np.abs(R).max())
+        assert np.abs(K - oracle.element_matrix(cell, k, xa, 0.3)).max() > 1e-3 * scale
+
+
 @pytest.mark.parametrize("cell,k", [("tri", 2), ("tet", 2), ("quad", 2), ("hex", 1), ("tri", 3)])
 def test_element_matrix_scaling_and_rotation(cell, k):
     rng = np.random.default_rng(5)
@@ -458,6 +481,11 @@ def test_row_selection_matches_full():
 PATCH = [("tri", 1, 0.2), ("tri", 2, 0.2), ("tri", 3, 0.2), ("tet", 1, 0.15), ("tet", 2, 0.15),
          ("tet", 3, 0.15), ("quad", 1, 0.0), ("quad", 2, 0.0), ("quad", 3, 0.0), ("hex", 1, 0.0),
          ("hex", 2, 0.0)]
+# general (non-affine) bilinear / trilinear cells: the (k+1)-point Gauss rule
+# integrates the nodal forces of a constant stress exactly (the integrand
+# adj(J)^T grad phi is a polynomial of degree <= k + 1 per direction), so
+# the patch test holds on distorted meshes too
+PATCH_DISTORTED = [("quad", 1, 0.2), ("quad", 2, 0.2), ("quad", 3, 0.2), ("hex", 1, 0.15), ("hex", 2, 0.15)]
 
 
 def patch_mesh(cell, jitter):
@@ -467,11 +495,11 @@ def patch_mesh(cell, jitter):
     if cell == "tet":
         return W.kuhn_tets(3, 2, 2, jitter, g), (3, 2, 2)
     if cell == "quad":
-        return W.structured_quad(4, 3), (4, 3)
-    return W.structured_hex(2, 2, 2), (2, 2, 2)
+        return W.quad_grid(4, 3, jitter, g), (4, 3)
+    return W.hex_grid(3, 3, 3, jitter, g), (3, 3, 3)
 
 
-@pytest.mark.parametrize("cell,k,jit", PATCH)
+@pytest.mark.parametrize("cell,k,jit", PATCH + PATCH_DISTORTED)
 def test_patch_test_affine_field(cell, k, jit):
     """rho = 1, u = interpolant of an affine field: (K u)_i = 0 at every dof
     whose node is not on the boundary (constant stress, no body force)."""
