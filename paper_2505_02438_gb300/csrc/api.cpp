@@ -34,7 +34,7 @@ static void free_device(DeviceMesh &d)
 {
     void *ptrs[] = {d.indptr, d.indices, d.cell_node, d.node_off, d.inc_ptr, d.inc,
                     d.pos, d.geo, d.M, d.K, d.scratch, d.Edf, d.kappa, d.K0, d.sectors, d.udf, d.part,
-                    d.inc_e, d.inc_a, d.counter};
+                    d.inc_e, d.inc_a, d.counter, d.xcell, d.qw, d.qdphi, d.qdgeo};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     d = DeviceMesh{};
@@ -160,6 +160,17 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
     UP(d.inc_a, h.inc_a, "inc_a");
     UP(d.pos, h.pos, "pos");
     UP(d.M, ref.M, "reference integrals");
+    if (h.nonaffine) {
+        // general bilinear / trilinear cells: corner coordinates and the
+        // reference Gauss rule with the basis gradients at its points
+        RefQuad rq;
+        build_tensor_quadrature(ref, rq);
+        d.nq = rq.nq;
+        UP(d.xcell, h.xcell, "corner coordinates");
+        UP(d.qw, rq.w, "quadrature weights");
+        UP(d.qdphi, rq.dphi, "basis gradients");
+        UP(d.qdgeo, rq.dgeo, "vertex-basis gradients");
+    }
 #undef UP
     // geometry: all cells when cached, one otherwise
     if (s == SOPTX_OK) {
@@ -247,6 +258,7 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
     std::vector<int32_t>().swap(h.inc);
     std::vector<int32_t>().swap(h.inc_e);
     std::vector<uint8_t>().swap(h.inc_a);
+    std::vector<double>().swap(h.xcell);
     *out = m;
     return SOPTX_OK;
 }

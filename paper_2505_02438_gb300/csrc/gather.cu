@@ -318,18 +318,19 @@ __global__ void __launch_bounds__(kGW * 32, 2) k_gather_nodes(const GatherArgs<K
 }
 
 // The same gather for the cell types whose row blocks tile exactly into
-// the group's lanes (d nb = LPR R): P2 tetrahedra and P3 triangles.  Every
+// the group's lanes (d nb = LPR R): P2 tetrahedra, P3 triangles, Q1 hexahedra
+// and Q1 quadrilaterals.  Every
 // lane-round constant is fixed at compile time or per lane; the positions of
 // a cell's nodes arrive once per cell (lane b of the group loads pos(e, b))
 // and reach the lanes that need them by shuffles; the item loop is unrolled
 // by two so the prefetched item never has to be copied.
-template <int D, int NB, typename KT, bool SENS, int NPW, int R>
+template <int D, int NB, typename KT, bool SENS, int NPW, int R, int LPR>
 __global__ void __launch_bounds__(kGW * 32, 2) k_gather_rows(const GatherArgs<KT> A)
 {
     using KE = KEntry<KT>;
     using KV = typename KE::T;
-    constexpr int GL = 32 / NPW, LPR = GL / D, LDOF = D * NB, NPOS = (NB + GL - 1) / GL;
-    static_assert(LPR * R == LDOF, "the rounds must tile the row block");
+    constexpr int GL = 32 / NPW, LDOF = D * NB, NPOS = (NB + GL - 1) / GL;
+    static_assert(LPR * R == LDOF && D * LPR <= GL, "the rounds must tile the row block");
     static_assert(NPOS <= 2, "at most two positions per lane");
     extern __shared__ float2 smem_s[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
@@ -525,15 +526,14 @@ int ggrid(int64_t items, int per) { return (int)std::max<int64_t>(1, std::min<in
 // P3 triangles (20 columns): 4 nodes x 2 rows x 4 lanes, 5 rounds; anything
 // else one node per warp, 10 (3D) or 16 (2D) lanes per row, chunks of 4 rounds.
 template <int D, typename KT, int NPW, typename Kern>
-cudaError_t gather_launch(const soptx_mesh_s &m, const double *rho, double *vals, bool sens, int R, Kern kern,
-                          cudaStream_t st)
+cudaError_t gather_launch(const soptx_mesh_s &m, const double *rho, double *vals, bool sens, int R, int lpr,
+                          Kern kern, cudaStream_t st)
 {
     const auto &h = m.h;
     GatherArgs<KT> A;
     A.nn = h.nn;
     A.nb = h.nb;
     A.max_deg = h.max_deg;
-    const int lpr = 32 / NPW / D;
     const int rounds = (h.ldof + lpr - 1) / lpr;
     A.nck = (rounds + R - 1) / R;
     A.node_off = m.d.node_off;
@@ -566,16 +566,20 @@ template <int D, typename KT>
 cudaError_t gather_t(const soptx_mesh_s &m, const double *rho, double *vals, bool sens, cudaStream_t st)
 {
     const int nb = m.h.nb;
+#define SOPTX_ROWS(NB, NPW, R, LPR)                                                                            \
+    return gather_launch<D, KT, NPW>(m, rho, vals, sens, R, LPR,                                              \
+                                     sens ? k_gather_rows<D, NB, KT, true, NPW, R, LPR>                        \
+                                          : k_gather_rows<D, NB, KT, false, NPW, R, LPR>,                      \
+                                     st)
     if constexpr (D == 3) {
-        if (nb == 10)   // P2 tetrahedra: 2 nodes x 3 rows x 5 lanes, 6 rounds
-            return gather_launch<D, KT, 2>(m, rho, vals, sens, 6,
-                                           sens ? k_gather_rows<3, 10, KT, true, 2, 6> : k_gather_rows<3, 10, KT, false, 2, 6>, st);
+        if (nb == 10) SOPTX_ROWS(10, 2, 6, 5);   // P2 tetrahedra: 2 nodes x 3 rows x 5 lanes, 6 rounds
+        if (nb == 8) SOPTX_ROWS(8, 2, 6, 4);     // Q1 hexahedra: 2 nodes x 3 rows x 4 lanes, 6 rounds
     } else {
-        if (nb == 10)   // P3 triangles: 4 nodes x 2 rows x 4 lanes, 5 rounds
-            return gather_launch<D, KT, 4>(m, rho, vals, sens, 5,
-                                           sens ? k_gather_rows<2, 10, KT, true, 4, 5> : k_gather_rows<2, 10, KT, false, 4, 5>, st);
+        if (nb == 10) SOPTX_ROWS(10, 4, 5, 4);   // P3 triangles: 4 nodes x 2 rows x 4 lanes, 5 rounds
+        if (nb == 4) SOPTX_ROWS(4, 4, 2, 4);     // Q1 quadrilaterals: 4 nodes x 2 rows x 4 lanes, 2 rounds
     }
-    return gather_launch<D, KT, 1>(m, rho, vals, sens, 4,
+#undef SOPTX_ROWS
+    return gather_launch<D, KT, 1>(m, rho, vals, sens, 4, 32 / D,
                                    sens ? k_gather_nodes<D, KT, true, 1, 4, true> : k_gather_nodes<D, KT, false, 1, 4, true>, st);
 }
 

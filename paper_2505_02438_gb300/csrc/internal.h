@@ -45,6 +45,18 @@ struct RefElement {
 };
 bool build_ref_element(int cell, int order, RefElement &ref, std::string &err);
 
+// Gauss-Legendre rule of the reference square / cube, (order + 1) points per
+// direction, with the reference gradients of the order-k basis and of the
+// vertex (order-1) basis at the points: the standard numerical assembly of
+// general (non-affine) bilinear / trilinear cells.
+struct RefQuad {
+    int nq = 0, nvc = 0;
+    std::vector<double> w;      // [nq]
+    std::vector<double> dphi;   // [nq][nb][dim]
+    std::vector<double> dgeo;   // [nq][nvc][dim]
+};
+void build_tensor_quadrature(const RefElement &ref, RefQuad &q);
+
 // ---------------------------------------------------------------- host mesh setup
 struct HostMesh {
     int dim = 0, cell = 0, order = 0, nb = 0, ldof = 0, nvc = 0;
@@ -59,6 +71,8 @@ struct HostMesh {
     std::vector<uint16_t> pos;          // [ninc][nb] column block of node b in row n
     std::vector<double> geo;            // [nc][dim*dim + 1]: G = J^-1 (row-major), |det J|
     bool uniform = false;               // every cell has the same Jacobian
+    bool nonaffine = false;             // some tensor cell is not a parallelogram / parallelepiped
+    std::vector<double> xcell;          // [nc][nvc][dim] corner coordinates (non-affine meshes)
     bool lattice = false;               // order-1 box lattice in canonical numbering
     int lat_n[3] = {1, 1, 1};           // cells per axis
     int max_deg = 0;
@@ -81,6 +95,11 @@ struct DeviceMesh {
     uint16_t *pos = nullptr;       // [ninc][nb]
     double *geo = nullptr;         // [nc][dim*dim+1]
     double *M = nullptr;           // reference integrals [dim][dim][nb][nb]
+    double *xcell = nullptr;       // non-affine meshes: corner coordinates [nc][nvc][dim]
+    double *qw = nullptr;          //   quadrature weights [nq]
+    double *qdphi = nullptr;       //   basis gradients at the points [nq][nb][dim]
+    double *qdgeo = nullptr;       //   vertex-basis gradients at the points [nq][nvc][dim]
+    int nq = 0;
     void *K = nullptr;             // uniform: [ldof][ldof]; cached: [nc][ldof][ldof]
     double *scratch = nullptr;     // partial sums
     int64_t scratch_len = 0;

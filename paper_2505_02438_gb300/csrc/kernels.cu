@@ -110,6 +110,88 @@ int grid_for(int64_t items, int per_block)
     return (int)(g < 1 ? 1 : g);
 }
 
+// K_e^0 of general (non-affine) bilinear / trilinear cells by the reference
+// Gauss rule: per point q, J = sum_v x_v (grad N_v)^T, G = J^-1 and
+// g_a = G^T grad phi_a; P^{ab}_ij = sum_q w_q |det J_q| (g_a)_i (g_b)_j; then
+// the same isotropic combination as the affine kernel.  One block per cell;
+// G, w |det J| and the physical gradients of every point are staged in shared
+// memory.  Computed in CT, stored as OT.
+template <typename CT, typename OT>
+__global__ void k_element_matrices_quad(int dim, int nb, int nvc, int nq, int64_t n_elems,
+                                        const double *__restrict__ xcell, const double *__restrict__ qw,
+                                        const double *__restrict__ dphi, const double *__restrict__ dgeo,
+                                        double lam, double mu, OT *__restrict__ K)
+{
+    extern __shared__ double qsm[];
+    double *Gs = qsm;                      // [nq][dim][dim], G[m][i] = (J^-1)_{m i}
+    double *wd = Gs + nq * dim * dim;      // [nq]
+    double *gx = wd + nq;                  // [nq][nb][dim]
+    const int ldof = dim * nb;
+    for (int64_t e = blockIdx.x; e < n_elems; e += gridDim.x) {
+        const double *xv = xcell + e * nvc * dim;
+        for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+            double J[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            for (int v = 0; v < nvc; v++)
+                for (int i = 0; i < dim; i++)
+                    for (int m = 0; m < dim; m++) J[i * dim + m] += xv[v * dim + i] * dgeo[(q * nvc + v) * dim + m];
+            double *G = Gs + q * dim * dim;
+            double det;
+            if (dim == 2) {
+                det = J[0] * J[3] - J[1] * J[2];
+                G[0] = J[3] / det;
+                G[1] = -J[1] / det;
+                G[2] = -J[2] / det;
+                G[3] = J[0] / det;
+            } else {
+                const double a00 = J[4] * J[8] - J[5] * J[7], a01 = J[2] * J[7] - J[1] * J[8],
+                             a02 = J[1] * J[5] - J[2] * J[4];
+                det = J[0] * a00 + J[3] * a01 + J[6] * a02;
+                G[0] = a00 / det;
+                G[1] = a01 / det;
+                G[2] = a02 / det;
+                G[3] = (J[5] * J[6] - J[3] * J[8]) / det;
+                G[4] = (J[0] * J[8] - J[2] * J[6]) / det;
+                G[5] = (J[2] * J[3] - J[0] * J[5]) / det;
+                G[6] = (J[3] * J[7] - J[4] * J[6]) / det;
+                G[7] = (J[1] * J[6] - J[0] * J[7]) / det;
+                G[8] = (J[0] * J[4] - J[1] * J[3]) / det;
+            }
+            wd[q] = qw[q] * fabs(det);
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < nq * nb; t += blockDim.x) {
+            const int q = t / nb, a = t - q * nb;
+            const double *G = Gs + q * dim * dim;
+            for (int i = 0; i < dim; i++) {
+                double s = 0.0;
+                for (int m = 0; m < dim; m++) s += G[m * dim + i] * dphi[(q * nb + a) * dim + m];
+                gx[(q * nb + a) * dim + i] = s;
+            }
+        }
+        __syncthreads();
+        OT *Ke = K + (size_t)e * ldof * ldof;
+        for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
+            const int a = t / nb, b = t - a * nb;
+            CT P[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            for (int q = 0; q < nq; q++) {
+                const double *ga = gx + (q * nb + a) * dim, *gb = gx + (q * nb + b) * dim;
+                const CT w = (CT)wd[q];
+                for (int i = 0; i < dim; i++)
+                    for (int j = 0; j < dim; j++) P[i * dim + j] += w * (CT)ga[i] * (CT)gb[j];
+            }
+            CT tr = 0;
+            for (int m = 0; m < dim; m++) tr += P[m * dim + m];
+            for (int i = 0; i < dim; i++)
+                for (int j = 0; j < dim; j++) {
+                    CT v = (CT)lam * P[i * dim + j] + (CT)mu * P[j * dim + i];
+                    if (i == j) v += (CT)mu * tr;
+                    store_entry(Ke, (size_t)(dim * a + i) * ldof + dim * b + j, v);
+                }
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 __global__ void k_reduce_partials(int n, const double *__restrict__ partial, double *__restrict__ c)
@@ -151,6 +233,21 @@ cudaError_t launch_element_matrices(const soptx_mesh_s &m, int64_t n_elems, cuda
     const int grid = (int)std::min<int64_t>(std::max<int64_t>(n_elems, 1), 152 * 64);
     const int threads = 128;
     if (n_elems == 0) return cudaSuccess;
+    if (h.nonaffine) {
+        const size_t smem = (size_t)m.d.nq * (h.dim * h.dim + 1 + h.nb * h.dim) * sizeof(double);
+        auto k32 = k_element_matrices_quad<float, float>;
+        auto k64 = k_element_matrices_quad<double, float2>;
+        cudaError_t err = cudaFuncSetAttribute(m.prec == SOPTX_ELEM_FP32 ? (const void *)k32 : (const void *)k64,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        if (m.prec == SOPTX_ELEM_FP32)
+            k32<<<grid, threads, smem, st>>>(h.dim, h.nb, 1 << h.dim, m.d.nq, n_elems, m.d.xcell, m.d.qw, m.d.qdphi,
+                                             m.d.qdgeo, m.mat.lam, m.mat.mu, (float *)m.d.K);
+        else
+            k64<<<grid, threads, smem, st>>>(h.dim, h.nb, 1 << h.dim, m.d.nq, n_elems, m.d.xcell, m.d.qw, m.d.qdphi,
+                                             m.d.qdgeo, m.mat.lam, m.mat.mu, (float2 *)m.d.K);
+        return cudaGetLastError();
+    }
     if (m.prec == SOPTX_ELEM_FP32)
         k_element_matrices<float, float><<<grid, threads, 0, st>>>(h.dim, h.nb, n_elems, m.d.geo, m.d.M, m.mat.lam,
                                                                    m.mat.mu, (float *)m.d.K);

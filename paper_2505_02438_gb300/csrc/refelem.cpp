@@ -14,6 +14,7 @@
 //    nodes i/k of [0,1]; the integral factorises into 1D integrals of
 //    l_i l_j, l_i' l_j and l_i' l_j'.
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <map>
 #include <numeric>
@@ -243,6 +244,88 @@ bool build_ref_element(int cell, int order, RefElement &ref, std::string &err)
                     }
     }
     return true;
+}
+
+// Gauss-Legendre nodes and weights on [0, 1]: roots of the Legendre polynomial
+// P_n by Newton's method from the asymptotic guesses cos(pi (i + 3/4) / (n + 1/2)),
+// P_n and P_n' from the three-term recurrence; w = 2 / ((1 - x^2) P_n'(x)^2) on
+// [-1, 1], halved for [0, 1].
+static void gauss_legendre01(int n, std::vector<double> &t, std::vector<double> &w)
+{
+    t.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; i++) {
+        double x = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; it++) {
+            double p0 = 1.0, p1 = x;
+            for (int j = 1; j < n; j++) {
+                const double p2 = ((2.0 * j + 1.0) * x * p1 - j * p0) / (j + 1.0);
+                p0 = p1;
+                p1 = p2;
+            }
+            const double pn = n == 0 ? 1.0 : p1, pm = n == 1 ? 1.0 : p0;
+            dp = n * (x * pn - pm) / (x * x - 1.0);
+            const double dx = pn / dp;
+            x -= dx;
+            if (std::fabs(dx) < 1e-17) break;
+        }
+        // ascending order on [0, 1]
+        t[n - 1 - i] = 0.5 * (x + 1.0);
+        w[n - 1 - i] = 1.0 / ((1.0 - x * x) * dp * dp);
+    }
+}
+
+// 1D Lagrange polynomial l_i on the equispaced nodes j/k and its derivative at t
+static void lagrange1d(int k, int i, double t, double &val, double &der)
+{
+    val = 1.0;
+    der = 0.0;
+    for (int j = 0; j <= k; j++) {
+        if (j == i) continue;
+        const double den = (double)(i - j) / k;
+        der = der * ((t - (double)j / k) / den) + val / den;
+        val *= (t - (double)j / k) / den;
+    }
+}
+
+void build_tensor_quadrature(const RefElement &ref, RefQuad &q)
+{
+    const int dim = ref.dim, k = ref.order, n = k + 1, nb = ref.nb;
+    const int nvc = 1 << dim;
+    std::vector<double> t1, w1;
+    gauss_legendre01(n, t1, w1);
+    q.nvc = nvc;
+    q.nq = 1;
+    for (int m = 0; m < dim; m++) q.nq *= n;
+    q.w.assign(q.nq, 0.0);
+    q.dphi.assign((size_t)q.nq * nb * dim, 0.0);
+    q.dgeo.assign((size_t)q.nq * nvc * dim, 0.0);
+    for (int p = 0; p < q.nq; p++) {
+        int idx[3] = {p % n, (p / n) % n, p / (n * n)};
+        double xi[3] = {0, 0, 0}, w = 1.0;
+        for (int m = 0; m < dim; m++) {
+            xi[m] = t1[idx[m]];
+            w *= w1[idx[m]];
+        }
+        q.w[p] = w;
+        for (int a = 0; a < nb; a++) {
+            double val[3], der[3];
+            for (int m = 0; m < dim; m++) lagrange1d(k, ref.lat[a][m], xi[m], val[m], der[m]);
+            for (int m = 0; m < dim; m++) {
+                double g = der[m];
+                for (int o = 0; o < dim; o++)
+                    if (o != m) g *= val[o];
+                q.dphi[((size_t)p * nb + a) * dim + m] = g;
+            }
+        }
+        for (int v = 0; v < nvc; v++)
+            for (int m = 0; m < dim; m++) {
+                double g = ((v >> m) & 1) ? 1.0 : -1.0;
+                for (int o = 0; o < dim; o++)
+                    if (o != m) g *= ((v >> o) & 1) ? xi[o] : 1.0 - xi[o];
+                q.dgeo[((size_t)p * nvc + v) * dim + m] = g;
+            }
+    }
 }
 
 }  // namespace soptx

@@ -93,18 +93,41 @@ bool geometry(HostMesh &hm, const double *coords, const int32_t *cv, std::string
         double scale = 0.0;
         for (int q = 0; q < d * d; q++) scale = std::max(scale, std::fabs(J[q]));
         if (!is_simplex(hm.cell)) {
-            // affine check: every corner at x0 + sum_m bit_m J[:, m]
-            for (int v = 0; v < nvc; v++) {
+            // affine check: every corner at x0 + sum_m bit_m J[:, m]; a general
+            // (bilinear / trilinear) cell is integrated by Gauss quadrature
+            bool affine = true;
+            for (int v = 0; v < nvc && affine; v++) {
                 const double *xv = coords + (int64_t)c[v] * d;
                 for (int i = 0; i < d; i++) {
                     double want = x0[i];
                     for (int m = 0; m < d; m++)
                         if ((v >> m) & 1) want += J[i * d + m];
-                    if (std::fabs(xv[i] - want) > 1e-10 * scale) {
-                        err = "cell " + std::to_string(e) +
-                              " is not a parallelogram/parallelepiped (non-affine tensor cells are not supported)";
+                    if (std::fabs(xv[i] - want) > 1e-10 * scale) affine = false;
+                }
+            }
+            if (!affine) {
+                // the Jacobian at every corner (edges toward the corner's
+                // neighbours along each axis) must keep one sign
+                hm.nonaffine = true;
+                double sgn = 0.0;
+                for (int v = 0; v < nvc; v++) {
+                    double Jc[9];
+                    const double *xv = coords + (int64_t)c[v] * d;
+                    for (int m = 0; m < d; m++) {
+                        const double *xn = coords + (int64_t)c[v ^ (1 << m)] * d;
+                        const double s = ((v >> m) & 1) ? -1.0 : 1.0;
+                        for (int i = 0; i < d; i++) Jc[i * d + m] = s * (xn[i] - xv[i]);
+                    }
+                    const double dc = d == 2 ? Jc[0] * Jc[3] - Jc[1] * Jc[2]
+                                             : Jc[0] * (Jc[4] * Jc[8] - Jc[5] * Jc[7]) -
+                                                   Jc[1] * (Jc[3] * Jc[8] - Jc[5] * Jc[6]) +
+                                                   Jc[2] * (Jc[3] * Jc[7] - Jc[4] * Jc[6]);
+                    if (!std::isfinite(dc) || std::fabs(dc) <= 1e-12 * std::pow(scale, d) ||
+                        (sgn != 0.0 && (dc > 0.0) != (sgn > 0.0))) {
+                        err = "cell " + std::to_string(e) + " is inverted or degenerate at corner " + std::to_string(v);
                         return false;
                     }
+                    sgn = dc;
                 }
             }
         }
@@ -146,6 +169,14 @@ bool geometry(HostMesh &hm, const double *coords, const int32_t *cv, std::string
             for (int q = 0; q < d * d; q++)
                 if (std::fabs(J[q] - J0[q]) > 1e-14 * j0max) hm.uniform = false;
         }
+    }
+    if (hm.nonaffine) {
+        hm.uniform = false;
+        hm.xcell.resize((size_t)hm.nc * nvc * d);
+        for (int64_t e = 0; e < hm.nc; e++)
+            for (int v = 0; v < nvc; v++)
+                for (int i = 0; i < d; i++)
+                    hm.xcell[((size_t)e * nvc + v) * d + i] = coords[(int64_t)cv[e * nvc + v] * d + i];
     }
     return true;
 }

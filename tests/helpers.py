@@ -38,6 +38,13 @@ def small_cases():
     cases.append(("hex_q2_4x3x2", "hex", 2, c, cl))
     c, cl = W.structured_hex(2, 2, 1)
     cases.append(("hex_q3_2x2x1", "hex", 3, c, cl))
+    # general (non-affine) bilinear / trilinear cells: Gauss quadrature per cell
+    for k in (1, 2, 3):
+        c, cl = W.quad_grid(9, 6, 0.2, g(20 + k))
+        cases.append(("quad_q%d_9x6_distorted" % k, "quad", k, c, cl))
+    for k, sh in ((1, (5, 4, 3)), (2, (3, 3, 2)), (3, (2, 2, 2))):
+        c, cl = W.hex_grid(*sh, 0.15, g(30 + k))
+        cases.append(("hex_q%d_%dx%dx%d_distorted" % ((k,) + sh), "hex", k, c, cl))
     for k in (1, 2, 3):
         c, cl = W.triangle_grid(17, 9, 0.2, g(k))
         cases.append(("tri_p%d_17x9_jitter" % k, "tri", k, c, cl))

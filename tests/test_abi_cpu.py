@@ -81,6 +81,16 @@ def test_paths_selected():
     assert host_plan("tri", 1, *W.triangle_grid(4, 3, 0.2, np.random.default_rng(0)))["path"] == "cached"
 
 
+def test_distorted_tensor_cells_take_the_cached_path():
+    """General (non-affine) quads / hexes are integrated by Gauss quadrature
+    per cell: accepted, numbered like any mesh, never lattice or uniform."""
+    from paper_2505_02438_gb300.api import host_plan
+    g = np.random.default_rng(0)
+    pl = host_plan("quad", 2, *W.quad_grid(5, 4, 0.2, g))
+    assert pl["path"] == "cached" and pl["ndof"] == 2 * 11 * 9
+    assert host_plan("hex", 1, *W.hex_grid(3, 3, 2, 0.15, g))["path"] == "cached"
+
+
 def test_empty_mesh_plan():
     from paper_2505_02438_gb300.api import host_plan
     pl = host_plan("tri", 2, np.zeros((3, 2)), np.zeros((0, 3), np.int32))
@@ -90,7 +100,7 @@ def test_empty_mesh_plan():
 @pytest.mark.parametrize("bad,msg", [
     (lambda c, cl: (c, np.where(cl == 0, 10 ** 6, cl)), "out of range"),
     (lambda c, cl: (c, np.concatenate([cl[:, :1], cl[:, :1], cl[:, 2:]], 1)), "repeats a vertex"),
-    (lambda c, cl: (np.where(np.arange(len(c))[:, None] == 5, c * 1.1 + 0.3, c), cl), "not a parallelogram"),
+    (lambda c, cl: (np.where(np.arange(len(c))[:, None] == 6, c + 1.8, c), cl), "inverted or degenerate"),
 ])
 def test_invalid_meshes_rejected(bad, msg):
     from paper_2505_02438_gb300 import _native as N
