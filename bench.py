@@ -323,6 +323,74 @@ def run_serve(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_solve(args, rank, world, local_rank):
+    """The step after assembly on the hex Q1 120x40x40 cantilever: y = K x on
+    the assembled values (timed like the assembly: L2 flushed between calls),
+    and one Jacobi-preconditioned CG solve with x = 0 fixed and a tip load."""
+    import torch
+    import paper_2505_02438_gb300 as P
+    from paper_2505_02438_gb300 import build as B
+    if rank != 0:
+        return
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    B.build_library()
+    wl = workload("hex")
+    mesh = P.Mesh.from_workload(wl)
+    nnz, ndof, d = mesh.nnz, mesh.ndof, wl.dim
+    rho = torch.as_tensor(wl.rho, device=dev)
+    vals = mesh.assemble_K(rho)
+    x = torch.as_tensor(wl.displacement(ndof), device=dev)
+    y = torch.empty_like(x)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        mesh.spmv(vals, x, y)
+    torch.cuda.synchronize()
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    sampler = ClockSampler(local_rank)
+    with sampler:
+        for k in range(K):
+            flush.zero_()
+            ev[k][0].record(stream)
+            mesh.spmv(vals, x, y)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    alg = 8 * nnz + 4 * nnz // d + 16 * ndof
+    peak, peak_kind = peaks()
+    achieved = alg / (ms / K / 1e3) / 1e9
+    # one constrained solve: cantilever fixed at x = 0, unit load spread over the tip nodes, -z
+    coords = wl.coords
+    nn = ndof // d
+    fixed = torch.zeros(ndof, dtype=torch.uint8)
+    f = torch.zeros(ndof, dtype=torch.float64)
+    xs = torch.as_tensor(coords[:nn, 0])
+    fixed.view(nn, d)[xs < 1e-9] = 1
+    tip = torch.nonzero(xs > xs.max() - 1e-9).squeeze(1)
+    f.view(nn, d)[tip, d - 1] = -1.0 / len(tip)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    u, info = mesh.solve(vals, fixed.to(dev), f.to(dev), rtol=args.cg_rtol, max_iter=args.cg_max_iter, check_every=20)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    cg_ms = e0.elapsed_time(e1)
+    line = {"metric": "y = K x on the assembled CSR values, GNNZ/s; CG solve of K u = F", "value": nnz * K / (ms / 1e3) / 1e9,
+            "unit": "GNNZ/s", "n_gpus": 1, "steps": K, "warmup": args.warmup, "ms_per_step": ms / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC["hex"], "nnz": nnz, "ndof": ndof,
+                       "l2": "flushed (256 MiB write) between steps"},
+            "roofline": {"bound": "hbm", "kernel": "k_spmv", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": None, "alg_bytes_per_launch": alg},
+            "cg": {"iterations": info["iterations"], "converged": info["converged"],
+                   "rel_residual": info["rel_residual"], "rtol": args.cg_rtol, "ms": cg_ms,
+                   "ms_per_iteration": cg_ms / max(1, info["iterations"]),
+                   "problem": "cantilever: x = 0 face fixed, unit -z load over the x = L nodes, rho ~ U(0.001, 1)"},
+            "clocks": sampler.summary(), "gpu_launches": K}
+    print(json.dumps(line), flush=True)
+
+
 WORKLOAD_DESC = {
     "hex": "3D cantilever box 120x40x40 trilinear hex Q1 (192,000 cells, 610,203 dofs), FP64 K(rho) CSR + dc + c",
     "tet": "Kuhn P2 tetrahedra 60x20x20x6 (144,000 cells), jittered, FP64 K(rho) CSR + dc + c",
@@ -473,10 +541,12 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="hex", choices=sorted(WORKLOAD_DESC) + ["serve"])
+    ap.add_argument("--workload", default="hex", choices=sorted(WORKLOAD_DESC) + ["serve", "solve"])
     ap.add_argument("--elem-prec", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cg-rtol", type=float, default=1e-6)
+    ap.add_argument("--cg-max-iter", type=int, default=3000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -487,6 +557,9 @@ def main():
         return
     if args.workload == "serve":
         run_serve(args, rank, world, local_rank)
+        return
+    if args.workload == "solve":
+        run_solve(args, rank, world, local_rank)
         return
     if world > 1:
         import torch

@@ -214,3 +214,32 @@ def compliance_vjp(cell, k, coords, cells, mat, rho, u, g, want_u=True):
                                   E0, Emin, nu, p, int(ps), _p(rho), _p(u), float(g), _p(gr),
                                   _p(gu) if want_u else None), "compliance_vjp")
     return gr, gu
+
+
+def spmv(rowptr, cols, vals, x):
+    """y = K x for a CSR matrix, row by row in column order (plain loops over
+    numpy slices)."""
+    x = np.asarray(x, np.float64)
+    y = np.zeros(len(rowptr) - 1)
+    for r in range(len(y)):
+        sl = slice(rowptr[r], rowptr[r + 1])
+        y[r] = np.dot(vals[sl], x[cols[sl]])
+    return y
+
+
+def solve_dirichlet(rowptr, cols, vals, fixed, f, u_fixed):
+    """The discrete equilibrium K u = f (Sec. 2.2) with Dirichlet constraints:
+    u = u_fixed on the constrained dofs, K_ff u_f = f_f - K_fd u_d on the free
+    ones, solved directly (scipy's sparse LU as the library routine).
+    Returns u [ndof]."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    n = len(rowptr) - 1
+    K = sp.csr_matrix((vals, cols, rowptr), shape=(n, n))
+    fixed = np.asarray(fixed, bool)
+    free = ~fixed
+    u = np.zeros(n)
+    u[fixed] = np.asarray(u_fixed, np.float64)[fixed]
+    rhs = np.asarray(f, np.float64)[free] - K[free][:, fixed] @ u[fixed]
+    u[free] = spla.spsolve(K[free][:, free].tocsc(), rhs)
+    return u

@@ -27,6 +27,14 @@ class Material(ctypes.Structure):
                 ("p", ctypes.c_double), ("plane_strain", ctypes.c_int32)]
 
 
+class CgOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("check_every", ctypes.c_int32)]
+
+
+class CgResult(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32), ("rel_residual", ctypes.c_double)]
+
+
 class ServerOpts(ctypes.Structure):
     _fields_ = [("hbm_cap_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32), ("n_streams", ctypes.c_int32),
                 ("max_queue", ctypes.c_int32), ("device", ctypes.c_int32)]
@@ -68,6 +76,8 @@ SIGNATURES = {
     "soptx_mesh_destroy": (i32, [P]),
     "soptx_host_plan": (i32, [i32, i32, i32, i64, P, i64, P, Pi64, Pi64, Pi32, Pi32, P, P, P]),
     "soptx_lattice_sensitivity_noalloc": (i32, [i32, P, P, ctypes.POINTER(Material), P, P, P, P, P]),
+    "soptx_spmv": (i32, [P, P, P, P, P]),
+    "soptx_solve_cg": (i32, [P, P, P, P, P, ctypes.POINTER(CgOpts), P, ctypes.POINTER(CgResult)]),
     "soptx_server_create": (i32, [ctypes.POINTER(ServerOpts), PP]),
     "soptx_serve_submit": (i32, [P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
     "soptx_serve_wait": (i32, [P, ctypes.c_uint64, i64, ctypes.POINTER(Result)]),

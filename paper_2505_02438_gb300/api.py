@@ -134,6 +134,33 @@ class Mesh:
         return grad_rho, grad_u
 
 
+    # ------------------------------------------------------------ the step after assembly
+    def spmv(self, vals, x, y=None, stream=None):
+        """y = K x with the CSR values `vals` (e.g. from assemble_K)."""
+        if y is None:
+            y = torch.empty(self.ndof, dtype=torch.float64, device=self.device)
+        N.check(N.lib().soptx_spmv(self._h, _dptr(vals, torch.float64, self.nnz, "vals"),
+                                   _dptr(x, torch.float64, self.ndof, "x"), _dptr(y, torch.float64, self.ndof, "y"),
+                                   _stream(stream)))
+        return y
+
+    def solve(self, vals, fixed, f, u_fixed=None, rtol=1e-10, max_iter=10000, check_every=10, stream=None):
+        """K u = f on the free dofs (fixed: bool/uint8 [ndof]; u = u_fixed on the
+        constrained ones, 0 if not given) by Jacobi-preconditioned CG.
+        Returns (u, dict(iterations, converged, rel_residual))."""
+        fixed = fixed.to(device=self.device, dtype=torch.uint8).contiguous()
+        u = torch.zeros(self.ndof, dtype=torch.float64, device=self.device) if u_fixed is None else \
+            u_fixed.to(device=self.device, dtype=torch.float64).clone().contiguous()
+        opts = N.CgOpts(float(rtol), int(max_iter), int(check_every))
+        res = N.CgResult()
+        N.check(N.lib().soptx_solve_cg(self._h, _dptr(vals, torch.float64, self.nnz, "vals"),
+                                       _dptr(fixed, torch.uint8, self.ndof, "fixed"),
+                                       _dptr(f, torch.float64, self.ndof, "f"),
+                                       _dptr(u, torch.float64, self.ndof, "u"), ctypes.byref(opts), _stream(stream),
+                                       ctypes.byref(res)))
+        return u, dict(iterations=res.iterations, converged=bool(res.converged), rel_residual=res.rel_residual)
+
+
 def version():
     return N.lib().soptx_version().decode()
 

@@ -34,7 +34,7 @@ static void free_device(DeviceMesh &d)
 {
     void *ptrs[] = {d.indptr, d.indices, d.cell_node, d.node_off, d.inc_ptr, d.inc,
                     d.pos, d.geo, d.M, d.K, d.scratch, d.Edf, d.kappa, d.K0, d.sectors, d.udf, d.part,
-                    d.inc_e, d.inc_a, d.counter, d.xcell, d.qw, d.qdphi, d.qdgeo};
+                    d.inc_e, d.inc_a, d.counter, d.xcell, d.qw, d.qdphi, d.qdgeo, d.cg};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     d = DeviceMesh{};

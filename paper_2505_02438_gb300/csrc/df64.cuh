@@ -96,6 +96,15 @@ __device__ __forceinline__ df df_split(double x)
     return df{__uint_as_float(hb), l};
 }
 
+// df_split with exact zeros (and values below 2^-1022) mapped to (0, 0)
+// without the FP64 route, for inputs where zeros are common.
+__device__ __forceinline__ df df_split_z(double x)
+{
+    const uint32_t hi = (uint32_t)(__double_as_longlong(x) >> 32);
+    if (((hi >> 20) & 0x7ffu) == 0u) return df{0.f, 0.f};
+    return df_split(x);
+}
+
 // FP64 value of p + e, where p = round(a b) and e carries the product's
 // rounding error and cross terms (|e| <= 8 ulp(p)), built from the bit
 // patterns with integer operations: the double of p is exact (widen the

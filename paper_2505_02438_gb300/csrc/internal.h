@@ -112,6 +112,8 @@ struct DeviceMesh {
     // general path
     float2 *udf = nullptr;         // [ndof] u as float pairs
     double *part = nullptr;        // [nc][nb] per-(cell, node) partials of u_e^T K_e^0 u_e
+    // equilibrium solve (allocated by the first soptx_solve_cg)
+    double *cg = nullptr;          // r z p q diag [ndof], scalars, partials, counters
 };
 
 struct Material {

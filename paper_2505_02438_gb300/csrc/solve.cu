@@ -1,0 +1,422 @@
+// The step after assembly (include/soptx_solve.h): y = K x on the mesh's CSR
+// values, and Jacobi-preconditioned conjugate gradients for K u = f under
+// Dirichlet constraints.
+//
+//  k_spmv      : four nodes per warp, eight lanes per node; each lane takes
+//                the columns c, c+8, ... of the node's column list (shared by
+//                its d rows) and accumulates the first d-1 row sums in
+//                float-pair arithmetic (FP32 pipes) and the last row's with
+//                FP64 fused multiply-adds (FP64 pipe); the node's lanes then
+//                add their sums by a fixed butterfly.
+//                Optionally zeroes constrained rows and sums p . y over the grid.
+//  k_cg_*      : the element-wise CG updates with their dot products; every
+//                grid sum is a fixed-order block partial plus a last-block
+//                total, so the iterates are bitwise reproducible.
+// One FP64 fused multiply-add per stored value would bind the product to this
+// GPU's FP64 pipe (measured: 76% busy, 177 us on the hex Q1 120x40x40 matrix)
+// and float pairs for all of them to the issue rate (114 us), so the rows are
+// split between the two.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <vector>
+
+#include "df64.cuh"
+#include "internal.h"
+#include "kernels_common.cuh"
+#include "../../include/soptx_solve.h"
+
+namespace soptx {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kSpWarps = 8;
+constexpr int kCgThreads = 256;
+
+// Sums of NV values over the grid into out[0..NV), deterministic (a fixed
+// tree per block, the last block to finish adds the block partials in index
+// order).  partial: [NV][gridDim.x]; *counter is zero between calls.
+template <int NV>
+__device__ __forceinline__ void grid_sums(const double (&mine)[NV], double *__restrict__ partial,
+                                          unsigned *__restrict__ counter, double *__restrict__ out)
+{
+    __shared__ double red[NV][kCgThreads / 32];
+    __shared__ double fin[NV][kCgThreads];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        double v = mine[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        if (lane == 0) red[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NV; k++) {
+            double t = 0.0;
+            for (int w = 0; w < nw; w++) t += red[k][w];
+            partial[(size_t)k * gridDim.x + blockIdx.x] = t;
+        }
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int k = 0; k < NV; k++) {
+        double t = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(partial + (size_t)k * gridDim.x + b);
+        fin[k][threadIdx.x] = t;
+    }
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int k = 0; k < NV; k++) fin[k][threadIdx.x] += fin[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NV; k++) out[k] = fin[k][0];
+        *counter = 0u;
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kSpWarps * 32)
+k_spmv(int64_t nn, const int64_t *__restrict__ node_off, const int32_t *__restrict__ indices,
+       const double *__restrict__ vals, const double *__restrict__ x, double *__restrict__ y,
+       const uint8_t *__restrict__ fixed, const double *__restrict__ dotv, double *__restrict__ partial,
+       unsigned *__restrict__ counter, double *__restrict__ dot_out)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 3, c = lane & 7;       // 4 nodes per warp, 8 lanes per node
+    double mine = 0.0;
+    const int64_t step = (int64_t)gridDim.x * kSpWarps * 4;
+    for (int64_t n0 = ((int64_t)blockIdx.x * kSpWarps + warp) * 4; n0 < nn; n0 += step) {
+        const int64_t n = n0 + g;
+        const bool has = n < nn;
+        // float-pair sums of the node's d rows over this lane's columns c, c+8, ...
+        // rows 0 .. d-2 in float pairs on the FP32 pipes, row d-1 in FP64
+        // (DFMA) on the FP64 pipe, so that both pipes share the products
+        float S[D], C[D];
+        double Sd = 0.0;
+#pragma unroll
+        for (int i = 0; i < D; i++) S[i] = C[i] = 0.f;
+        int len = 0;
+        if (has) {
+            const int64_t off = node_off[n];
+            len = D * (int)(node_off[n + 1] - off);
+            const int64_t base = (int64_t)D * D * off;
+            const int32_t *cols = indices + base;                 // the node's rows share row 0's columns
+            const double *v = vals + base;
+            // four column rounds per pass: every load of the pass is issued
+            // before the arithmetic (a round past the row reads nothing and adds 0)
+            constexpr int U = 4;
+            for (int t0 = c; t0 < len; t0 += 8 * U) {
+                int cj[U];
+                double xr[U], vr[U][D];
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int t = t0 + 8 * u;
+                    cj[u] = t < len ? cols[t] : -1;
+                }
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int t = t0 + 8 * u;
+                    xr[u] = cj[u] >= 0 ? x[cj[u]] : 0.0;
+#pragma unroll
+                    for (int i = 0; i < D; i++) vr[u][i] = t < len ? __ldcs(v + (int64_t)i * len + t) : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const df xv = df_split_z(xr[u]);
+#pragma unroll
+                    for (int i = 0; i < D - 1; i++) {
+                        const df pr = df_mul_raw(df_split_z(vr[u][i]), xv);
+                        float s2, err;
+                        two_sum(S[i], pr.h, s2, err);
+                        S[i] = s2;
+                        C[i] = __fadd_rn(C[i], __fadd_rn(pr.l, err));
+                    }
+                    Sd = fma(vr[u][D - 1], xr[u], Sd);
+                }
+            }
+        }
+        // fixed-order butterfly over the node's 8 lanes; every lane ends with the same bits
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const double So = __shfl_xor_sync(kFull, Sd, o);
+            Sd = (c & o) == 0 ? Sd + So : So + Sd;
+        }
+#pragma unroll
+        for (int i = 0; i < D - 1; i++)
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                const float So = __shfl_xor_sync(kFull, S[i], o), Co = __shfl_xor_sync(kFull, C[i], o);
+                // order the pair by lane so both partners add the same operands in the same order
+                const bool lo = (c & o) == 0;
+                const float Sa = lo ? S[i] : So, Ca = lo ? C[i] : Co, Sb = lo ? So : S[i], Cb = lo ? Co : C[i];
+                float s2, err;
+                two_sum(Sa, Sb, s2, err);
+                S[i] = s2;
+                C[i] = __fadd_rn(__fadd_rn(Ca, Cb), err);
+            }
+        if (has && c < D) {
+            float h = 0.f, l = 0.f;
+#pragma unroll
+            for (int i = 0; i < D - 1; i++)
+                if (i == c) two_sum(S[i], C[i], h, l);
+            const int64_t row = (int64_t)D * n + c;
+            const double sv = c == D - 1 ? Sd : df_to_double(h, l);
+            const double yv = (fixed && fixed[row]) ? 0.0 : sv;
+            y[row] = yv;
+            if (dotv) mine = fma(dotv[row], yv, mine);
+        }
+    }
+    if (dot_out) {
+        const double m1[1] = {mine};
+        grid_sums<1>(m1, partial, counter, dot_out);
+    }
+}
+
+// diag[row] = K[row][row]: the diagonal sits in the node's own column block;
+// a binary search over row 0's sorted columns finds it.  A free row with a
+// non-positive diagonal raises *bad.
+template <int D>
+__global__ void k_diag(int64_t nn, const int64_t *__restrict__ node_off, const int32_t *__restrict__ indices,
+                       const double *__restrict__ vals, const uint8_t *__restrict__ fixed, double *__restrict__ diag,
+                       int *__restrict__ bad)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < D * nn; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t n = r / D;
+        const int i = (int)(r - n * D);
+        const int64_t off = node_off[n];
+        const int len = D * (int)(node_off[n + 1] - off);
+        const int64_t base = (int64_t)D * D * off;
+        const int32_t *cols = indices + base;
+        int lo = 0, hi = len;
+        const int32_t want = (int32_t)(D * n);
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (cols[mid] < want) lo = mid + 1;
+            else hi = mid;
+        }
+        double dv = 0.0;
+        if (lo < len && cols[lo] == want) dv = vals[base + (int64_t)i * len + lo + i];
+        const bool fx = fixed[r] != 0;
+        diag[r] = fx ? 1.0 : dv;
+        if (!fx && !(dv > 0.0)) atomicExch(bad, 1);
+    }
+}
+
+// u = 0 on the free dofs (the prescribed values stay on the constrained ones)
+__global__ void k_cg_zero_free(int64_t ndof, const uint8_t *__restrict__ fixed, double *__restrict__ u)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < ndof; r += (int64_t)gridDim.x * blockDim.x)
+        if (!fixed[r]) u[r] = 0.0;
+}
+
+// r = f - K u_D on the free rows (q holds K u_D with constrained rows zeroed),
+// z = r / diag, p = z; sums r.z and r.r
+__global__ void __launch_bounds__(kCgThreads)
+k_cg_start(int64_t ndof, const uint8_t *__restrict__ fixed, const double *__restrict__ f,
+           const double *__restrict__ q, const double *__restrict__ diag, double *__restrict__ r,
+           double *__restrict__ z, double *__restrict__ p, double *__restrict__ partial,
+           unsigned *__restrict__ counter, double *__restrict__ out)
+{
+    double m[2] = {0.0, 0.0};
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < ndof; k += (int64_t)gridDim.x * blockDim.x) {
+        const double rv = fixed[k] ? 0.0 : f[k] - q[k];
+        const double zv = rv / diag[k];
+        r[k] = rv;
+        z[k] = zv;
+        p[k] = zv;
+        m[0] = fma(rv, zv, m[0]);
+        m[1] = fma(rv, rv, m[1]);
+    }
+    grid_sums<2>(m, partial, counter, out);
+}
+
+// alpha = (r.z) / (p.q); u += alpha p; r -= alpha q; z = r / diag; sums r.z, r.r
+__global__ void __launch_bounds__(kCgThreads)
+k_cg_step(int64_t ndof, const uint8_t *__restrict__ fixed, const double *__restrict__ diag,
+          const double *__restrict__ p, const double *__restrict__ q, double *__restrict__ u,
+          double *__restrict__ r, double *__restrict__ z, const double *__restrict__ rz_old,
+          const double *__restrict__ pq, double *__restrict__ partial, unsigned *__restrict__ counter,
+          double *__restrict__ out)
+{
+    const double den = *pq;
+    const double alpha = den != 0.0 ? *rz_old / den : 0.0;
+    double m[2] = {0.0, 0.0};
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < ndof; k += (int64_t)gridDim.x * blockDim.x) {
+        if (fixed[k]) continue;
+        u[k] = fma(alpha, p[k], u[k]);
+        const double rv = fma(-alpha, q[k], r[k]);
+        const double zv = rv / diag[k];
+        r[k] = rv;
+        z[k] = zv;
+        m[0] = fma(rv, zv, m[0]);
+        m[1] = fma(rv, rv, m[1]);
+    }
+    grid_sums<2>(m, partial, counter, out);
+}
+
+// beta = (r.z)_new / (r.z)_old; p = z + beta p (zero on constrained dofs)
+__global__ void k_cg_direction(int64_t ndof, const uint8_t *__restrict__ fixed, const double *__restrict__ z,
+                               double *__restrict__ p, const double *__restrict__ rz_new,
+                               const double *__restrict__ rz_old)
+{
+    const double den = *rz_old;
+    const double beta = den != 0.0 ? *rz_new / den : 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < ndof; k += (int64_t)gridDim.x * blockDim.x)
+        p[k] = fixed[k] ? 0.0 : fma(beta, p[k], z[k]);
+}
+
+int spmv_grid(int64_t nn) { return (int)std::max<int64_t>(1, std::min<int64_t>((nn + 2 * kSpWarps - 1) / (2 * kSpWarps), 152 * 8)); }
+int cg_grid(int64_t ndof) { return (int)std::max<int64_t>(1, std::min<int64_t>((ndof + kCgThreads - 1) / kCgThreads, 152 * 4)); }
+
+cudaError_t launch_spmv(const soptx_mesh_s &m, const double *vals, const double *x, double *y, const uint8_t *fixed,
+                        const double *dotv, double *partial, unsigned *counter, double *dot_out, cudaStream_t st)
+{
+    const auto &h = m.h;
+    if (h.nn == 0) return cudaSuccess;
+    const int grid = spmv_grid(h.nn);
+    if (h.dim == 3)
+        k_spmv<3><<<grid, kSpWarps * 32, 0, st>>>(h.nn, m.d.node_off, m.d.indices, vals, x, y, fixed, dotv, partial,
+                                                  counter, dot_out);
+    else
+        k_spmv<2><<<grid, kSpWarps * 32, 0, st>>>(h.nn, m.d.node_off, m.d.indices, vals, x, y, fixed, dotv, partial,
+                                                  counter, dot_out);
+    return cudaGetLastError();
+}
+
+soptx_status cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return SOPTX_OK;
+    cudaGetLastError();
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? SOPTX_ENOMEM : SOPTX_ECUDA;
+}
+
+}  // namespace
+}  // namespace soptx
+
+using namespace soptx;
+
+extern "C" {
+
+soptx_status soptx_spmv(soptx_mesh m, const double *d_vals, const double *d_x, double *d_y, void *stream)
+{
+    if (!m) SOPTX_FAIL(SOPTX_EINVAL, "mesh is NULL");
+    if (m->h.nnz > 0 && (!d_vals || !d_x || !d_y)) SOPTX_FAIL(SOPTX_EINVAL, "d_vals / d_x / d_y is NULL");
+    return cuda_fail(launch_spmv(*m, d_vals, d_x, d_y, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                 (cudaStream_t)stream),
+                     "soptx_spmv");
+}
+
+soptx_status soptx_solve_cg(soptx_mesh m, const double *d_vals, const uint8_t *d_fixed, const double *d_f,
+                            double *d_u, const soptx_cg_opts *o, void *stream, soptx_cg_result *res)
+{
+    if (!m || !o || !res) SOPTX_FAIL(SOPTX_EINVAL, "mesh / opts / result is NULL");
+    *res = soptx_cg_result{0, 0, 0.0};
+    if (!(o->rtol > 0.0) || o->max_iter < 1 || o->check_every < 1)
+        SOPTX_FAIL(SOPTX_EINVAL, "need rtol > 0, max_iter >= 1, check_every >= 1");
+    const auto &h = m->h;
+    if (h.ndof == 0) {
+        res->converged = 1;
+        return SOPTX_OK;
+    }
+    if (!d_vals || !d_fixed || !d_f || !d_u) SOPTX_FAIL(SOPTX_EINVAL, "d_vals / d_fixed / d_f / d_u is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    auto &d = m->d;
+    const int sgrid = spmv_grid(h.nn), cgrid = cg_grid(h.ndof);
+    const int pmax = std::max(sgrid, cgrid);
+    // workspace: r z p q diag [ndof], scalars [8], partials [2][pmax], counters, flag
+    if (!d.cg) {
+        const size_t bytes = ((size_t)5 * h.ndof + 8 + 2 * (size_t)pmax) * sizeof(double) + 64;
+        void *p = nullptr;
+        cudaError_t e = dev_alloc(&p, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "CG workspace");
+        e = cudaMemsetAsync(p, 0, bytes, st);
+        if (e != cudaSuccess) {
+            cudaFree(p);
+            return cuda_fail(e, "CG workspace");
+        }
+        d.cg = (double *)p;
+        m->device_bytes += (int64_t)bytes;
+    }
+    double *r = d.cg, *z = r + h.ndof, *pv = z + h.ndof, *q = pv + h.ndof, *diag = q + h.ndof;
+    double *S = diag + h.ndof;              // 0,1: r.z (ping-pong)  2: p.q  3: r.r
+    double *partial = S + 8;
+    unsigned *counter = (unsigned *)(partial + 2 * (size_t)pmax);
+    int *bad = (int *)(counter + 4);
+
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+        const int dg = cg_grid(h.ndof);
+        if (h.dim == 3) k_diag<3><<<dg, kCgThreads, 0, st>>>(h.nn, d.node_off, d.indices, d_vals, d_fixed, diag, bad);
+        else k_diag<2><<<dg, kCgThreads, 0, st>>>(h.nn, d.node_off, d.indices, d_vals, d_fixed, diag, bad);
+        e = cudaGetLastError();
+    }
+    int bad_h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "soptx_solve_cg");
+    if (bad_h) SOPTX_FAIL(SOPTX_EINVAL, "a free dof has a non-positive diagonal (no element touches it?)");
+
+    // start: u = u_D, r = f - K u_D on the free rows, z = p = r / diag
+    k_cg_zero_free<<<cgrid, kCgThreads, 0, st>>>(h.ndof, d_fixed, d_u);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_spmv(*m, d_vals, d_u, q, d_fixed, nullptr, nullptr, nullptr, nullptr, st);
+    if (e == cudaSuccess) {
+        k_cg_start<<<cgrid, kCgThreads, 0, st>>>(h.ndof, d_fixed, d_f, q, diag, r, z, pv, partial, counter, S + 2);
+        e = cudaGetLastError();
+    }
+    // k_cg_start wrote (r.z, r.r) to S[2], S[3]; move r.z into the ping-pong slot 0
+    if (e == cudaSuccess) e = cudaMemcpyAsync(S, S + 2, sizeof(double), cudaMemcpyDeviceToDevice, st);
+    double rr0 = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&rr0, S + 3, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "soptx_solve_cg");
+    const double r0 = std::sqrt(rr0);
+    if (r0 == 0.0) {
+        res->converged = 1;
+        return SOPTX_OK;
+    }
+    double rr = rr0;
+    int it = 0;
+    while (it < o->max_iter) {
+        const int par = it & 1;
+        double *rz_old = S + par, *rz_new = S + (par ^ 1);
+        // q = K p (constrained rows zero), p.q -> S[2]
+        e = launch_spmv(*m, d_vals, pv, q, d_fixed, pv, partial, counter, S + 2, st);
+        if (e != cudaSuccess) break;
+        // u, r, z; (r.z, r.r) -> rz_new, S[3] through a two-slot sum
+        k_cg_step<<<cgrid, kCgThreads, 0, st>>>(h.ndof, d_fixed, diag, pv, q, d_u, r, z, rz_old, S + 2, partial,
+                                                counter, S + 4);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) break;
+        e = cudaMemcpyAsync(rz_new, S + 4, sizeof(double), cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(S + 3, S + 5, sizeof(double), cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) break;
+        k_cg_direction<<<cgrid, kCgThreads, 0, st>>>(h.ndof, d_fixed, z, pv, rz_new, rz_old);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) break;
+        it++;
+        if (it % o->check_every == 0 || it == o->max_iter) {
+            e = cudaMemcpyAsync(&rr, S + 3, sizeof(double), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) break;
+            if (std::sqrt(rr) <= o->rtol * r0) {
+                res->converged = 1;
+                break;
+            }
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "soptx_solve_cg");
+    res->iterations = it;
+    res->rel_residual = std::sqrt(rr) / r0;
+    return SOPTX_OK;
+}
+
+}  // extern "C"

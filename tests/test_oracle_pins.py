@@ -633,3 +633,37 @@ def test_compliance_vjp_central_differences():
         assert abs(fd - gr[e]) <= tol
     Ku = np.array([np.dot(v[rp[r]:rp[r + 1]], u[ci[rp[r]:rp[r + 1]]]) for r in range(ndof)])
     np.testing.assert_allclose(gu, 2 * g * Ku, rtol=1e-13, atol=1e-13 * np.abs(gu).max())
+
+
+# ---------------------------------------------------------------- the step after assembly (NEXT row f1)
+
+@pytest.mark.parametrize("cell,k,jit", [("quad", 2, 0.2), ("hex", 1, 0.15), ("tet", 2, 0.15), ("tri", 3, 0.2)])
+def test_dirichlet_solve_reproduces_affine_field(cell, k, jit):
+    """Patch test of the constrained solve: a homogeneous body (one density
+    for every cell), u = an affine field on every boundary dof, no load; the
+    discrete solution is that field at every dof (it lies in the element space
+    and its constant stress is in equilibrium)."""
+    (coords, cells), shape = patch_mesh(cell, jit)
+    d = W.DIM[cell]
+    xn = oracle.node_coords(cell, k, coords, cells)
+    A = np.random.default_rng(3).standard_normal((d, d))
+    b = np.random.default_rng(4).standard_normal(d)
+    ulin = (xn @ A.T + b).ravel()
+    rho = np.full(len(cells), 0.6)
+    rp, ci, v, ndof = oracle.assemble(cell, k, coords, cells, (1.0, 1e-9, 0.3, 3.0, 0), rho)
+    bnd = ~np.all((xn > 1e-9) & (xn < np.array(shape) - 1e-9), axis=1)
+    fixed = np.repeat(bnd, d)
+    u = oracle.solve_dirichlet(rp, ci, v, fixed, np.zeros(ndof), ulin)
+    assert (~fixed).sum() > 0
+    assert np.abs(u - ulin).max() < 1e-10 * np.abs(ulin).max()
+
+
+def test_spmv_matches_dense_product():
+    """The oracle's CSR product against a dense matrix-vector product."""
+    coords, cells = W.kuhn_tets(2, 2, 1, 0.1, np.random.default_rng(0))
+    rp, ci, v, ndof = oracle.assemble("tet", 2, coords, cells, (1.0, 1e-9, 0.3, 3.0, 0), np.full(len(cells), 0.7))
+    K = np.zeros((ndof, ndof))
+    for r in range(ndof):
+        K[r, ci[rp[r]:rp[r + 1]]] = v[rp[r]:rp[r + 1]]
+    x = np.random.default_rng(1).standard_normal(ndof)
+    np.testing.assert_allclose(oracle.spmv(rp, ci, v, x), K @ x, rtol=0, atol=1e-13 * np.abs(K).sum(1).max())
