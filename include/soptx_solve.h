@@ -25,26 +25,30 @@ extern "C" {
 soptx_status soptx_spmv(soptx_mesh mesh, const double *d_vals, const double *d_x, double *d_y, void *stream);
 
 typedef struct {
-    double rtol;           /* stop when ||r_free|| <= rtol * ||r_free at the start|| (> 0)     */
+    double rtol;           /* stop when ||r_free|| <= rtol * ||f_free - K_fd u_d|| (> 0)       */
     int32_t max_iter;      /* iteration cap (>= 1)                                             */
     int32_t check_every;   /* the residual is read back to the host every this many steps (>= 1) */
+    int32_t warm_start;    /* nonzero: start from the free entries of d_u instead of 0         */
 } soptx_cg_opts;
 
 typedef struct {
     int32_t iterations;    /* CG steps taken                                                   */
     int32_t converged;     /* 1 when the residual test was met                                 */
-    double rel_residual;   /* ||r_free|| / ||r_free at the start|| at the last check           */
+    double rel_residual;   /* ||r_free|| / ||f_free - K_fd u_d|| at the last check             */
 } soptx_cg_result;
 
 /*
  * K u = f on the free dofs, u fixed where d_fixed[dof] != 0 (Dirichlet):
  * Jacobi-preconditioned conjugate gradients started from u = 0 on the free
- * dofs, so the right-hand side is f - K u_D on the free rows.
+ * dofs (or from the free entries of d_u with warm_start, e.g. the previous
+ * design's displacements in an optimisation loop); the residual is measured
+ * against the right-hand side f - K u_D on the free rows.
  *   d_vals  : device float64 [nnz], the assembled K
  *   d_fixed : device uint8 [ndof], nonzero marks a constrained dof
  *   d_f     : device float64 [ndof], the load (ignored on constrained dofs)
  *   d_u     : device float64 [ndof]; on entry the prescribed values on the
- *             constrained dofs (other entries ignored), on exit the solution
+ *             constrained dofs (and the initial guess elsewhere with
+ *             warm_start, else ignored), on exit the solution
  * Runs on `stream` and returns when done: the host reads the residual back
  * every opts->check_every steps.  The first call on a mesh allocates its CG
  * vectors (5 ndof doubles), kept until soptx_mesh_destroy.  Sums are taken in

@@ -243,3 +243,90 @@ def solve_dirichlet(rowptr, cols, vals, fixed, f, u_fixed):
     rhs = np.asarray(f, np.float64)[free] - K[free][:, fixed] @ u[fixed]
     u[free] = spla.spsolve(K[free][:, free].tocsc(), rhs)
     return u
+
+
+# ---------------------------------------------------------------- after the sensitivities (Sec. 2.3-2.4)
+
+def filter_weights(centroids, rmin):
+    """H_ij = max(0, rmin - |c_i - c_j|) (Sec. 2.4), by brute force over all
+    pairs, row by row; returns a scipy CSR matrix."""
+    import scipy.sparse as sp
+    c = np.asarray(centroids, np.float64)
+    rows, cols, vals = [], [], []
+    for i in range(len(c)):
+        dist = np.sqrt(((c - c[i]) ** 2).sum(axis=1))
+        j = np.nonzero(dist < rmin)[0]
+        rows.append(np.full(len(j), i))
+        cols.append(j)
+        vals.append(rmin - dist[j])
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(len(c), len(c)))
+
+
+def sensitivity_filter(H, rho, dc, gamma=1e-3):
+    """Sigmund's filter (Sec. 2.4): sum_j H_ij rho_j dc_j / (max(gamma, rho_i) sum_j H_ij)."""
+    return (H @ (rho * dc)) / (np.maximum(gamma, rho) * np.asarray(H.sum(axis=1)).ravel())
+
+
+def density_filter(H, vol, x):
+    """Density filter (Sec. 2.4): sum_j H_ij v_j x_j / sum_j H_ij v_j."""
+    return (H @ (vol * x)) / (H @ vol)
+
+
+def density_filter_grad(H, vol, g):
+    """The density filter's chain rule (Sec. 2.4):
+    d psi / d x_j = sum_i H_ij v_j / (sum_k H_ik v_k) d psi / d rho~_i."""
+    return vol * (H.T @ (g / (H @ vol)))
+
+
+def heaviside(x, beta):
+    """Heaviside projection and its derivative (Sec. 2.4)."""
+    t = np.exp(-beta * x)
+    return 1.0 - t + x * np.exp(-beta), beta * t + np.exp(-beta)
+
+
+def oc_update(rho, dc, dv, vol, volfrac, move=0.2, eta=0.5, l_lo=0.0, l_hi=1e9, tol=1e-3):
+    """Optimality criteria (Sec. 2.3, Algorithm 1): rho_e B_e^eta clamped to
+    the move limits, B_e = -dc_e / (lambda dv_e), lambda by bisection on the
+    volume until (l_hi - l_lo) / (l_hi + l_lo) <= tol; rho_e B_e^eta is
+    evaluated as q_e lambda^-eta with q_e = rho_e (max(0, -dc_e) / dv_e)^eta.
+    Returns (rho_new, lambda)."""
+    rho = np.asarray(rho, np.float64)
+    q = rho * np.power(np.maximum(0.0, -np.asarray(dc)) / np.asarray(dv), eta)
+    lo_b, hi_b = np.maximum(0.0, rho - move), np.minimum(1.0, rho + move)
+    target = volfrac * np.sum(vol)
+    lo, hi, lmid = l_lo, l_hi, 0.5 * (l_lo + l_hi)
+    for _ in range(100):
+        if not (hi - lo) / (hi + lo) > tol:
+            break
+        lmid = 0.5 * (hi + lo)
+        x = np.minimum(hi_b, np.maximum(lo_b, q * lmid ** (-eta)))
+        if np.dot(vol, x) > target:
+            lo = lmid
+        else:
+            hi = lmid
+    return np.minimum(hi_b, np.maximum(lo_b, q * lmid ** (-eta))), lmid
+
+
+def oc_loop(cell, k, coords, cells, mat, fixed, f, rmin, volfrac, vol, centroids, max_iter=200, tol=1e-2,
+            move=0.2, eta=0.5, callback=None):
+    """Compliance minimisation by Algorithm 1 (Sec. 2.3) with the sensitivity
+    filter (Sec. 2.4), every step plain: K(rho) and u by the oracle's assembly
+    and direct constrained solve, dc and c by the oracle's sensitivity, the
+    filter and the OC update above; stops when max |rho_new - rho| <= tol.
+    Returns (rho, history [(c, change)])."""
+    H = filter_weights(centroids, rmin)
+    x = np.full(len(cells), float(volfrac))
+    hist = []
+    for it in range(max_iter):
+        rp, ci, v, ndof = assemble(cell, k, coords, cells, mat, x)
+        u = solve_dirichlet(rp, ci, v, fixed, f, np.zeros(ndof))
+        dc, s, c = sensitivity(cell, k, coords, cells, mat, x, u)
+        xnew, lam = oc_update(x, sensitivity_filter(H, x, dc), vol, vol, volfrac, move, eta)
+        change = float(np.abs(xnew - x).max())
+        hist.append((float(c), change))
+        if callback:
+            callback(it, hist[-1])
+        x = xnew
+        if change <= tol:
+            break
+    return x, hist

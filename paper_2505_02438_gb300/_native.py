@@ -28,11 +28,17 @@ class Material(ctypes.Structure):
 
 
 class CgOpts(ctypes.Structure):
-    _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("check_every", ctypes.c_int32)]
+    _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("warm_start", ctypes.c_int32)]
 
 
 class CgResult(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32), ("rel_residual", ctypes.c_double)]
+
+
+class OcOpts(ctypes.Structure):
+    _fields_ = [("volfrac", ctypes.c_double), ("move", ctypes.c_double), ("eta", ctypes.c_double),
+                ("l_lo", ctypes.c_double), ("l_hi", ctypes.c_double), ("tol", ctypes.c_double)]
 
 
 class ServerOpts(ctypes.Structure):
@@ -78,6 +84,14 @@ SIGNATURES = {
     "soptx_lattice_sensitivity_noalloc": (i32, [i32, P, P, ctypes.POINTER(Material), P, P, P, P, P]),
     "soptx_spmv": (i32, [P, P, P, P, P]),
     "soptx_solve_cg": (i32, [P, P, P, P, P, ctypes.POINTER(CgOpts), P, ctypes.POINTER(CgResult)]),
+    "soptx_filter_create": (i32, [i32, i64, P, P, ctypes.c_double, P, PP]),
+    "soptx_filter_info": (i32, [P, Pi64, Pi64]),
+    "soptx_filter_sensitivity": (i32, [P, P, P, P, P]),
+    "soptx_filter_density": (i32, [P, P, P, P]),
+    "soptx_filter_density_grad": (i32, [P, P, P, P]),
+    "soptx_filter_destroy": (i32, [P]),
+    "soptx_heaviside": (i32, [i64, ctypes.c_double, P, P, P, P]),
+    "soptx_oc_update": (i32, [i64, P, P, P, P, ctypes.POINTER(OcOpts), P, P, P]),
     "soptx_server_create": (i32, [ctypes.POINTER(ServerOpts), PP]),
     "soptx_serve_submit": (i32, [P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
     "soptx_serve_wait": (i32, [P, ctypes.c_uint64, i64, ctypes.POINTER(Result)]),

@@ -144,14 +144,18 @@ class Mesh:
                                    _stream(stream)))
         return y
 
-    def solve(self, vals, fixed, f, u_fixed=None, rtol=1e-10, max_iter=10000, check_every=10, stream=None):
+    def solve(self, vals, fixed, f, u_fixed=None, rtol=1e-10, max_iter=10000, check_every=10, u0=None,
+              stream=None):
         """K u = f on the free dofs (fixed: bool/uint8 [ndof]; u = u_fixed on the
-        constrained ones, 0 if not given) by Jacobi-preconditioned CG.
-        Returns (u, dict(iterations, converged, rel_residual))."""
+        constrained ones, 0 if not given) by Jacobi-preconditioned CG from 0, or
+        from the free entries of u0.  Returns (u, dict(iterations, converged,
+        rel_residual))."""
         fixed = fixed.to(device=self.device, dtype=torch.uint8).contiguous()
         u = torch.zeros(self.ndof, dtype=torch.float64, device=self.device) if u_fixed is None else \
             u_fixed.to(device=self.device, dtype=torch.float64).clone().contiguous()
-        opts = N.CgOpts(float(rtol), int(max_iter), int(check_every))
+        if u0 is not None:
+            u = torch.where(fixed.bool(), u, u0.to(device=self.device, dtype=torch.float64)).contiguous()
+        opts = N.CgOpts(float(rtol), int(max_iter), int(check_every), int(u0 is not None))
         res = N.CgResult()
         N.check(N.lib().soptx_solve_cg(self._h, _dptr(vals, torch.float64, self.nnz, "vals"),
                                        _dptr(fixed, torch.uint8, self.ndof, "fixed"),

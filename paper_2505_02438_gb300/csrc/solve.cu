@@ -364,9 +364,27 @@ soptx_status soptx_solve_cg(soptx_mesh m, const double *d_vals, const uint8_t *d
     if (e != cudaSuccess) return cuda_fail(e, "soptx_solve_cg");
     if (bad_h) SOPTX_FAIL(SOPTX_EINVAL, "a free dof has a non-positive diagonal (no element touches it?)");
 
-    // start: u = u_D, r = f - K u_D on the free rows, z = p = r / diag
-    k_cg_zero_free<<<cgrid, kCgThreads, 0, st>>>(h.ndof, d_fixed, d_u);
-    e = cudaGetLastError();
+    // the scale of the residual test: ||f - K u_D|| on the free rows
+    double rr0 = 0.0;
+    // z = u_D on the constrained dofs, 0 on the free ones
+    e = cudaMemcpyAsync(z, d_u, h.ndof * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) {
+        k_cg_zero_free<<<cgrid, kCgThreads, 0, st>>>(h.ndof, d_fixed, z);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = launch_spmv(*m, d_vals, z, q, d_fixed, nullptr, nullptr, nullptr, nullptr, st);
+    if (e == cudaSuccess) {
+        k_cg_start<<<cgrid, kCgThreads, 0, st>>>(h.ndof, d_fixed, d_f, q, diag, r, z, pv, partial, counter, S + 2);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&rr0, S + 3, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "soptx_solve_cg");
+    // start: u = u_D and 0 (or the given guess) on the free rows, r = f - K u, z = p = r / diag
+    if (!o->warm_start) {
+        k_cg_zero_free<<<cgrid, kCgThreads, 0, st>>>(h.ndof, d_fixed, d_u);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = launch_spmv(*m, d_vals, d_u, q, d_fixed, nullptr, nullptr, nullptr, nullptr, st);
     if (e == cudaSuccess) {
         k_cg_start<<<cgrid, kCgThreads, 0, st>>>(h.ndof, d_fixed, d_f, q, diag, r, z, pv, partial, counter, S + 2);
@@ -374,16 +392,16 @@ soptx_status soptx_solve_cg(soptx_mesh m, const double *d_vals, const uint8_t *d
     }
     // k_cg_start wrote (r.z, r.r) to S[2], S[3]; move r.z into the ping-pong slot 0
     if (e == cudaSuccess) e = cudaMemcpyAsync(S, S + 2, sizeof(double), cudaMemcpyDeviceToDevice, st);
-    double rr0 = 0.0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&rr0, S + 3, sizeof(double), cudaMemcpyDeviceToHost, st);
+    double rr = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&rr, S + 3, sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "soptx_solve_cg");
     const double r0 = std::sqrt(rr0);
-    if (r0 == 0.0) {
+    if (r0 == 0.0 || std::sqrt(rr) <= o->rtol * r0) {
         res->converged = 1;
+        res->rel_residual = r0 == 0.0 ? 0.0 : std::sqrt(rr) / r0;
         return SOPTX_OK;
     }
-    double rr = rr0;
     int it = 0;
     while (it < o->max_iter) {
         const int par = it & 1;

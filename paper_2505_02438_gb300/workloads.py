@@ -258,3 +258,20 @@ def serving_stream(n_jobs=64, iters=8, wl=5, scale=1.0):
 def poisson_arrivals(n, rate_per_s, wl=5):
     """Arrival times (seconds) of n requests at the given Poisson rate."""
     return np.cumsum(rng(wl, 3).exponential(1.0 / rate_per_s, size=n))
+
+
+def cantilever_3d_oc(nx=60, ny=20, nz=4):
+    """The 3D cantilever of the paper's Sec. 5.4: a box of nx x ny x nz unit
+    hexahedra, the x = 0 face fixed, a downward load (-1 along y) on every node
+    of the bottom edge of the right end (x = nx, y = 0).  Returns
+    (workload, fixed dof mask [ndof] bool, load [ndof]) with dofs
+    node-interleaved and the vertex lattice as the node numbering."""
+    coords, cells = structured_hex(nx, ny, nz)
+    wl = Workload("cantilever3d_%dx%dx%d" % (nx, ny, nz), "hex", 1, coords, cells, rho=np.full(len(cells), 0.3),
+                  seed_base=8)
+    ndof = 3 * len(coords)
+    fixed = np.repeat(coords[:, 0] < 1e-9, 3)
+    f = np.zeros(ndof)
+    tip = np.nonzero((coords[:, 0] > nx - 1e-9) & (coords[:, 1] < 1e-9))[0]
+    f[3 * tip + 1] = -1.0
+    return wl, fixed, f

@@ -667,3 +667,84 @@ def test_spmv_matches_dense_product():
         K[r, ci[rp[r]:rp[r + 1]]] = v[rp[r]:rp[r + 1]]
     x = np.random.default_rng(1).standard_normal(ndof)
     np.testing.assert_allclose(oracle.spmv(rp, ci, v, x), K @ x, rtol=0, atol=1e-13 * np.abs(K).sum(1).max())
+
+
+# ---------------------------------------------------------------- filters and the OC update (NEXT rows f2, f3)
+
+def _centroids(cell, coords, cells):
+    return np.asarray(coords)[np.asarray(cells)].mean(axis=1)
+
+
+def test_filter_weights_symmetric_with_rmin_diagonal():
+    coords, cells = W.kuhn_tets(4, 3, 2, 0.15, np.random.default_rng(2))
+    H = oracle.filter_weights(_centroids("tet", coords, cells), 1.3).toarray()
+    np.testing.assert_allclose(H, H.T, rtol=0, atol=0)
+    np.testing.assert_allclose(np.diag(H), 1.3)
+    assert np.all(H >= 0.0)
+
+
+def test_density_filter_keeps_constants_and_its_chain_rule_is_the_adjoint():
+    """rho~ of a constant field is that constant; <g, F x> = <F^T g, x>."""
+    coords, cells = W.triangle_grid(9, 6, 0.2, np.random.default_rng(3))
+    cen = _centroids("tri", coords, cells)
+    vol = np.random.default_rng(4).uniform(0.3, 0.6, len(cells))
+    H = oracle.filter_weights(cen, 2.2)
+    np.testing.assert_allclose(oracle.density_filter(H, vol, np.full(len(cells), 0.37)), 0.37, rtol=1e-15)
+    g, x = np.random.default_rng(5).standard_normal((2, len(cells)))
+    lhs = g @ oracle.density_filter(H, vol, x)
+    rhs = oracle.density_filter_grad(H, vol, g) @ x
+    assert abs(lhs - rhs) <= 1e-13 * (np.abs(g).sum() * np.abs(x).max())
+
+
+def test_sensitivity_filter_constant_field():
+    """With rho = 1 and dc constant the weighted average returns dc."""
+    coords, cells = W.structured_quad(8, 5)
+    H = oracle.filter_weights(_centroids("quad", coords, cells), 1.8)
+    out = oracle.sensitivity_filter(H, np.ones(len(cells)), np.full(len(cells), -2.5))
+    np.testing.assert_allclose(out, -2.5, rtol=1e-15)
+
+
+def test_heaviside_derivative_and_small_beta_limit():
+    x = np.linspace(0.0, 1.0, 11)
+    for beta in (1.0, 8.0):
+        y, dy = oracle.heaviside(x, beta)
+        h = 1e-6
+        fd = (oracle.heaviside(x + h, beta)[0] - oracle.heaviside(x - h, beta)[0]) / (2 * h)
+        np.testing.assert_allclose(dy, fd, rtol=1e-7, atol=1e-9)
+        assert abs(y[0]) < 1e-15 and abs(y[-1] - 1.0) < 1e-15
+    np.testing.assert_allclose(oracle.heaviside(x, 1e-9)[0], x, atol=1e-9)
+
+
+def test_oc_update_meets_volume_and_move_limits():
+    g = np.random.default_rng(6)
+    n = 500
+    rho = g.uniform(0.05, 1.0, n)
+    dc = -g.uniform(0.1, 5.0, n)
+    vol = g.uniform(0.5, 1.5, n)
+    new, lam = oracle.oc_update(rho, dc, vol, vol, 0.4, move=0.2, eta=0.5)
+    assert np.all(new >= np.maximum(0, rho - 0.2) - 1e-15) and np.all(new <= np.minimum(1, rho + 0.2) + 1e-15)
+    # the volume sits at the target to the bisection's tolerance
+    tight, _ = oracle.oc_update(rho, dc, vol, vol, 0.4, tol=1e-12)
+    assert abs(np.dot(vol, tight) / vol.sum() - 0.4) < 1e-9
+    assert abs(np.dot(vol, new) / vol.sum() - 0.4) < 5e-3
+    # cells strictly inside their bounds follow rho B^eta at the returned multiplier
+    inside = (new > np.maximum(0, rho - 0.2) + 1e-12) & (new < np.minimum(1, rho + 0.2) - 1e-12)
+    np.testing.assert_allclose(new[inside], rho[inside] * np.sqrt(-dc[inside] / (lam * vol[inside])), rtol=1e-13)
+
+
+def test_oc_loop_reproduces_the_papers_3d_cantilever():
+    """Algorithm 1 with the sensitivity filter on the paper's 3D cantilever
+    (Sec. 5.4: 60x20x4 hexahedra, volume fraction 0.3, r = 1.5): the paper
+    prints c = 2063.5625 after 54 iterations (Sec. 5.4-5.6); the stored
+    trajectory (tests/golden/make_cantilever3d_oc.py) is this loop's."""
+    with open(os.path.join(GOLDEN, "paper_cantilever3d.json")) as fh:
+        paper = json.load(fh)["60x20x4"]
+    with open(os.path.join(GOLDEN, "cantilever3d_60x20x4_oc.json")) as fh:
+        stored = json.load(fh)
+    wl, fixed, f = W.cantilever_3d_oc(60, 20, 4)
+    assert 3 * len(wl.coords) == paper["dofs"] and len(wl.cells) == paper["cells"]
+    x, hist = oracle.oc_loop("hex", 1, wl.coords, wl.cells, (1.0, 1e-9, 0.3, 3.0, 0), fixed, f, paper["rmin"],
+                             paper["volfrac"], np.ones(len(wl.cells)), _centroids("hex", wl.coords, wl.cells))
+    assert len(hist) == paper["iterations"]
+    assert abs(hist[-1][0] - paper["c"]) <= 5e-5
+    np.testing.assert_allclose([h[0] for h in hist], stored["c"], rtol=1e-10)
