@@ -187,7 +187,7 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
         else B += (int64_t)bytes;
     }
     if (s == SOPTX_OK) {
-        d.scratch_len = std::max<int64_t>(std::max<int64_t>(sensitivity_scratch_len(*m), lattice_sens_grid(h.nc)), 1);
+        d.scratch_len = std::max<int64_t>(std::max<int64_t>(sensitivity_scratch_len(*m), lattice_partials_len(h)), 1);
         cudaError_t e = dev_alloc((void **)&d.scratch, d.scratch_len * sizeof(double));
         if (e != cudaSuccess) { cudaGetLastError(); s = cuda_status(e, "scratch"); }
         else B += d.scratch_len * (int64_t)sizeof(double);
@@ -221,8 +221,10 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
         std::vector<float2> sectors;
         // FP32 element matrices carry their rounding into K^0: zeros hold to about 2^-24 there
         const double zero_tol = prec == SOPTX_ELEM_FP32 ? 1e-5 : 1e-13;
-        if (s == SOPTX_OK && !g_no_sectors.load() && build_lattice_sectors(h.dim, K0, zero_tol, sectors))
+        if (s == SOPTX_OK && !g_no_sectors.load() && build_lattice_sectors(h.dim, K0, zero_tol, sectors)) {
             s = upload(&d.sectors, sectors, st, B, "sectors");
+            h.sectors = sectors;
+        }
         if (s == SOPTX_OK) {
             cudaError_t e = dev_alloc((void **)&d.Edf, (size_t)std::max<int64_t>(h.nc, 1) * sizeof(float2));
             if (e != cudaSuccess) { cudaGetLastError(); s = cuda_status(e, "element moduli"); }

@@ -75,6 +75,7 @@ struct HostMesh {
     std::vector<double> xcell;          // [nc][nvc][dim] corner coordinates (non-affine meshes)
     bool lattice = false;               // order-1 box lattice in canonical numbering
     int lat_n[3] = {1, 1, 1};           // cells per axis
+    std::vector<float2> sectors;        // [2^d][d][d] Walsh-sector blocks of K^0 (empty: no split)
     int max_deg = 0;
 };
 
@@ -150,6 +151,9 @@ bool build_lattice_sectors(int dim, const std::vector<double> &K0, double zero_t
 cudaError_t launch_lattice_sensitivity(const soptx_mesh_s &m, const double *rho, const double *u, double *out,
                                        double *c, const double *gscale, cudaStream_t st);
 int lattice_sens_grid(int64_t nc);
+int lattice_partials_len(const HostMesh &h);
+cudaError_t launch_lattice_step(const soptx_mesh_s &m, const double *rho, const double *u, double *vals, double *dc,
+                                double *c, cudaStream_t st);
 cudaError_t launch_gather(const soptx_mesh_s &m, const double *rho, const double *u, double *vals, double *dc,
                           double *c, const double *gscale, cudaStream_t st);
 int gather_finalize_grid(int64_t nc);

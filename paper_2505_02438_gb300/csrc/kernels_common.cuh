@@ -70,6 +70,13 @@ __device__ __forceinline__ double warp_sum(double v)
 struct Material;
 SimpParams simp_params(const Material &m);
 
+// Walsh-sector blocks B_c[i][j] of a box element's K^0 as float pairs, passed
+// to a kernel by value: kernel parameters live in the constant bank, which the
+// FP32 instructions read as operands without a shared-memory load.
+template <int D> struct SectorTable {
+    float2 b[(1 << D) * D * D];
+};
+
 // Sum of `mine` over the grid into *c, deterministically: each block writes its
 // partial (a fixed-order butterfly per warp, then the warps in order), the last block to finish (an
 // atomic ticket on *counter) adds all partials in index order and resets the

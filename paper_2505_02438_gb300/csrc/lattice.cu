@@ -157,11 +157,11 @@ __device__ __forceinline__ float2 load_corner(const float2 *__restrict__ Edf, co
 #define SOPTX_LATTICE_MINBLOCKS 4
 #endif
 template <int WPB>
-__global__ void __launch_bounds__(WPB * 32, SOPTX_LATTICE_MINBLOCKS)
-k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restrict__ node_off,
-                    const float2 *__restrict__ Edf, const float2 *__restrict__ kappa_g,
-                    const double *__restrict__ K0, const double *__restrict__ rho, SimpParams sp,
-                    double *__restrict__ vals)
+__device__ __forceinline__ void
+lattice_assemble3_warps(int nx, int ny, int nz, int64_t nn, const int64_t *__restrict__ node_off,
+                        const float2 *__restrict__ Edf, const float2 *__restrict__ kappa_g,
+                        const double *__restrict__ K0, const double *__restrict__ rho, SimpParams sp,
+                        double *__restrict__ vals)
 {
     const int lane = threadIdx.x & 31;
     const int dl = lane < 27 ? lane : 26;
@@ -302,6 +302,16 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restric
     if (lane == 0) bulk_wait_all();
 }
 
+template <int WPB>
+__global__ void __launch_bounds__(WPB * 32, SOPTX_LATTICE_MINBLOCKS)
+k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restrict__ node_off,
+                    const float2 *__restrict__ Edf, const float2 *__restrict__ kappa_g,
+                    const double *__restrict__ K0, const double *__restrict__ rho, SimpParams sp,
+                    double *__restrict__ vals)
+{
+    lattice_assemble3_warps<WPB>(nx, ny, nz, nn, node_off, Edf, kappa_g, K0, rho, sp, vals);
+}
+
 // 2D: three nodes per warp, lanes 9g .. 9g+8 serve node g, one lane per offset.
 template <int WPB>
 __global__ void __launch_bounds__(WPB * 32)
@@ -408,21 +418,25 @@ __host__ __device__ constexpr bool sector_zero(int c, int i, int j)
 // components i.  With w_{t,i} = sum_a f_t(a) u_{a,i} (a fast Walsh transform),
 //     u_e^T K^0 u_e = sum_c sum_ij w_{c^e_i, i} B_c[i][j] w_{c^e_j, j},
 // B_c[i][j] = f_{c^e_i}^T K^0_{ij} f_{c^e_j} / 4^d, each term of the outer sum
-// a non-negative energy.  One thread per cell, float-pair arithmetic.
+// a non-negative energy.  One thread per cell, float-pair arithmetic; the
+// blocks come in as kernel parameters.
+#ifndef SOPTX_SENS_MINB
+#define SOPTX_SENS_MINB 8
+#endif
+constexpr int kSensThreads = 128;
+
+// Cells first, first + stride, ... of the lattice: writes
+// dc_e = g E'(rho_e) u_e^T K^0 u_e and returns this thread's share of
+// sum_e E(rho_e) u_e^T K^0 u_e.
 template <int D>
-__global__ void __launch_bounds__(128, 4)
-k_lattice_sens(int nx, int ny, int nz, int64_t nc, const double *__restrict__ rho, const double *__restrict__ u,
-               SimpParams sp, const float2 *__restrict__ Bg, const double *__restrict__ gscale,
-               double *__restrict__ out, double *__restrict__ partial, unsigned *__restrict__ counter,
-               double *__restrict__ c)
+__device__ __forceinline__ double lattice_sens_cells(int64_t first, int64_t stride, int nx, int ny, int64_t nc,
+                                                     const double *__restrict__ rho, const double *__restrict__ u,
+                                                     const SimpParams &sp, const SectorTable<D> &B, double g,
+                                                     double *__restrict__ out)
 {
     constexpr int NCR = 1 << D;
-    __shared__ float2 Bs[NCR * D * D];
-    for (int t = threadIdx.x; t < NCR * D * D; t += blockDim.x) Bs[t] = Bg[t];
-    __syncthreads();
-    const double g = gscale ? *gscale : -1.0;
     double mine = 0.0;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc; e += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t e = first; e < nc; e += stride) {
         const uint32_t ue = (uint32_t)e;
         const int ex = (int)(ue % (uint32_t)nx);
         const uint32_t r = ue / (uint32_t)nx;
@@ -460,7 +474,7 @@ k_lattice_sens(int nx, int ny, int nz, int64_t nc, const double *__restrict__ rh
 #pragma unroll
                 for (int j = i; j < D; j++) {
                     if (sector_zero(c, i, j)) continue;
-                    const float2 bb = Bs[(c * D + i) * D + j];     // off-diagonal entries pre-doubled
+                    const float2 bb = B.b[(c * D + i) * D + j];     // off-diagonal entries pre-doubled
                     const df t = df_mul_raw(df_mul_raw(x[i], x[j]), df{bb.x, bb.y});
                     float err;
                     two_sum(S, t.h, S, err);
@@ -474,15 +488,65 @@ k_lattice_sens(int nx, int ny, int nz, int64_t nc, const double *__restrict__ rh
         out[e] = g * simp_dE(sp, re) * sd;
         mine += simp_E(sp, re) * sd;
     }
+    return mine;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kSensThreads, SOPTX_SENS_MINB)
+k_lattice_sens(int nx, int ny, int64_t nc, const double *__restrict__ rho, const double *__restrict__ u,
+               SimpParams sp, const SectorTable<D> B, const double *__restrict__ gscale,
+               double *__restrict__ out, double *__restrict__ partial, unsigned *__restrict__ counter,
+               double *__restrict__ c)
+{
+    const double g = gscale ? *gscale : -1.0;
+    const double mine = lattice_sens_cells<D>(blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                                              (int64_t)gridDim.x * blockDim.x, nx, ny, nc, rho, u, sp, B, g, out);
+    if (c) grid_sum_last_block(mine, partial, counter, c);
+}
+
+// One pass of the 3D step: each warp assembles its node chunks, then the
+// block's threads take the cells of the sensitivity pass, so the cell work
+// fills the issue slots the assembly leaves and the two tails overlap.  dc_e
+// has the compliance sign (-E'), as from soptx_sensitivity.
+template <int WPB>
+__global__ void __launch_bounds__(WPB * 32, SOPTX_LATTICE_MINBLOCKS)
+k_lattice_step3(int nx, int ny, int nz, int64_t nn, int64_t nc, const int64_t *__restrict__ node_off,
+                const float2 *__restrict__ Edf, const float2 *__restrict__ kappa_g, const double *__restrict__ K0,
+                const double *__restrict__ rho, const double *__restrict__ u, SimpParams sp,
+                const SectorTable<3> B, double *__restrict__ vals, double *__restrict__ dc,
+                double *__restrict__ partial, unsigned *__restrict__ counter, double *__restrict__ c)
+{
+    lattice_assemble3_warps<WPB>(nx, ny, nz, nn, node_off, Edf, kappa_g, K0, rho, sp, vals);
+    const double mine = lattice_sens_cells<3>(blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                                              (int64_t)gridDim.x * blockDim.x, nx, ny, nc, rho, u, sp, B, -1.0, dc);
     if (c) grid_sum_last_block(mine, partial, counter, c);
 }
 
 }  // namespace
 
-constexpr int kSensThreads = 128;
 int lattice_sens_grid(int64_t nc)
 {
-    return (int)std::max<int64_t>(1, std::min<int64_t>((nc + kSensThreads - 1) / kSensThreads, 152 * 12));
+    return (int)std::max<int64_t>(1, std::min<int64_t>((nc + kSensThreads - 1) / kSensThreads, 152 * 8));
+}
+
+constexpr int kAsmWarps = 8;
+static int lattice_assemble3_grid(int64_t nn)
+{
+    const int64_t chunks = (nn + kChunk - 1) / kChunk;
+    return (int)std::max<int64_t>(1, std::min<int64_t>((chunks + kAsmWarps - 1) / kAsmWarps, 152 * 4));
+}
+
+int lattice_partials_len(const HostMesh &h)
+{
+    return std::max(lattice_sens_grid(h.nc), h.dim == 3 ? lattice_assemble3_grid(h.nn) : 1);
+}
+
+template <int D>
+static SectorTable<D> sector_table(const std::vector<float2> &v)
+{
+    SectorTable<D> B;
+    for (int t = 0; t < (1 << D) * D * D; t++) B.b[t] = v[t];
+    return B;
 }
 
 cudaError_t launch_lattice_sensitivity(const soptx_mesh_s &m, const double *rho, const double *u, double *out,
@@ -490,13 +554,14 @@ cudaError_t launch_lattice_sensitivity(const soptx_mesh_s &m, const double *rho,
 {
     const auto &h = m.h;
     const int grid = lattice_sens_grid(h.nc);
+    if ((int)h.sectors.size() != (h.dim << h.dim) * h.dim) return cudaErrorInvalidValue;
     if (h.dim == 3)
-        k_lattice_sens<3><<<grid, kSensThreads, 0, st>>>(h.lat_n[0], h.lat_n[1], h.lat_n[2], h.nc, rho, u,
-                                                         simp_params(m.mat), (const float2 *)m.d.sectors, gscale, out,
-                                                         m.d.scratch, m.d.counter, c);
+        k_lattice_sens<3><<<grid, kSensThreads, 0, st>>>(h.lat_n[0], h.lat_n[1], h.nc, rho, u, simp_params(m.mat),
+                                                         sector_table<3>(h.sectors), gscale, out, m.d.scratch,
+                                                         m.d.counter, c);
     else
-        k_lattice_sens<2><<<grid, kSensThreads, 0, st>>>(h.lat_n[0], h.lat_n[1], 1, h.nc, rho, u, simp_params(m.mat),
-                                                         (const float2 *)m.d.sectors, gscale, out, m.d.scratch,
+        k_lattice_sens<2><<<grid, kSensThreads, 0, st>>>(h.lat_n[0], h.lat_n[1], h.nc, rho, u, simp_params(m.mat),
+                                                         sector_table<2>(h.sectors), gscale, out, m.d.scratch,
                                                          m.d.counter, c);
     return cudaGetLastError();
 }
@@ -504,7 +569,7 @@ cudaError_t launch_lattice_sensitivity(const soptx_mesh_s &m, const double *rho,
 // Sector blocks B_c[i][j] of a box element's K^0 (see k_lattice_sens), the
 // off-diagonal ones doubled (only i <= j is summed), the entries that vanish
 // on every box (sector_zero) checked against zero_tol relative to the largest
-// sector entry; returns
+// sector entry and stored as zeros; returns
 // false when K^0 does not split into the 2^d sectors (then the general
 // sensitivity kernel is used).
 bool build_lattice_sectors(int dim, const std::vector<double> &K0, double zero_tol, std::vector<float2> &B)
@@ -537,7 +602,8 @@ bool build_lattice_sectors(int dim, const std::vector<double> &K0, double zero_t
     for (int c = 0; c < ncr; c++)
         for (int i = 0; i < dim; i++)
             for (int j = 0; j < dim; j++) {
-                const double x = (i == j ? 1.0 : 2.0) * norm *
+                // the entries that vanish on every box are stored as exact zeros
+                const double x = sector_zero(c, i, j) ? 0.0 : (i == j ? 1.0 : 2.0) * norm *
                                  F[(((size_t)(c ^ (1 << i)) * dim + i) * ncr + (c ^ (1 << j))) * dim + j];
                 const float hh = (float)x;
                 B[((size_t)c * dim + i) * dim + j] = make_float2(hh, (float)(x - (double)hh));
@@ -554,10 +620,9 @@ cudaError_t launch_lattice_assemble(const soptx_mesh_s &m, const double *rho, do
     k_simp_df<<<std::max(egrid, 1), eb, 0, st>>>(h.nc, rho, sp, (float2 *)m.d.Edf);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    constexpr int WPB = 8;
+    constexpr int WPB = kAsmWarps;
     if (h.dim == 3) {
-        const int64_t chunks = (h.nn + kChunk - 1) / kChunk;
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((chunks + WPB - 1) / WPB, 152 * 4));
+        const int grid = lattice_assemble3_grid(h.nn);
         k_lattice_assemble3<WPB><<<grid, WPB * 32, 0, st>>>(h.lat_n[0], h.lat_n[1], h.lat_n[2], h.nn, m.d.node_off,
                                                             (const float2 *)m.d.Edf, (const float2 *)m.d.kappa,
                                                             m.d.K0, rho, sp, vals);
@@ -568,6 +633,32 @@ cudaError_t launch_lattice_assemble(const soptx_mesh_s &m, const double *rho, do
                                                             (const float2 *)m.d.Edf, (const float2 *)m.d.kappa,
                                                             m.d.K0, rho, sp, vals);
     }
+    return cudaGetLastError();
+}
+
+// Assembly and sensitivity of one step.  In 3D with the sector split, one
+// launch does both (after the element moduli); otherwise the two passes run
+// back to back.
+cudaError_t launch_lattice_step(const soptx_mesh_s &m, const double *rho, const double *u, double *vals, double *dc,
+                                double *c, cudaStream_t st)
+{
+    const auto &h = m.h;
+    if (h.dim != 3 || (int)h.sectors.size() != (3 << 3) * 3 || h.nn == 0) {
+        cudaError_t err = launch_lattice_assemble(m, rho, vals, st);
+        if (err != cudaSuccess) return err;
+        return launch_lattice_sensitivity(m, rho, u, dc, c, nullptr, st);
+    }
+    const SimpParams sp = simp_params(m.mat);
+    const int eb = 256;
+    const int egrid = (int)std::min<int64_t>((h.nc + eb - 1) / eb, 152 * 8);
+    k_simp_df<<<std::max(egrid, 1), eb, 0, st>>>(h.nc, rho, sp, (float2 *)m.d.Edf);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    constexpr int WPB = kAsmWarps;
+    k_lattice_step3<WPB><<<lattice_assemble3_grid(h.nn), WPB * 32, 0, st>>>(
+        h.lat_n[0], h.lat_n[1], h.lat_n[2], h.nn, h.nc, m.d.node_off, (const float2 *)m.d.Edf,
+        (const float2 *)m.d.kappa, m.d.K0, rho, u, sp, sector_table<3>(h.sectors), vals, dc, m.d.scratch,
+        m.d.counter, c);
     return cudaGetLastError();
 }
 

@@ -38,11 +38,6 @@ constexpr int kNaMaxDevices = 64;
 static double *g_partials_ptr[kNaMaxDevices];
 static std::mutex g_partials_mu;
 
-// Sector blocks of the box element, passed by value (no device buffer).
-template <int D> struct SectorTable {
-    float2 b[(1 << D) * D * D];
-};
-
 // The cell computation of k_lattice_sens: Walsh transform of each displacement
 // component over the 2^d corners, then the 2^d sector quadratic forms.
 template <int D>
