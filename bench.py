@@ -471,22 +471,22 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    # One step is the public call that does both passes (soptx_assemble_and_sensitivity):
-    # a single launch after the element moduli on the 3D box lattice, the fused
-    # gather on the general path.  The 2D lattice runs its two kernels back to back.
-    single_pass = mesh.path != "lattice" or wl.dim == 3
+    # The box-lattice path runs assembly and sensitivity as separate kernels
+    # (timed apart); the general path does both in one fused gather pass.
+    fused = mesh.path != "lattice"
 
     def step_calls(evs):
-        evs[0].record(stream)
-        mesh.step(rho, u, vals, dc, c)
-        evs[1].record(stream)
-
-    def split_calls(evs):
-        evs[0].record(stream)
-        mesh.assemble_K(rho, vals)
-        evs[1].record(stream)
-        mesh.sensitivity(rho, u, dc, c)
-        evs[2].record(stream)
+        if fused:
+            evs[0].record(stream)
+            mesh.step(rho, u, vals, dc, c)
+            evs[1].record(stream)
+            evs[2].record(stream)
+        else:
+            evs[0].record(stream)
+            mesh.assemble_K(rho, vals)
+            evs[1].record(stream)
+            mesh.sensitivity(rho, u, dc, c)
+            evs[2].record(stream)
 
     warm_ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     for _ in range(args.warmup):
@@ -508,22 +508,11 @@ def run_ours(args, rank, world, local_rank):
         if world > 1:
             torch.distributed.barrier()
         wall = time.perf_counter() - wall0
-    step_ms = sum(e[0].elapsed_time(e[1]) for e in ev)
-    step_ms = max_over_ranks([step_ms], world, dev)[0]
+    asm_ms = sum(e[0].elapsed_time(e[1]) for e in ev)
+    sens_ms = sum(e[1].elapsed_time(e[2]) for e in ev)
+    step_ms = asm_ms + sens_ms
+    step_ms, asm_ms, sens_ms = max_over_ranks([step_ms, asm_ms, sens_ms], world, dev)
     clocks = sampler.summary()
-
-    # the two separate calls (soptx_assemble_K, soptx_sensitivity), timed apart
-    n_split = min(K, 500)
-    sev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(n_split)]
-    for _ in range(max(args.warmup, 3)):
-        split_calls(warm_ev)
-    for k in range(n_split):
-        flush.zero_()
-        split_calls(sev[k])
-    torch.cuda.synchronize()
-    asm_ms = sum(e[0].elapsed_time(e[1]) for e in sev)
-    sens_ms = sum(e[1].elapsed_time(e[2]) for e in sev)
-    asm_ms, sens_ms = max_over_ranks([asm_ms, sens_ms], world, dev)
 
     # end to end: pinned host inputs -> device, step, dc and c back to the host
     n_e2e = min(K, 200)
@@ -552,19 +541,15 @@ def run_ours(args, rank, world, local_rank):
         return
     ab = algorithmic_bytes(wl, nnz, ndof)
     peak, peak_kind = peaks()
-    if single_pass:
-        # one pass does both: its algorithmic bytes are the whole step's (the
-        # step's time also holds the short element-moduli launch)
-        achieved = ab["step"] / (step_ms / K / 1e3) / 1e9
-        if mesh.path == "lattice":
-            kernel_name, kernel_file = "k_lattice_step3", "lattice.cu"
-        else:
-            kernel_name = "k_gather_rows" if (wl.dim, mesh.nb) in ((3, 10), (3, 8), (2, 10), (2, 4)) else "k_gather_nodes"
-            kernel_file = "gather.cu"
-        alg_launch = ab["step"]
+    asm_avg_s = asm_ms / K / 1e3
+    if fused:
+        # one pass does both: its algorithmic bytes are the whole step's
+        achieved = ab["step"] / asm_avg_s / 1e9
+        kernel_name = "k_gather_rows" if (wl.dim, mesh.nb) in ((3, 10), (3, 8), (2, 10), (2, 4)) else "k_gather_nodes"
+        kernel_file, alg_launch = "gather.cu", ab["step"]
     else:
-        achieved = ab["assemble"] / (asm_ms / n_split / 1e3) / 1e9
-        kernel_name, kernel_file, alg_launch = "k_lattice_assemble2", "lattice.cu", ab["assemble"]
+        achieved = ab["assemble"] / asm_avg_s / 1e9
+        kernel_name, kernel_file, alg_launch = "k_lattice_assemble3", "lattice.cu", ab["assemble"]
     traffic = traffic_record(kernel_file, kernel_name)
     value = job_rate(nnz, world, K, step_ms) / 1e9
     line = {
@@ -576,8 +561,7 @@ def run_ours(args, rank, world, local_rank):
                    "n_cells": nc, "elem_prec": args.elem_prec, "l2": "flushed (256 MiB write) between steps",
                    "parallelism": "replicas" if world > 1 else "single"},
         "sens_elems_per_s": job_rate(nc, world, K, step_ms),
-        "single_pass_step": single_pass, "setup_s": setup_s,
-        "separate_calls": {"assemble_ms": asm_ms / n_split, "sensitivity_ms": sens_ms / n_split, "steps": n_split},
+        "assemble_ms": asm_ms / K, "sensitivity_ms": sens_ms / K, "fused_step": fused, "setup_s": setup_s,
         "step_alg_bytes": ab["step"], "step_hbm_frac": ab["step"] / (step_ms / K / 1e3) / 1e9 / peak,
         "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
@@ -586,9 +570,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": job_rate(nnz, world, n_e2e, e2e_ms) / 1e9, "unit": "GNNZ/s",
                 "h2d_bytes_per_step": 8 * (nc + ndof), "d2h_bytes_per_step": 8 * (nc + 1),
                 "steps": n_e2e},
-        # lattice 3D: element moduli + the one-pass kernel; general path: moduli and u pairs, gather,
-        # finalize (+ sum of c); lattice 2D: moduli, assembly, sensitivity
-        "gpu_launches": (2 if mesh.path == "lattice" and wl.dim == 3 else 3) * K,
+        "gpu_launches": 3 * K,   # SIMP moduli, assembly (+ fused sensitivity), sensitivity or finalize (+ sum of c)
         "wall_s_timed_region": wall,
     }
     if args.elem_prec == "fp32":

@@ -187,7 +187,7 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
         else B += (int64_t)bytes;
     }
     if (s == SOPTX_OK) {
-        d.scratch_len = std::max<int64_t>(std::max<int64_t>(sensitivity_scratch_len(*m), lattice_partials_len(h)), 1);
+        d.scratch_len = std::max<int64_t>(std::max<int64_t>(sensitivity_scratch_len(*m), lattice_sens_grid(h.nc)), 1);
         cudaError_t e = dev_alloc((void **)&d.scratch, d.scratch_len * sizeof(double));
         if (e != cudaSuccess) { cudaGetLastError(); s = cuda_status(e, "scratch"); }
         else B += d.scratch_len * (int64_t)sizeof(double);

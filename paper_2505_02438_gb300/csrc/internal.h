@@ -151,9 +151,6 @@ bool build_lattice_sectors(int dim, const std::vector<double> &K0, double zero_t
 cudaError_t launch_lattice_sensitivity(const soptx_mesh_s &m, const double *rho, const double *u, double *out,
                                        double *c, const double *gscale, cudaStream_t st);
 int lattice_sens_grid(int64_t nc);
-int lattice_partials_len(const HostMesh &h);
-cudaError_t launch_lattice_step(const soptx_mesh_s &m, const double *rho, const double *u, double *vals, double *dc,
-                                double *c, cudaStream_t st);
 cudaError_t launch_gather(const soptx_mesh_s &m, const double *rho, const double *u, double *vals, double *dc,
                           double *c, const double *gscale, cudaStream_t st);
 int gather_finalize_grid(int64_t nc);

@@ -157,11 +157,11 @@ __device__ __forceinline__ float2 load_corner(const float2 *__restrict__ Edf, co
 #define SOPTX_LATTICE_MINBLOCKS 4
 #endif
 template <int WPB>
-__device__ __forceinline__ void
-lattice_assemble3_warps(int nx, int ny, int nz, int64_t nn, const int64_t *__restrict__ node_off,
-                        const float2 *__restrict__ Edf, const float2 *__restrict__ kappa_g,
-                        const double *__restrict__ K0, const double *__restrict__ rho, SimpParams sp,
-                        double *__restrict__ vals)
+__global__ void __launch_bounds__(WPB * 32, SOPTX_LATTICE_MINBLOCKS)
+k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restrict__ node_off,
+                    const float2 *__restrict__ Edf, const float2 *__restrict__ kappa_g,
+                    const double *__restrict__ K0, const double *__restrict__ rho, SimpParams sp,
+                    double *__restrict__ vals)
 {
     const int lane = threadIdx.x & 31;
     const int dl = lane < 27 ? lane : 26;
@@ -302,16 +302,6 @@ lattice_assemble3_warps(int nx, int ny, int nz, int64_t nn, const int64_t *__res
     if (lane == 0) bulk_wait_all();
 }
 
-template <int WPB>
-__global__ void __launch_bounds__(WPB * 32, SOPTX_LATTICE_MINBLOCKS)
-k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restrict__ node_off,
-                    const float2 *__restrict__ Edf, const float2 *__restrict__ kappa_g,
-                    const double *__restrict__ K0, const double *__restrict__ rho, SimpParams sp,
-                    double *__restrict__ vals)
-{
-    lattice_assemble3_warps<WPB>(nx, ny, nz, nn, node_off, Edf, kappa_g, K0, rho, sp, vals);
-}
-
 // 2D: three nodes per warp, lanes 9g .. 9g+8 serve node g, one lane per offset.
 template <int WPB>
 __global__ void __launch_bounds__(WPB * 32)
@@ -419,24 +409,22 @@ __host__ __device__ constexpr bool sector_zero(int c, int i, int j)
 //     u_e^T K^0 u_e = sum_c sum_ij w_{c^e_i, i} B_c[i][j] w_{c^e_j, j},
 // B_c[i][j] = f_{c^e_i}^T K^0_{ij} f_{c^e_j} / 4^d, each term of the outer sum
 // a non-negative energy.  One thread per cell, float-pair arithmetic; the
-// blocks come in as kernel parameters.
+// blocks arrive as kernel parameters (constant bank, read as instruction
+// operands); 64 registers, 8 blocks per SM.
 #ifndef SOPTX_SENS_MINB
 #define SOPTX_SENS_MINB 8
 #endif
-constexpr int kSensThreads = 128;
-
-// Cells first, first + stride, ... of the lattice: writes
-// dc_e = g E'(rho_e) u_e^T K^0 u_e and returns this thread's share of
-// sum_e E(rho_e) u_e^T K^0 u_e.
 template <int D>
-__device__ __forceinline__ double lattice_sens_cells(int64_t first, int64_t stride, int nx, int ny, int64_t nc,
-                                                     const double *__restrict__ rho, const double *__restrict__ u,
-                                                     const SimpParams &sp, const SectorTable<D> &B, double g,
-                                                     double *__restrict__ out)
+__global__ void __launch_bounds__(128, SOPTX_SENS_MINB)
+k_lattice_sens(int nx, int ny, int64_t nc, const double *__restrict__ rho, const double *__restrict__ u,
+               SimpParams sp, const SectorTable<D> B, const double *__restrict__ gscale,
+               double *__restrict__ out, double *__restrict__ partial, unsigned *__restrict__ counter,
+               double *__restrict__ c)
 {
     constexpr int NCR = 1 << D;
+    const double g = gscale ? *gscale : -1.0;
     double mine = 0.0;
-    for (int64_t e = first; e < nc; e += stride) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc; e += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t ue = (uint32_t)e;
         const int ex = (int)(ue % (uint32_t)nx);
         const uint32_t r = ue / (uint32_t)nx;
@@ -488,57 +476,15 @@ __device__ __forceinline__ double lattice_sens_cells(int64_t first, int64_t stri
         out[e] = g * simp_dE(sp, re) * sd;
         mine += simp_E(sp, re) * sd;
     }
-    return mine;
-}
-
-template <int D>
-__global__ void __launch_bounds__(kSensThreads, SOPTX_SENS_MINB)
-k_lattice_sens(int nx, int ny, int64_t nc, const double *__restrict__ rho, const double *__restrict__ u,
-               SimpParams sp, const SectorTable<D> B, const double *__restrict__ gscale,
-               double *__restrict__ out, double *__restrict__ partial, unsigned *__restrict__ counter,
-               double *__restrict__ c)
-{
-    const double g = gscale ? *gscale : -1.0;
-    const double mine = lattice_sens_cells<D>(blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
-                                              (int64_t)gridDim.x * blockDim.x, nx, ny, nc, rho, u, sp, B, g, out);
-    if (c) grid_sum_last_block(mine, partial, counter, c);
-}
-
-// One pass of the 3D step: each warp assembles its node chunks, then the
-// block's threads take the cells of the sensitivity pass, so the cell work
-// fills the issue slots the assembly leaves and the two tails overlap.  dc_e
-// has the compliance sign (-E'), as from soptx_sensitivity.
-template <int WPB>
-__global__ void __launch_bounds__(WPB * 32, SOPTX_LATTICE_MINBLOCKS)
-k_lattice_step3(int nx, int ny, int nz, int64_t nn, int64_t nc, const int64_t *__restrict__ node_off,
-                const float2 *__restrict__ Edf, const float2 *__restrict__ kappa_g, const double *__restrict__ K0,
-                const double *__restrict__ rho, const double *__restrict__ u, SimpParams sp,
-                const SectorTable<3> B, double *__restrict__ vals, double *__restrict__ dc,
-                double *__restrict__ partial, unsigned *__restrict__ counter, double *__restrict__ c)
-{
-    lattice_assemble3_warps<WPB>(nx, ny, nz, nn, node_off, Edf, kappa_g, K0, rho, sp, vals);
-    const double mine = lattice_sens_cells<3>(blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
-                                              (int64_t)gridDim.x * blockDim.x, nx, ny, nc, rho, u, sp, B, -1.0, dc);
     if (c) grid_sum_last_block(mine, partial, counter, c);
 }
 
 }  // namespace
 
+constexpr int kSensThreads = 128;
 int lattice_sens_grid(int64_t nc)
 {
     return (int)std::max<int64_t>(1, std::min<int64_t>((nc + kSensThreads - 1) / kSensThreads, 152 * 8));
-}
-
-constexpr int kAsmWarps = 8;
-static int lattice_assemble3_grid(int64_t nn)
-{
-    const int64_t chunks = (nn + kChunk - 1) / kChunk;
-    return (int)std::max<int64_t>(1, std::min<int64_t>((chunks + kAsmWarps - 1) / kAsmWarps, 152 * 4));
-}
-
-int lattice_partials_len(const HostMesh &h)
-{
-    return std::max(lattice_sens_grid(h.nc), h.dim == 3 ? lattice_assemble3_grid(h.nn) : 1);
 }
 
 template <int D>
@@ -620,9 +566,10 @@ cudaError_t launch_lattice_assemble(const soptx_mesh_s &m, const double *rho, do
     k_simp_df<<<std::max(egrid, 1), eb, 0, st>>>(h.nc, rho, sp, (float2 *)m.d.Edf);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    constexpr int WPB = kAsmWarps;
+    constexpr int WPB = 8;
     if (h.dim == 3) {
-        const int grid = lattice_assemble3_grid(h.nn);
+        const int64_t chunks = (h.nn + kChunk - 1) / kChunk;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((chunks + WPB - 1) / WPB, 152 * 4));
         k_lattice_assemble3<WPB><<<grid, WPB * 32, 0, st>>>(h.lat_n[0], h.lat_n[1], h.lat_n[2], h.nn, m.d.node_off,
                                                             (const float2 *)m.d.Edf, (const float2 *)m.d.kappa,
                                                             m.d.K0, rho, sp, vals);
@@ -633,32 +580,6 @@ cudaError_t launch_lattice_assemble(const soptx_mesh_s &m, const double *rho, do
                                                             (const float2 *)m.d.Edf, (const float2 *)m.d.kappa,
                                                             m.d.K0, rho, sp, vals);
     }
-    return cudaGetLastError();
-}
-
-// Assembly and sensitivity of one step.  In 3D with the sector split, one
-// launch does both (after the element moduli); otherwise the two passes run
-// back to back.
-cudaError_t launch_lattice_step(const soptx_mesh_s &m, const double *rho, const double *u, double *vals, double *dc,
-                                double *c, cudaStream_t st)
-{
-    const auto &h = m.h;
-    if (h.dim != 3 || (int)h.sectors.size() != (3 << 3) * 3 || h.nn == 0) {
-        cudaError_t err = launch_lattice_assemble(m, rho, vals, st);
-        if (err != cudaSuccess) return err;
-        return launch_lattice_sensitivity(m, rho, u, dc, c, nullptr, st);
-    }
-    const SimpParams sp = simp_params(m.mat);
-    const int eb = 256;
-    const int egrid = (int)std::min<int64_t>((h.nc + eb - 1) / eb, 152 * 8);
-    k_simp_df<<<std::max(egrid, 1), eb, 0, st>>>(h.nc, rho, sp, (float2 *)m.d.Edf);
-    cudaError_t err = cudaGetLastError();
-    if (err != cudaSuccess) return err;
-    constexpr int WPB = kAsmWarps;
-    k_lattice_step3<WPB><<<lattice_assemble3_grid(h.nn), WPB * 32, 0, st>>>(
-        h.lat_n[0], h.lat_n[1], h.lat_n[2], h.nn, h.nc, m.d.node_off, (const float2 *)m.d.Edf,
-        (const float2 *)m.d.kappa, m.d.K0, rho, u, sp, sector_table<3>(h.sectors), vals, dc, m.d.scratch,
-        m.d.counter, c);
     return cudaGetLastError();
 }
 
