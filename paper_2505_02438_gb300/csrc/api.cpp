@@ -34,7 +34,7 @@ static void free_device(DeviceMesh &d)
 {
     void *ptrs[] = {d.indptr, d.indices, d.cell_node, d.node_off, d.inc_ptr, d.inc,
                     d.pos, d.geo, d.M, d.K, d.scratch, d.Edf, d.kappa, d.K0, d.sectors, d.udf, d.part,
-                    d.inc_e, d.inc_a, d.counter, d.xcell, d.qw, d.qdphi, d.qdgeo, d.cg};
+                    d.inc_e, d.inc_a, d.counter, d.xcell, d.qw, d.qdphi, d.qdgeo, d.cg, d.lat_bad};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     d = DeviceMesh{};
@@ -229,6 +229,13 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
             cudaError_t e = dev_alloc((void **)&d.Edf, (size_t)std::max<int64_t>(h.nc, 1) * sizeof(float2));
             if (e != cudaSuccess) { cudaGetLastError(); s = cuda_status(e, "element moduli"); }
             else B += std::max<int64_t>(h.nc, 1) * (int64_t)sizeof(float2);
+        }
+        if (s == SOPTX_OK && h.dim == 3) {
+            const size_t bytes = (size_t)(1 + h.nc) * sizeof(unsigned);
+            cudaError_t e = dev_alloc((void **)&d.lat_bad, bytes);
+            if (e == cudaSuccess) e = cudaMemsetAsync(d.lat_bad, 0, sizeof(unsigned), st);
+            if (e != cudaSuccess) { cudaGetLastError(); s = cuda_status(e, "out-of-range cell list"); }
+            else B += (int64_t)bytes;
         }
         if (s == SOPTX_OK) s = cuda_status(cudaStreamSynchronize(st), "mesh setup");
     }

@@ -110,6 +110,7 @@ struct DeviceMesh {
     float2 *kappa = nullptr;       // [3^d][d][d] reference blocks as float pairs
     double *K0 = nullptr;          // [ldof][ldof] unit-modulus matrix in FP64
     float2 *sectors = nullptr;     // [2^d][d][d] Walsh-sector blocks of K^0 (nullptr: no split)
+    unsigned *lat_bad = nullptr;   // 3D: [0] count, [1..nc] cells with out-of-range moduli (per call)
     // general path
     float2 *udf = nullptr;         // [ndof] u as float pairs
     double *part = nullptr;        // [nc][nb] per-(cell, node) partials of u_e^T K_e^0 u_e

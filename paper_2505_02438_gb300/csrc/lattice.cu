@@ -18,7 +18,9 @@
 // offset delta, and writes the node's d rows (d * d * deg(n) contiguous CSR
 // values) with coalesced stores.  The element moduli arrive from k_simp_df
 // as float pairs; a node touching a modulus outside [2^-60, 2^60] (flagged by
-// a NaN low word) is done in plain FP64 instead.
+// a NaN low word) is done in plain FP64 instead: in 2D by its warp, in 3D by
+// a short kernel after the assembly (the cells are listed by k_simp_df), which
+// keeps the rare path out of the 3D kernel's register allocation.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -32,10 +34,22 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-__global__ void k_simp_df(int64_t nc, const double *__restrict__ rho, SimpParams sp, float2 *__restrict__ Edf)
+// Element moduli as float pairs.  With `bad` given, the cells whose modulus
+// is flagged out of range (NaN low word) are appended to bad[1..nc] and
+// counted in bad[0] (order immaterial: the nodes around them are redone in
+// FP64 with the current densities, so entries left by an earlier call whose
+// fix-up never ran are harmless).
+__global__ void k_simp_df(int64_t nc, const double *__restrict__ rho, SimpParams sp, float2 *__restrict__ Edf,
+                          unsigned *__restrict__ bad)
 {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc; e += (int64_t)gridDim.x * blockDim.x)
-        Edf[e] = simp_E_pair(sp, rho[e]);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc; e += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = simp_E_pair(sp, rho[e]);
+        Edf[e] = v;
+        if (bad && isnan(v.y)) {
+            const unsigned k = atomicAdd(bad, 1u);
+            if (k < (unsigned)nc) bad[1 + k] = (unsigned)e;
+        }
+    }
 }
 
 __device__ __forceinline__ df shfl_df(df v, int src)
@@ -213,7 +227,6 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restric
                 off_next = node_off[n + 1];
             }
             const df Ec = df{cur.x, cur.y};
-            const bool bad = lane < 8 && isnan(cur.y);
             const bool interior = idx[0] > 0 && idx[0] < nx && idx[1] > 0 && idx[1] < ny && idx[2] > 0 && idx[2] < nz;
             bool valid;
             int mi, rowlen;
@@ -233,9 +246,7 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restric
                 rowlen = 3 * cnt[0] * cnt[1] * cnt[2];
             }
             double *base = vals + 9 * off;
-            if (__any_sync(kFull, bad)) {
-                lattice_node_fp64<3>(nx, ny, nz, idx[0], idx[1], idx[2], dl, valid, mi, rowlen, base, K0, rho, sp);
-            } else {
+            {
                 // stage X: lanes 0..15 -> (ox, cy, cz)
                 const df xL = shfl_df(Ec, 2 * yzx), xH = shfl_df(Ec, 2 * yzx + 1);
                 const df X = combine(ox == 0, cx_, xL, xH);
@@ -300,6 +311,42 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restric
         }
     }
     if (lane == 0) bulk_wait_all();
+}
+
+// The 3D nodes around cells whose modulus lies outside the float-pair range
+// (listed by k_simp_df; the assembly wrote them from the flagged pairs) are
+// redone in plain FP64, one warp per (cell, corner), after the assembly
+// kernel has finished; then the list is emptied for the next call.  A node
+// shared by several listed cells is written again with the same values.
+__global__ void __launch_bounds__(256)
+k_lattice_fixup3(int nx, int ny, int nz, const int64_t *__restrict__ node_off, const double *__restrict__ K0,
+                 const double *__restrict__ rho, SimpParams sp, double *__restrict__ vals, unsigned *__restrict__ bad)
+{
+    const unsigned nbad = min(bad[0], (unsigned)nx * (unsigned)ny * (unsigned)nz);
+    const int lane = threadIdx.x & 31;
+    const int dl = lane < 27 ? lane : 26;
+    const int dx = dl % 3 - 1, dy = (dl / 3) % 3 - 1, dz = dl / 9 - 1;
+    const int N[3] = {nx, ny, nz};
+    for (unsigned t = threadIdx.x >> 5; t < 8u * nbad; t += blockDim.x >> 5) {
+        const unsigned e = bad[1 + t / 8], corner = t % 8;
+        const unsigned r = e / (unsigned)nx;
+        const int idx[3] = {(int)(e % (unsigned)nx) + (int)(corner & 1), (int)(r % (unsigned)ny) + (int)((corner >> 1) & 1),
+                            (int)(r / (unsigned)ny) + (int)(corner >> 2)};
+        const int64_t n = idx[0] + (int64_t)(nx + 1) * (idx[1] + (int64_t)(ny + 1) * idx[2]);
+        int lo[3], cnt[3];
+        for (int m = 0; m < 3; m++) {
+            lo[m] = idx[m] > 0 ? -1 : 0;
+            cnt[m] = (idx[m] < N[m] ? 1 : 0) - lo[m] + 1;
+        }
+        const bool valid = lane < 27 && dx >= lo[0] && dx < lo[0] + cnt[0] && dy >= lo[1] && dy < lo[1] + cnt[1] &&
+                           dz >= lo[2] && dz < lo[2] + cnt[2];
+        const int mi = (dx - lo[0]) + cnt[0] * ((dy - lo[1]) + cnt[1] * (dz - lo[2]));
+        const int rowlen = 3 * cnt[0] * cnt[1] * cnt[2];
+        lattice_node_fp64<3>(nx, ny, nz, idx[0], idx[1], idx[2], dl, valid, mi, rowlen, vals + 9 * node_off[n], K0,
+                             rho, sp);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) bad[0] = 0u;
 }
 
 // 2D: three nodes per warp, lanes 9g .. 9g+8 serve node g, one lane per offset.
@@ -563,7 +610,7 @@ cudaError_t launch_lattice_assemble(const soptx_mesh_s &m, const double *rho, do
     const SimpParams sp = simp_params(m.mat);
     const int eb = 256;
     const int egrid = (int)std::min<int64_t>((h.nc + eb - 1) / eb, 152 * 8);
-    k_simp_df<<<std::max(egrid, 1), eb, 0, st>>>(h.nc, rho, sp, (float2 *)m.d.Edf);
+    k_simp_df<<<std::max(egrid, 1), eb, 0, st>>>(h.nc, rho, sp, (float2 *)m.d.Edf, h.dim == 3 ? m.d.lat_bad : nullptr);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     constexpr int WPB = 8;
@@ -573,6 +620,10 @@ cudaError_t launch_lattice_assemble(const soptx_mesh_s &m, const double *rho, do
         k_lattice_assemble3<WPB><<<grid, WPB * 32, 0, st>>>(h.lat_n[0], h.lat_n[1], h.lat_n[2], h.nn, m.d.node_off,
                                                             (const float2 *)m.d.Edf, (const float2 *)m.d.kappa,
                                                             m.d.K0, rho, sp, vals);
+        err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+        k_lattice_fixup3<<<1, 256, 0, st>>>(h.lat_n[0], h.lat_n[1], h.lat_n[2], m.d.node_off, m.d.K0, rho, sp, vals,
+                                             m.d.lat_bad);
     } else {
         const int64_t groups = (h.nn + 2) / 3;
         const int grid = (int)std::min<int64_t>((groups + WPB - 1) / WPB, 152 * 8);
