@@ -570,9 +570,9 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": job_rate(nnz, world, n_e2e, e2e_ms) / 1e9, "unit": "GNNZ/s",
                 "h2d_bytes_per_step": 8 * (nc + ndof), "d2h_bytes_per_step": 8 * (nc + 1),
                 "steps": n_e2e},
-        # lattice 3D: moduli, assembly, out-of-range fix-up, sensitivity (+ sum of c); lattice 2D: moduli,
-        # assembly, sensitivity; general path: moduli and u pairs, fused gather, finalize (+ sum of c)
-        "gpu_launches": (4 if mesh.path == "lattice" and wl.dim == 3 else 3) * K,
+        # lattice: moduli, assembly, sensitivity (+ sum of c); general path: moduli and u pairs,
+        # fused gather, finalize (+ sum of c)
+        "gpu_launches": 3 * K,
         "wall_s_timed_region": wall,
     }
     if args.elem_prec == "fp32":

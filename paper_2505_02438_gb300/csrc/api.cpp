@@ -231,10 +231,10 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
             else B += std::max<int64_t>(h.nc, 1) * (int64_t)sizeof(float2);
         }
         if (s == SOPTX_OK && h.dim == 3) {
-            const size_t bytes = (size_t)(1 + h.nc) * sizeof(unsigned);
+            const size_t bytes = 16;
             cudaError_t e = dev_alloc((void **)&d.lat_bad, bytes);
-            if (e == cudaSuccess) e = cudaMemsetAsync(d.lat_bad, 0, sizeof(unsigned), st);
-            if (e != cudaSuccess) { cudaGetLastError(); s = cuda_status(e, "out-of-range cell list"); }
+            if (e == cudaSuccess) e = cudaMemsetAsync(d.lat_bad, 0, bytes, st);
+            if (e != cudaSuccess) { cudaGetLastError(); s = cuda_status(e, "out-of-range flag"); }
             else B += (int64_t)bytes;
         }
         if (s == SOPTX_OK) s = cuda_status(cudaStreamSynchronize(st), "mesh setup");

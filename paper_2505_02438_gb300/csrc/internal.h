@@ -110,7 +110,7 @@ struct DeviceMesh {
     float2 *kappa = nullptr;       // [3^d][d][d] reference blocks as float pairs
     double *K0 = nullptr;          // [ldof][ldof] unit-modulus matrix in FP64
     float2 *sectors = nullptr;     // [2^d][d][d] Walsh-sector blocks of K^0 (nullptr: no split)
-    unsigned *lat_bad = nullptr;   // 3D: [0] count, [1..nc] cells with out-of-range moduli (per call)
+    unsigned *lat_bad = nullptr;   // 3D: generation of the last call that met out-of-range moduli
     // general path
     float2 *udf = nullptr;         // [ndof] u as float pairs
     double *part = nullptr;        // [nc][nb] per-(cell, node) partials of u_e^T K_e^0 u_e
@@ -135,6 +135,7 @@ struct soptx_mesh_s {
     int prec = SOPTX_ELEM_FP64;
     soptx_path path = SOPTX_PATH_CACHED;
     int64_t device_bytes = 0;
+    mutable uint32_t lattice_gen = 0;   // calls of the 3D lattice assembly (marks the out-of-range flag)
 };
 
 namespace soptx {

@@ -18,9 +18,9 @@
 // offset delta, and writes the node's d rows (d * d * deg(n) contiguous CSR
 // values) with coalesced stores.  The element moduli arrive from k_simp_df
 // as float pairs; a node touching a modulus outside [2^-60, 2^60] (flagged by
-// a NaN low word) is done in plain FP64 instead: in 2D by its warp, in 3D by
-// a short kernel after the assembly (the cells are listed by k_simp_df), which
-// keeps the rare path out of the 3D kernel's register allocation.
+// a NaN low word) is done in plain FP64 instead: in 2D by its warp at once, in
+// 3D by k_simp_df before the assembly (whose warps then skip the node), which
+// keeps the rare path out of the assembly kernel's registers.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -33,24 +33,6 @@ namespace soptx {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-
-// Element moduli as float pairs.  With `bad` given, the cells whose modulus
-// is flagged out of range (NaN low word) are appended to bad[1..nc] and
-// counted in bad[0] (order immaterial: the nodes around them are redone in
-// FP64 with the current densities, so entries left by an earlier call whose
-// fix-up never ran are harmless).
-__global__ void k_simp_df(int64_t nc, const double *__restrict__ rho, SimpParams sp, float2 *__restrict__ Edf,
-                          unsigned *__restrict__ bad)
-{
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc; e += (int64_t)gridDim.x * blockDim.x) {
-        const float2 v = simp_E_pair(sp, rho[e]);
-        Edf[e] = v;
-        if (bad && isnan(v.y)) {
-            const unsigned k = atomicAdd(bad, 1u);
-            if (k < (unsigned)nc) bad[1 + k] = (unsigned)e;
-        }
-    }
-}
 
 __device__ __forceinline__ df shfl_df(df v, int src)
 {
@@ -83,6 +65,13 @@ __device__ __forceinline__ df combine(bool lsel, float coef, df L, df H)
     const df lhs = lsel ? L : H;
     return df_add(lhs, df{__fmul_rn(coef, L.h), __fmul_rn(coef, L.l)});
 }
+// The same without the final renormalisation, for the stages whose output
+// feeds further float-pair sums.
+__device__ __forceinline__ df combine_lazy(bool lsel, float coef, df L, df H)
+{
+    const df lhs = lsel ? L : H;
+    return df_add_lazy(lhs, df{__fmul_rn(coef, L.h), __fmul_rn(coef, L.l)});
+}
 __device__ __forceinline__ float opt_coef(int o) { return o == 2 ? 1.f : (o == 3 ? -1.f : 0.f); }
 
 __device__ __forceinline__ int axis_opt(int delta, bool in_class)
@@ -92,9 +81,10 @@ __device__ __forceinline__ int axis_opt(int delta, bool in_class)
 
 // Plain-FP64 version of one node's rows (used for out-of-range moduli).
 template <int D>
-__device__ __noinline__ void lattice_node_fp64(int nx, int ny, int nz, int ix, int iy, int iz, int dl, bool valid,
-                                               int mi, int rowlen, double *base, const double *__restrict__ K0,
-                                               const double *__restrict__ rho, SimpParams sp)
+__device__ __forceinline__ void lattice_node_fp64_body(int nx, int ny, int nz, int ix, int iy, int iz, int dl,
+                                                       bool valid, int mi, int rowlen, double *base,
+                                                       const double *__restrict__ K0, const double *__restrict__ rho,
+                                                       const SimpParams &sp)
 {
     if (!valid) return;
     const int N[3] = {nx, ny, nz}, idx[3] = {ix, iy, iz};
@@ -122,6 +112,13 @@ __device__ __noinline__ void lattice_node_fp64(int nx, int ny, int nz, int ix, i
             base[i * rowlen + D * mi + j] = acc;
         }
 }
+template <int D>
+__device__ __noinline__ void lattice_node_fp64(int nx, int ny, int nz, int ix, int iy, int iz, int dl, bool valid,
+                                               int mi, int rowlen, double *base, const double *__restrict__ K0,
+                                               const double *__restrict__ rho, SimpParams sp)
+{
+    lattice_node_fp64_body<D>(nx, ny, nz, ix, iy, iz, dl, valid, mi, rowlen, base, K0, rho, sp);
+}
 
 // Node chunks per warp: consecutive nodes, so the lattice index is decoded once
 // per chunk and then stepped; the next node's moduli are fetched before the
@@ -133,6 +130,29 @@ constexpr int kChunk = 16;
 #define SOPTX_LATTICE_FP64_CLASSES 2
 #endif
 constexpr int kFp64Classes = SOPTX_LATTICE_FP64_CLASSES < 1 ? 1 : SOPTX_LATTICE_FP64_CLASSES;
+
+// Row layout of node idx in the CSR values: whether the lane's offset delta is
+// a neighbour (valid), its position mi among the node's neighbours and the
+// length of each of the node's d rows.
+__device__ __forceinline__ void node_layout3(const int idx[3], const int N[3], int dx, int dy, int dz, int lane,
+                                             bool &valid, int &mi, int &rowlen)
+{
+    if (idx[0] > 0 && idx[0] < N[0] && idx[1] > 0 && idx[1] < N[1] && idx[2] > 0 && idx[2] < N[2]) {
+        valid = lane < 27;
+        mi = lane;
+        rowlen = 81;
+        return;
+    }
+    int lo[3], cnt[3];
+    for (int m = 0; m < 3; m++) {
+        lo[m] = idx[m] > 0 ? -1 : 0;
+        cnt[m] = (idx[m] < N[m] ? 1 : 0) - lo[m] + 1;
+    }
+    valid = lane < 27 && dx >= lo[0] && dx < lo[0] + cnt[0] && dy >= lo[1] && dy < lo[1] + cnt[1] &&
+            dz >= lo[2] && dz < lo[2] + cnt[2];
+    mi = (dx - lo[0]) + cnt[0] * ((dy - lo[1]) + cnt[1] * (dz - lo[2]));
+    rowlen = 3 * cnt[0] * cnt[1] * cnt[2];
+}
 
 struct NodeIter {
     int idx[3];
@@ -175,7 +195,7 @@ __global__ void __launch_bounds__(WPB * 32, SOPTX_LATTICE_MINBLOCKS)
 k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restrict__ node_off,
                     const float2 *__restrict__ Edf, const float2 *__restrict__ kappa_g,
                     const double *__restrict__ K0, const double *__restrict__ rho, SimpParams sp,
-                    double *__restrict__ vals)
+                    double *__restrict__ vals, const unsigned *__restrict__ flag, unsigned gen)
 {
     const int lane = threadIdx.x & 31;
     const int dl = lane < 27 ? lane : 26;
@@ -193,6 +213,8 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restric
     // destination; the copy engine writes a buffer out while the warp fills
     // the other one
     __shared__ __align__(16) double stage_s[WPB][2][27 * 9 + 1];
+    // the 64 signed sums of the node being done (stage Z's output), per warp
+    __shared__ float2 tab_s[WPB][64];
     int buf = 0;
     for (int t = threadIdx.x; t < 27 * 9; t += blockDim.x) {
         kap_s[t] = kappa_g[t];
@@ -206,6 +228,10 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restric
     const int oz0 = (lane < 16) ? 0 : 1, oz1 = oz0 + 2;
     const float cx_ = opt_coef(ox), cy_ = opt_coef(oy), cz0_ = opt_coef(oz0), cz1_ = opt_coef(oz1);
     const int N[3] = {nx, ny, nz};
+
+    // k_simp_df of this call stored `gen` in *flag if some modulus is out of
+    // range (and wrote the rows of the nodes around those cells in FP64)
+    const bool anybad = __ldcg(flag) == gen;
 
     const int64_t nchunks = (nn + kChunk - 1) / kChunk;
     const int64_t warps = (int64_t)gridDim.x * WPB;
@@ -227,40 +253,33 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restric
                 off_next = node_off[n + 1];
             }
             const df Ec = df{cur.x, cur.y};
-            const bool interior = idx[0] > 0 && idx[0] < nx && idx[1] > 0 && idx[1] < ny && idx[2] > 0 && idx[2] < nz;
+            // a corner modulus outside the float-pair range: k_simp_df has
+            // written this node's rows in FP64, so nothing is stored here
+            unsigned badnode = 0u;
+            if (anybad) badnode = __ballot_sync(kFull, lane < 8 && isnan(cur.y));
             bool valid;
             int mi, rowlen;
-            if (interior) {
-                valid = lane < 27;
-                mi = lane;
-                rowlen = 81;
-            } else {
-                int lo[3], cnt[3];
-                for (int m = 0; m < 3; m++) {
-                    lo[m] = idx[m] > 0 ? -1 : 0;
-                    cnt[m] = (idx[m] < N[m] ? 1 : 0) - lo[m] + 1;
-                }
-                valid = lane < 27 && dx >= lo[0] && dx < lo[0] + cnt[0] && dy >= lo[1] && dy < lo[1] + cnt[1] &&
-                        dz >= lo[2] && dz < lo[2] + cnt[2];
-                mi = (dx - lo[0]) + cnt[0] * ((dy - lo[1]) + cnt[1] * (dz - lo[2]));
-                rowlen = 3 * cnt[0] * cnt[1] * cnt[2];
-            }
+            node_layout3(idx, N, dx, dy, dz, lane, valid, mi, rowlen);
             double *base = vals + 9 * off;
             {
                 // stage X: lanes 0..15 -> (ox, cy, cz)
                 const df xL = shfl_df(Ec, 2 * yzx), xH = shfl_df(Ec, 2 * yzx + 1);
-                const df X = combine(ox == 0, cx_, xL, xH);
+                const df X = combine_lazy(ox == 0, cx_, xL, xH);
                 // stage Y: lanes 0..31 -> (ox, oy, cz)
                 const df yL = shfl_df(X, ox + 4 * (2 * czy)), yH = shfl_df(X, ox + 4 * (1 + 2 * czy));
-                const df Y = combine(oy == 0, cy_, yL, yH);
+                const df Y = combine_lazy(oy == 0, cy_, yL, yH);
                 // stage Z: lane holds entries lane (A) and lane + 32 (B)
                 const df zL = shfl_df(Y, lane & 15), zH = shfl_df(Y, (lane & 15) + 16);
                 const df A = combine(oz0 == 0, cz0_, zL, zH), B = combine(false, cz1_, zL, zH);
+                float2 *tab = tab_s[threadIdx.x >> 5];
+                tab[lane] = make_float2(A.h, A.l);
+                tab[lane + 32] = make_float2(B.h, B.l);
+                __syncwarp();
                 df T[4];
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
-                    const df a = shfl_df(A, tq[q] & 31), b = shfl_df(B, tq[q] & 31);
-                    T[q] = tq[q] >= 32 ? b : a;
+                    const float2 t = tab[tq[q]];
+                    T[q] = df{t.x, t.y};
                 }
                 // the buffer about to be filled was handed to the copy engine two
                 // nodes ago: wait until that copy has read it
@@ -298,12 +317,12 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restric
                 // a value at an odd 8-byte phase at either end goes out by a plain store
                 const int blk = 3 * rowlen;
                 const int head = ph, mid = (blk - head) & ~1, tail = blk - head - mid;
-                if (lane == 0 && mid > 0) {
+                if (lane == 0 && mid > 0 && !badnode) {
                     bulk_store(base + head, stage + ph + head, (uint32_t)(8 * mid));
                     bulk_commit();
                 }
-                if (lane == 1 && head) __stcs(base, stage[ph]);
-                if (lane == 2 && tail) __stcs(base + blk - 1, stage[ph + blk - 1]);
+                if (lane == 1 && head && !badnode) __stcs(base, stage[ph]);
+                if (lane == 2 && tail && !badnode) __stcs(base + blk - 1, stage[ph + blk - 1]);
                 buf ^= 1;
             }
             cur = nxt;
@@ -313,40 +332,50 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restric
     if (lane == 0) bulk_wait_all();
 }
 
-// The 3D nodes around cells whose modulus lies outside the float-pair range
-// (listed by k_simp_df; the assembly wrote them from the flagged pairs) are
-// redone in plain FP64, one warp per (cell, corner), after the assembly
-// kernel has finished; then the list is emptied for the next call.  A node
-// shared by several listed cells is written again with the same values.
-__global__ void __launch_bounds__(256)
-k_lattice_fixup3(int nx, int ny, int nz, const int64_t *__restrict__ node_off, const double *__restrict__ K0,
-                 const double *__restrict__ rho, SimpParams sp, double *__restrict__ vals, unsigned *__restrict__ bad)
+// Element moduli as float pairs.  With `flag` given (3D lattice), a warp
+// whose cells include moduli outside the float-pair range (NaN low word)
+// stores `gen` in *flag and writes the rows of the nodes around each such
+// cell in plain FP64, lanes over the offsets; the assembly kernel then skips
+// those nodes.  A node next to several such cells is written again with the
+// same values.
+__global__ void k_simp_df(int nx, int ny, int nz, int64_t nc, const double *__restrict__ rho, SimpParams sp,
+                          float2 *__restrict__ Edf, const int64_t *__restrict__ node_off,
+                          const double *__restrict__ K0, double *__restrict__ vals, unsigned *__restrict__ flag,
+                          unsigned gen)
 {
-    const unsigned nbad = min(bad[0], (unsigned)nx * (unsigned)ny * (unsigned)nz);
     const int lane = threadIdx.x & 31;
-    const int dl = lane < 27 ? lane : 26;
-    const int dx = dl % 3 - 1, dy = (dl / 3) % 3 - 1, dz = dl / 9 - 1;
-    const int N[3] = {nx, ny, nz};
-    for (unsigned t = threadIdx.x >> 5; t < 8u * nbad; t += blockDim.x >> 5) {
-        const unsigned e = bad[1 + t / 8], corner = t % 8;
-        const unsigned r = e / (unsigned)nx;
-        const int idx[3] = {(int)(e % (unsigned)nx) + (int)(corner & 1), (int)(r % (unsigned)ny) + (int)((corner >> 1) & 1),
-                            (int)(r / (unsigned)ny) + (int)(corner >> 2)};
-        const int64_t n = idx[0] + (int64_t)(nx + 1) * (idx[1] + (int64_t)(ny + 1) * idx[2]);
-        int lo[3], cnt[3];
-        for (int m = 0; m < 3; m++) {
-            lo[m] = idx[m] > 0 ? -1 : 0;
-            cnt[m] = (idx[m] < N[m] ? 1 : 0) - lo[m] + 1;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); e0 < nc; e0 += stride) {
+        const int64_t e = e0 + lane;
+        bool isbad = false;
+        if (e < nc) {
+            const float2 v = simp_E_pair(sp, rho[e]);
+            Edf[e] = v;
+            isbad = isnan(v.y);
         }
-        const bool valid = lane < 27 && dx >= lo[0] && dx < lo[0] + cnt[0] && dy >= lo[1] && dy < lo[1] + cnt[1] &&
-                           dz >= lo[2] && dz < lo[2] + cnt[2];
-        const int mi = (dx - lo[0]) + cnt[0] * ((dy - lo[1]) + cnt[1] * (dz - lo[2]));
-        const int rowlen = 3 * cnt[0] * cnt[1] * cnt[2];
-        lattice_node_fp64<3>(nx, ny, nz, idx[0], idx[1], idx[2], dl, valid, mi, rowlen, vals + 9 * node_off[n], K0,
-                             rho, sp);
+        if (!flag) continue;
+        unsigned m = __ballot_sync(kFull, isbad);
+        if (!m) continue;
+        if (lane == 0) *flag = gen;
+        const int dl = lane < 27 ? lane : 26;
+        const int dx = dl % 3 - 1, dy = (dl / 3) % 3 - 1, dz = dl / 9 - 1;
+        const int N[3] = {nx, ny, nz};
+        while (m) {
+            const unsigned k = __ffs(m) - 1;
+            m &= m - 1u;
+            const uint32_t ce = (uint32_t)(e0 + k), r = ce / (uint32_t)nx;
+            for (int corner = 0; corner < 8; corner++) {
+                const int idx[3] = {(int)(ce % (uint32_t)nx) + (corner & 1), (int)(r % (uint32_t)ny) + ((corner >> 1) & 1),
+                                    (int)(r / (uint32_t)ny) + (corner >> 2)};
+                const int64_t n = idx[0] + (int64_t)(nx + 1) * (idx[1] + (int64_t)(ny + 1) * idx[2]);
+                bool valid;
+                int mi, rowlen;
+                node_layout3(idx, N, dx, dy, dz, lane, valid, mi, rowlen);
+                lattice_node_fp64<3>(nx, ny, nz, idx[0], idx[1], idx[2], dl, valid, mi, rowlen, vals + 9 * node_off[n],
+                                     K0, rho, sp);
+            }
+        }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) bad[0] = 0u;
 }
 
 // 2D: three nodes per warp, lanes 9g .. 9g+8 serve node g, one lane per offset.
@@ -610,7 +639,12 @@ cudaError_t launch_lattice_assemble(const soptx_mesh_s &m, const double *rho, do
     const SimpParams sp = simp_params(m.mat);
     const int eb = 256;
     const int egrid = (int)std::min<int64_t>((h.nc + eb - 1) / eb, 152 * 8);
-    k_simp_df<<<std::max(egrid, 1), eb, 0, st>>>(h.nc, rho, sp, (float2 *)m.d.Edf, h.dim == 3 ? m.d.lat_bad : nullptr);
+    // a fresh nonzero generation per call marks this call's out-of-range flag
+    unsigned gen = ++m.lattice_gen;
+    if (gen == 0u) gen = ++m.lattice_gen;
+    k_simp_df<<<std::max(egrid, 1), eb, 0, st>>>(h.lat_n[0], h.lat_n[1], h.lat_n[2], h.nc, rho, sp,
+                                                 (float2 *)m.d.Edf, m.d.node_off, m.d.K0, vals,
+                                                 h.dim == 3 ? m.d.lat_bad : nullptr, gen);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     constexpr int WPB = 8;
@@ -619,11 +653,7 @@ cudaError_t launch_lattice_assemble(const soptx_mesh_s &m, const double *rho, do
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((chunks + WPB - 1) / WPB, 152 * 4));
         k_lattice_assemble3<WPB><<<grid, WPB * 32, 0, st>>>(h.lat_n[0], h.lat_n[1], h.lat_n[2], h.nn, m.d.node_off,
                                                             (const float2 *)m.d.Edf, (const float2 *)m.d.kappa,
-                                                            m.d.K0, rho, sp, vals);
-        err = cudaGetLastError();
-        if (err != cudaSuccess) return err;
-        k_lattice_fixup3<<<1, 256, 0, st>>>(h.lat_n[0], h.lat_n[1], h.lat_n[2], m.d.node_off, m.d.K0, rho, sp, vals,
-                                             m.d.lat_bad);
+                                                            m.d.K0, rho, sp, vals, m.d.lat_bad, gen);
     } else {
         const int64_t groups = (h.nn + 2) / 3;
         const int grid = (int)std::min<int64_t>((groups + WPB - 1) / WPB, 152 * 8);

@@ -153,6 +153,25 @@ def test_lattice_out_of_range_moduli_take_fp64_route(P, cell, mk):
     assert np.all(np.abs(vals - v) <= TOL64 * va + 1e-300)
 
 
+def test_lattice_out_of_range_moduli_between_normal_calls(P):
+    """Calls with and without out-of-range moduli alternate on one 3D lattice
+    (several warps and blocks, cells of both kinds next to chunk borders): each
+    call matches the oracle, so no state of one call leaks into the next."""
+    c, cl = W.structured_hex(23, 9, 7)
+    mat = (1.0, 0.0, 0.3, 3.0, 0)
+    m = P.Mesh("hex", 1, c, cl, *mat)
+    assert m.path == "lattice"
+    g = np.random.default_rng(9)
+    normal = g.uniform(0.001, 1.0, len(cl))
+    tiny = normal.copy()
+    tiny[g.choice(len(cl), 40, replace=False)] = 1e-9      # E = 1e-27
+    tiny[g.choice(len(cl), 10, replace=False)] = 1e-30     # E = 1e-90, below the float range
+    for rho in (normal, tiny, normal, tiny, tiny, normal):
+        vals = m.assemble_K(to_dev(rho)).cpu().numpy()
+        rp, ci, v, va, _ = oracle_csr("hex", 1, c, cl, mat, rho)
+        assert np.all(np.abs(vals - v) <= TOL64 * va + 1e-300)
+
+
 def test_lattice_anisotropic_boxes(P):
     """Box cells with different edge lengths per axis and a shifted origin."""
     c, cl = W.structured_hex(6, 4, 3)
