@@ -84,7 +84,9 @@ typedef struct soptx_mesh_s *soptx_mesh;
 
 /* Which device path a mesh was given (soptx_mesh_path). */
 typedef enum {
-    SOPTX_PATH_LATTICE = 0,   /* order-1 box lattice: implicit maps, one K^0   */
+    SOPTX_PATH_LATTICE = 0,   /* order-1 box lattice: implicit maps, one K^0;
+                                 in 3D only while the used entries of K^0 span
+                                 at most 2^24 (else the uniform path)          */
     SOPTX_PATH_UNIFORM = 1,   /* every cell has the same Jacobian: one K^0     */
     SOPTX_PATH_CACHED = 2     /* per-cell K_e^0 cached on the device           */
 } soptx_path;
@@ -210,7 +212,9 @@ soptx_status soptx_mesh_destroy(soptx_mesh mesh);
  * validation, numbering and pattern construction as soptx_mesh_create and
  * returns the sizes and, for non-NULL host buffers, the results:
  *   indptr int64 [ndof+1], indices int32 [nnz], cell_nodes int32 [n_cells][nb],
- *   *path the device path a mesh would take.  Call once with NULL buffers to
+ *   *path the device path a mesh would take (a 3D box lattice whose boxes are
+ *   so elongated that K^0 spans more than 2^24 is planned as the lattice but
+ *   built on the uniform path).  Call once with NULL buffers to
  *   learn ndof / nnz, then again with buffers of those sizes.
  */
 soptx_status soptx_host_plan(int dim, soptx_cell cell, int order, int64_t n_vertices,

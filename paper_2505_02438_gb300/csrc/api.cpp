@@ -200,11 +200,12 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
     }
     if (s == SOPTX_OK) s = cuda_status(launch_element_matrices(*m, n_elem_mats, st), "element matrices kernel");
     if (s == SOPTX_OK) s = cuda_status(cudaStreamSynchronize(st), "mesh setup");
+    std::vector<double> K0;
     if (s == SOPTX_OK && m->path == SOPTX_PATH_LATTICE) {
         // the lattice kernels read one FP64 K^0, its reference blocks as float
         // pairs, and per-call element moduli
         const size_t n2 = (size_t)h.ldof * h.ldof;
-        std::vector<double> K0(n2);
+        K0.assign(n2, 0.0);
         if (prec == SOPTX_ELEM_FP32) {
             std::vector<float> Kf(n2);
             s = cuda_status(cudaMemcpy(Kf.data(), d.K, n2 * sizeof(float), cudaMemcpyDeviceToHost), "K0");
@@ -214,8 +215,11 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
             s = cuda_status(cudaMemcpy(Kp.data(), d.K, n2 * sizeof(float2), cudaMemcpyDeviceToHost), "K0");
             for (size_t q = 0; q < n2; q++) K0[q] = (double)Kp[q].x + (double)Kp[q].y;
         }
+        if (s == SOPTX_OK && h.dim == 3 && !lattice_kappa_shift(h.dim, K0, h.lat_kshift)) m->path = SOPTX_PATH_UNIFORM;
+    }
+    if (s == SOPTX_OK && m->path == SOPTX_PATH_LATTICE) {
         std::vector<float2> kappa;
-        build_lattice_kappa(h.dim, K0, kappa);
+        build_lattice_kappa(h.dim, K0, h.dim == 3 ? h.lat_kshift : 0, kappa);
         if (s == SOPTX_OK) s = upload(&d.K0, K0, st, B, "K0");
         if (s == SOPTX_OK) s = upload(&d.kappa, kappa, st, B, "kappa");
         std::vector<float2> sectors;

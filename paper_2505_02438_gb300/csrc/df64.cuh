@@ -129,6 +129,26 @@ __device__ __forceinline__ double df_to_double(float p, float e)
     return __longlong_as_double((long long)bits);
 }
 
+// The value of df_to_double with integer operations and two FP32 multiplies
+// only (no out-of-line path), times 2^k where bias = 0x38000000 + (k << 20)
+// (the FP32-to-FP64 exponent rebias plus k).  Valid for |p| < 2^84 and any
+// exponent of p: the correction scale 2^(46 - E) is applied as 2^64 * 2^(-18 - E),
+// both representable for E >= -126.  p = 0 gives a signed zero (e must be 0);
+// a denormal p gives a value within 2^-125 * 2^k of (p + e) 2^k.
+__device__ __forceinline__ double df_to_double_biased(float p, float e, uint32_t bias)
+{
+    const uint32_t hb = __float_as_uint(p);
+    const uint32_t sign = hb & 0x80000000u;
+    const uint32_t mag = hb & 0x7fffffffu;
+    const uint32_t hi = mag ? (sign | ((mag >> 3) + bias)) : sign;
+    const uint32_t lo = mag << 29;
+    const uint32_t s2 = ((236u << 23) - (mag & 0x7f800000u)) | sign;     // +-2^(-18 - E)
+    int32_t ci = __float2int_rn(__fmul_rn(__fmul_rn(e, 0x1p64f), __uint_as_float(s2)));
+    if ((mag & 0x007fffffu) == 0u && ci < 0) ci *= 2;                      // just below a power of two
+    const uint64_t bits = (((uint64_t)hi << 32) | lo) + (uint64_t)((int64_t)ci * 64);
+    return __longlong_as_double((long long)bits);
+}
+
 // Sum without the final renormalisation (s, e): enough when the result only
 // feeds further pair arithmetic.
 __device__ __forceinline__ df df_add_lazy(df a, df b)

@@ -76,6 +76,7 @@ struct HostMesh {
     bool lattice = false;               // order-1 box lattice in canonical numbering
     int lat_n[3] = {1, 1, 1};           // cells per axis
     std::vector<float2> sectors;        // [2^d][d][d] Walsh-sector blocks of K^0 (empty: no split)
+    int lat_kshift = 0;                 // 3D: the kappa pairs hold kappa 2^-lat_kshift
     int max_deg = 0;
 };
 
@@ -148,7 +149,8 @@ cudaError_t launch_Ku(const soptx_mesh_s &m, const double *rho, const double *u,
                       double *out, cudaStream_t st);
 int64_t sensitivity_scratch_len(const soptx_mesh_s &m);
 cudaError_t launch_lattice_assemble(const soptx_mesh_s &m, const double *rho, double *vals, cudaStream_t st);
-void build_lattice_kappa(int dim, const std::vector<double> &K0, std::vector<float2> &kappa);
+bool lattice_kappa_shift(int dim, const std::vector<double> &K0, int &shift);
+void build_lattice_kappa(int dim, const std::vector<double> &K0, int shift, std::vector<float2> &kappa);
 bool build_lattice_sectors(int dim, const std::vector<double> &K0, double zero_tol, std::vector<float2> &B);
 cudaError_t launch_lattice_sensitivity(const soptx_mesh_s &m, const double *rho, const double *u, double *out,
                                        double *c, const double *gscale, cudaStream_t st);

@@ -195,7 +195,8 @@ __global__ void __launch_bounds__(WPB * 32, SOPTX_LATTICE_MINBLOCKS)
 k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restrict__ node_off,
                     const float2 *__restrict__ Edf, const float2 *__restrict__ kappa_g,
                     const double *__restrict__ K0, const double *__restrict__ rho, SimpParams sp,
-                    double *__restrict__ vals, const unsigned *__restrict__ flag, unsigned gen)
+                    double *__restrict__ vals, const unsigned *__restrict__ flag, unsigned gen,
+                    uint32_t pbias, double kscale)
 {
     const int lane = threadIdx.x & 31;
     const int dl = lane < 27 ? lane : 26;
@@ -218,7 +219,7 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restric
     int buf = 0;
     for (int t = threadIdx.x; t < 27 * 9; t += blockDim.x) {
         kap_s[t] = kappa_g[t];
-        kapd_s[t] = (double)kappa_g[t].x + (double)kappa_g[t].y;
+        kapd_s[t] = ((double)kappa_g[t].x + (double)kappa_g[t].y) * kscale;
     }
     __syncthreads();
     // stage constants
@@ -295,7 +296,7 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restric
                     // the others multiply in float pairs and convert each entry.
                     double Td[kFp64Classes];
 #pragma unroll
-                    for (int q = 0; q < kFp64Classes; q++) Td[q] = df_to_double(T[q].h, T[q].l);
+                    for (int q = 0; q < kFp64Classes; q++) Td[q] = df_to_double_biased(T[q].h, T[q].l, 0x38000000u);
 #pragma unroll
                     for (int i = 0; i < 3; i++) {
                         double *row = stage + ph + i * rowlen + 3 * mi;
@@ -307,7 +308,7 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restric
                             } else {
                                 const float2 kv = kap_s[dl * 9 + i * 3 + j];
                                 const df v = df_mul_raw(df{kv.x, kv.y}, T[q]);
-                                row[j] = df_to_double(v.h, v.l);
+                                row[j] = df_to_double_biased(v.h, v.l, pbias);
                             }
                         }
                     }
@@ -653,7 +654,9 @@ cudaError_t launch_lattice_assemble(const soptx_mesh_s &m, const double *rho, do
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((chunks + WPB - 1) / WPB, 152 * 4));
         k_lattice_assemble3<WPB><<<grid, WPB * 32, 0, st>>>(h.lat_n[0], h.lat_n[1], h.lat_n[2], h.nn, m.d.node_off,
                                                             (const float2 *)m.d.Edf, (const float2 *)m.d.kappa,
-                                                            m.d.K0, rho, sp, vals, m.d.lat_bad, gen);
+                                                            m.d.K0, rho, sp, vals, m.d.lat_bad, gen,
+                                                            0x38000000u + ((uint32_t)h.lat_kshift << 20),
+                                                            std::ldexp(1.0, h.lat_kshift));
     } else {
         const int64_t groups = (h.nn + 2) / 3;
         const int grid = (int)std::min<int64_t>((groups + WPB - 1) / WPB, 152 * 8);
@@ -666,11 +669,11 @@ cudaError_t launch_lattice_assemble(const soptx_mesh_s &m, const double *rho, do
 
 // kappa_delta[i][j] = K0[(a*, i), (b*, j)] for every offset delta (x fastest),
 // a*, b* the corners of n and n + delta in the reference cell (high side on
-// zero axes).  Stored as float pairs.
-void build_lattice_kappa(int dim, const std::vector<double> &K0, std::vector<float2> &kappa)
+// zero axes).
+static std::vector<double> lattice_kappa_values(int dim, const std::vector<double> &K0)
 {
     const int nd = dim == 3 ? 27 : 9, ldof = dim * (1 << dim);
-    kappa.assign((size_t)nd * dim * dim, make_float2(0.f, 0.f));
+    std::vector<double> kap((size_t)nd * dim * dim, 0.0);
     for (int dl = 0; dl < nd; dl++) {
         int a = 0, b = 0, r = dl;
         for (int m = 0; m < dim; m++) {
@@ -681,12 +684,39 @@ void build_lattice_kappa(int dim, const std::vector<double> &K0, std::vector<flo
             b |= bm << m;
         }
         for (int i = 0; i < dim; i++)
-            for (int j = 0; j < dim; j++) {
-                const double x = K0[(size_t)(dim * a + i) * ldof + dim * b + j];
-                const float hh = (float)x;
-                const float ll = (float)(x - (double)hh);
-                kappa[(size_t)dl * dim * dim + i * dim + j] = make_float2(hh, ll);
-            }
+            for (int j = 0; j < dim; j++)
+                kap[(size_t)dl * dim * dim + i * dim + j] = K0[(size_t)(dim * a + i) * ldof + dim * b + j];
+    }
+    return kap;
+}
+
+// The 3D assembly multiplies float pairs of kappa 2^-shift, |kappa| 2^-shift in
+// [2^-24, 2), and lets the conversion to FP64 put 2^shift back; with element
+// moduli in [2^-60, 2^60] its products then stay below 2^84, and a product
+// that falls below the FP32 normal range is off by less than 1e-12 of its
+// entry's scale.  False when the kappa entries span more than 2^24 (entries
+// below 2^-40 of the largest count as zeros); those boxes take the general path.
+bool lattice_kappa_shift(int dim, const std::vector<double> &K0, int &shift)
+{
+    const std::vector<double> kap = lattice_kappa_values(dim, K0);
+    double kmax = 0.0, kmin = INFINITY;
+    for (double x : kap) kmax = std::max(kmax, std::fabs(x));
+    for (double x : kap)
+        if (std::fabs(x) > std::ldexp(kmax, -40)) kmin = std::min(kmin, std::fabs(x));
+    if (!(kmax > 0.0) || !std::isfinite(kmax) || !(kmin >= std::ldexp(kmax, -24))) return false;
+    shift = std::ilogb(kmax);
+    return shift > -900 && shift < 900;
+}
+
+// The kappa table times 2^-shift as float pairs.
+void build_lattice_kappa(int dim, const std::vector<double> &K0, int shift, std::vector<float2> &kappa)
+{
+    const std::vector<double> kap = lattice_kappa_values(dim, K0);
+    kappa.resize(kap.size());
+    for (size_t t = 0; t < kap.size(); t++) {
+        const double x = std::ldexp(kap[t], -shift);
+        const float hh = (float)x;
+        kappa[t] = make_float2(hh, (float)(x - (double)hh));
     }
 }
 

@@ -172,6 +172,15 @@ def test_lattice_out_of_range_moduli_between_normal_calls(P):
         assert np.all(np.abs(vals - v) <= TOL64 * va + 1e-300)
 
 
+def test_extreme_box_aspect_takes_general_path(P):
+    """Boxes whose element matrix entries span more than 2^24 (aspect ratio
+    10^4) leave the lattice kernels for the general path, and still match."""
+    c, cl = W.structured_hex(4, 3, 3)
+    c = c * np.array([1.0, 1.0, 1e-4])
+    m, *_ = check_assembly(P, "hex", 1, c, cl, "fp64")
+    assert m.path == "uniform"
+
+
 def test_lattice_anisotropic_boxes(P):
     """Box cells with different edge lengths per axis and a shifted origin."""
     c, cl = W.structured_hex(6, 4, 3)
