@@ -77,7 +77,6 @@ __device__ __forceinline__ df df_from_double(double x)
 // Out-of-line rare paths: keeping them as real calls stops the compiler from
 // if-converting them into FP64-pipe work on every element of a hot loop.
 static __device__ __noinline__ df df_from_double_slow(double x) { return df_from_double(x); }
-static __device__ __noinline__ double df_to_double_slow(float h, float l) { return (double)h + (double)l; }
 
 // Split a double into a pair with integer operations (no FP64 pipe): h keeps
 // the leading 24 significand bits (truncated), l the remaining 29 bits
@@ -111,19 +110,24 @@ __device__ __forceinline__ df df_split_z(double x)
 // exponent, shift the mantissa); e is scaled so that one unit is 2^6 ulps of
 // that double, rounded to an integer (cvt.rni), and added to the 64-bit
 // pattern.  The result is within 2^-46 |p| of p + e.  Below a power of two the
-// lower binade has half the ulp, hence the doubled step.  Magnitudes under
-// 2^-81 (or zero) take the FP64 pipe out of line.
+// lower binade has half the ulp, hence the doubled step.  For |p| < 2^-81
+// (denormal p included) p and e are first scaled by 2^96, exactly, and the
+// exponent is lowered by 96 again; p = 0 gives a signed zero.  No FP64
+// instruction and no out-of-line path, so the conversion costs a hot loop no
+// registers across a call.
 __device__ __forceinline__ double df_to_double(float p, float e)
 {
-    const uint32_t hb = __float_as_uint(p);
+    const bool small = (__float_as_uint(p) & 0x7f800000u) < (46u << 23);
+    const float f = small ? 0x1p96f : 1.0f;
+    const uint32_t hb = __float_as_uint(__fmul_rn(p, f));
+    const float es = __fmul_rn(e, f);
     const uint32_t sign = hb & 0x80000000u;
     const uint32_t mag = hb & 0x7fffffffu;
-    if (mag < (46u << 23)) return df_to_double_slow(p, e);
-    const uint32_t hi = sign | ((mag >> 3) + 0x38000000u);
+    const uint32_t hi = mag ? (sign | ((mag >> 3) + (small ? 0x32000000u : 0x38000000u))) : sign;
     const uint32_t lo = mag << 29;
-    // scale = 2^(46 - E) with p's sign, E the unbiased exponent of p
+    // scale = 2^(46 - E) with p's sign, E the unbiased exponent of the (scaled) p
     const uint32_t sbits = ((300u << 23) - (mag & 0x7f800000u)) | sign;
-    int32_t ci = __float2int_rn(__fmul_rn(e, __uint_as_float(sbits)));
+    int32_t ci = __float2int_rn(__fmul_rn(es, __uint_as_float(sbits)));
     if ((mag & 0x007fffffu) == 0u && ci < 0) ci *= 2;       // just below a power of two
     const uint64_t bits = (((uint64_t)hi << 32) | lo) + (uint64_t)((int64_t)ci * 64);
     return __longlong_as_double((long long)bits);
