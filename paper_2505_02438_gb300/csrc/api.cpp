@@ -241,6 +241,12 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
             if (e != cudaSuccess) { cudaGetLastError(); s = cuda_status(e, "out-of-range flag"); }
             else B += (int64_t)bytes;
         }
+        if (s == SOPTX_OK && d.sectors) {
+            // u as float pairs, made once per call by the one-call step
+            cudaError_t e = dev_alloc((void **)&d.udf, (size_t)std::max<int64_t>(h.ndof, 1) * sizeof(float2));
+            if (e != cudaSuccess) { cudaGetLastError(); s = cuda_status(e, "displacement pairs"); }
+            else B += std::max<int64_t>(h.ndof, 1) * (int64_t)sizeof(float2);
+        }
         if (s == SOPTX_OK) s = cuda_status(cudaStreamSynchronize(st), "mesh setup");
     }
     if (s == SOPTX_OK && (m->path != SOPTX_PATH_LATTICE || !d.sectors)) {

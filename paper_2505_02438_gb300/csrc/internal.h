@@ -113,7 +113,7 @@ struct DeviceMesh {
     float2 *sectors = nullptr;     // [2^d][d][d] Walsh-sector blocks of K^0 (nullptr: no split)
     unsigned *lat_bad = nullptr;   // 3D: generation of the last call that met out-of-range moduli
     // general path
-    float2 *udf = nullptr;         // [ndof] u as float pairs
+    float2 *udf = nullptr;         // [ndof] u as float pairs (general path; lattice: one-call step)
     double *part = nullptr;        // [nc][nb] per-(cell, node) partials of u_e^T K_e^0 u_e
     // equilibrium solve (allocated by the first soptx_solve_cg)
     double *cg = nullptr;          // r z p q diag [ndof], scalars, partials, counters
@@ -155,6 +155,8 @@ bool build_lattice_sectors(int dim, const std::vector<double> &K0, double zero_t
 cudaError_t launch_lattice_sensitivity(const soptx_mesh_s &m, const double *rho, const double *u, double *out,
                                        double *c, const double *gscale, cudaStream_t st);
 int lattice_sens_grid(int64_t nc);
+cudaError_t launch_lattice_step(const soptx_mesh_s &m, const double *rho, const double *u, double *vals, double *dc,
+                                double *c, cudaStream_t st);
 cudaError_t launch_gather(const soptx_mesh_s &m, const double *rho, const double *u, double *vals, double *dc,
                           double *c, const double *gscale, cudaStream_t st);
 int gather_finalize_grid(int64_t nc);

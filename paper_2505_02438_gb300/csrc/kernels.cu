@@ -283,6 +283,7 @@ cudaError_t launch_sensitivity(const soptx_mesh_s &m, const double *rho, const d
 cudaError_t launch_step(const soptx_mesh_s &m, const double *rho, const double *u, double *vals, double *dc,
                         double *c, cudaStream_t st)
 {
+    if (m.path == SOPTX_PATH_LATTICE && m.d.sectors && m.h.nc > 0) return launch_lattice_step(m, rho, u, vals, dc, c, st);
     if (m.path == SOPTX_PATH_LATTICE || m.h.nc == 0) {
         cudaError_t err = launch_assemble(m, rho, vals, st);
         if (err != cudaSuccess) return err;

@@ -333,7 +333,8 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restric
     if (lane == 0) bulk_wait_all();
 }
 
-// Element moduli as float pairs.  With `flag` given (3D lattice), a warp
+// Element moduli as float pairs (and, with u given, u as float pairs).  With
+// `flag` given (3D lattice), a warp
 // whose cells include moduli outside the float-pair range (NaN low word)
 // stores `gen` in *flag and writes the rows of the nodes around each such
 // cell in plain FP64, lanes over the offsets; the assembly kernel then skips
@@ -342,10 +343,16 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restric
 __global__ void k_simp_df(int nx, int ny, int nz, int64_t nc, const double *__restrict__ rho, SimpParams sp,
                           float2 *__restrict__ Edf, const int64_t *__restrict__ node_off,
                           const double *__restrict__ K0, double *__restrict__ vals, unsigned *__restrict__ flag,
-                          unsigned gen)
+                          unsigned gen, int64_t ndof, const double *__restrict__ u, float2 *__restrict__ udf)
 {
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // with u given (one call doing both passes), u as float pairs for the sensitivity kernel
+    if (u)
+        for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < ndof; r += stride) {
+            const df v = df_split(u[r]);
+            udf[r] = make_float2(v.h, v.l);
+        }
     for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); e0 < nc; e0 += stride) {
         const int64_t e = e0 + lane;
         bool isbad = false;
@@ -491,9 +498,17 @@ __host__ __device__ constexpr bool sector_zero(int c, int i, int j)
 #ifndef SOPTX_SENS_MINB
 #define SOPTX_SENS_MINB 8
 #endif
-template <int D>
+// Displacement entries: doubles split on the fly, or float pairs made once per call.
+__device__ __forceinline__ df load_u(const double *__restrict__ u, int64_t r) { return df_split(u[r]); }
+__device__ __forceinline__ df load_u(const float2 *__restrict__ u, int64_t r)
+{
+    const float2 v = u[r];
+    return df{v.x, v.y};
+}
+
+template <int D, typename UT>
 __global__ void __launch_bounds__(128, SOPTX_SENS_MINB)
-k_lattice_sens(int nx, int ny, int64_t nc, const double *__restrict__ rho, const double *__restrict__ u,
+k_lattice_sens(int nx, int ny, int64_t nc, const double *__restrict__ rho, const UT *__restrict__ u,
                SimpParams sp, const SectorTable<D> B, const double *__restrict__ gscale,
                double *__restrict__ out, double *__restrict__ partial, unsigned *__restrict__ counter,
                double *__restrict__ c)
@@ -513,7 +528,7 @@ k_lattice_sens(int nx, int ny, int64_t nc, const double *__restrict__ rho, const
             const int64_t node = (int64_t)(ex + (a & 1)) +
                                  (int64_t)(nx + 1) * ((ey + ((a >> 1) & 1)) + (int64_t)(ny + 1) * (ez + (a >> 2)));
 #pragma unroll
-            for (int i = 0; i < D; i++) w[a][i] = df_split(u[D * node + i]);
+            for (int i = 0; i < D; i++) w[a][i] = load_u(u, D * node + i);
         }
         // in-place Walsh transform along each axis
 #pragma unroll
@@ -572,21 +587,28 @@ static SectorTable<D> sector_table(const std::vector<float2> &v)
     return B;
 }
 
-cudaError_t launch_lattice_sensitivity(const soptx_mesh_s &m, const double *rho, const double *u, double *out,
-                                       double *c, const double *gscale, cudaStream_t st)
+template <typename UT>
+static cudaError_t lattice_sens_t(const soptx_mesh_s &m, const double *rho, const UT *u, double *out, double *c,
+                                  const double *gscale, cudaStream_t st)
 {
     const auto &h = m.h;
     const int grid = lattice_sens_grid(h.nc);
     if ((int)h.sectors.size() != (h.dim << h.dim) * h.dim) return cudaErrorInvalidValue;
     if (h.dim == 3)
-        k_lattice_sens<3><<<grid, kSensThreads, 0, st>>>(h.lat_n[0], h.lat_n[1], h.nc, rho, u, simp_params(m.mat),
-                                                         sector_table<3>(h.sectors), gscale, out, m.d.scratch,
-                                                         m.d.counter, c);
+        k_lattice_sens<3, UT><<<grid, kSensThreads, 0, st>>>(h.lat_n[0], h.lat_n[1], h.nc, rho, u,
+                                                             simp_params(m.mat), sector_table<3>(h.sectors), gscale,
+                                                             out, m.d.scratch, m.d.counter, c);
     else
-        k_lattice_sens<2><<<grid, kSensThreads, 0, st>>>(h.lat_n[0], h.lat_n[1], h.nc, rho, u, simp_params(m.mat),
-                                                         sector_table<2>(h.sectors), gscale, out, m.d.scratch,
-                                                         m.d.counter, c);
+        k_lattice_sens<2, UT><<<grid, kSensThreads, 0, st>>>(h.lat_n[0], h.lat_n[1], h.nc, rho, u,
+                                                             simp_params(m.mat), sector_table<2>(h.sectors), gscale,
+                                                             out, m.d.scratch, m.d.counter, c);
     return cudaGetLastError();
+}
+
+cudaError_t launch_lattice_sensitivity(const soptx_mesh_s &m, const double *rho, const double *u, double *out,
+                                       double *c, const double *gscale, cudaStream_t st)
+{
+    return lattice_sens_t(m, rho, u, out, c, gscale, st);
 }
 
 // Sector blocks B_c[i][j] of a box element's K^0 (see k_lattice_sens), the
@@ -634,7 +656,10 @@ bool build_lattice_sectors(int dim, const std::vector<double> &K0, double zero_t
     return true;
 }
 
-cudaError_t launch_lattice_assemble(const soptx_mesh_s &m, const double *rho, double *vals, cudaStream_t st)
+// The assembly; with u given (and m.d.udf), the moduli kernel also leaves u
+// as float pairs in m.d.udf for the sensitivity of the same step.
+static cudaError_t lattice_assemble_u(const soptx_mesh_s &m, const double *rho, const double *u, double *vals,
+                                      cudaStream_t st)
 {
     const auto &h = m.h;
     const SimpParams sp = simp_params(m.mat);
@@ -645,7 +670,8 @@ cudaError_t launch_lattice_assemble(const soptx_mesh_s &m, const double *rho, do
     if (gen == 0u) gen = ++m.lattice_gen;
     k_simp_df<<<std::max(egrid, 1), eb, 0, st>>>(h.lat_n[0], h.lat_n[1], h.lat_n[2], h.nc, rho, sp,
                                                  (float2 *)m.d.Edf, m.d.node_off, m.d.K0, vals,
-                                                 h.dim == 3 ? m.d.lat_bad : nullptr, gen);
+                                                 h.dim == 3 ? m.d.lat_bad : nullptr, gen, h.ndof,
+                                                 m.d.udf ? u : nullptr, m.d.udf);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     constexpr int WPB = 8;
@@ -665,6 +691,26 @@ cudaError_t launch_lattice_assemble(const soptx_mesh_s &m, const double *rho, do
                                                             m.d.K0, rho, sp, vals);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_lattice_assemble(const soptx_mesh_s &m, const double *rho, double *vals, cudaStream_t st)
+{
+    return lattice_assemble_u(m, rho, nullptr, vals, st);
+}
+
+// One call doing both passes: u is split into float pairs once, by the moduli
+// kernel, instead of at every corner of every cell.
+cudaError_t launch_lattice_step(const soptx_mesh_s &m, const double *rho, const double *u, double *vals, double *dc,
+                                double *c, cudaStream_t st)
+{
+    if (!m.d.udf || !u) {
+        cudaError_t err = lattice_assemble_u(m, rho, nullptr, vals, st);
+        if (err != cudaSuccess) return err;
+        return launch_lattice_sensitivity(m, rho, u, dc, c, nullptr, st);
+    }
+    cudaError_t err = lattice_assemble_u(m, rho, u, vals, st);
+    if (err != cudaSuccess) return err;
+    return lattice_sens_t(m, rho, (const float2 *)m.d.udf, dc, c, nullptr, st);
 }
 
 // kappa_delta[i][j] = K0[(a*, i), (b*, j)] for every offset delta (x fastest),
