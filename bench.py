@@ -157,14 +157,23 @@ def job_rate(units_per_rank, world, steps, ms_total):
     return world * units_per_rank * steps / (ms_total / 1e3)
 
 
+def kernel_source_sha(kernel_file):
+    """First 16 hex digits of the sha256 of a kernel file and the device headers it includes."""
+    csrc = os.path.join(ROOT, "paper_2505_02438_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in (kernel_file, "df64.cuh", "kernels_common.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_record(kernel_file, kernel_name):
     """dram bytes per launch of `kernel_name` from the committed ncu summary,
-    valid only while the kernel source is unchanged (its sha256 matches)."""
+    valid only while the kernel source is unchanged (kernel_source_sha matches)."""
     src = os.path.join(ROOT, "paper_2505_02438_gb300", "csrc", kernel_file)
     rec = os.path.join(ROOT, "profiles", "traffic.txt")
     if not (os.path.exists(src) and os.path.exists(rec)):
         return None
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = kernel_source_sha(kernel_file)
     for line in open(rec):
         kv = dict(x.split("=", 1) for x in line.split() if "=" in x)
         if kv.get("kernel") == kernel_name and kv.get("source_sha") == h:
