@@ -347,12 +347,21 @@ __global__ void k_simp_df(int nx, int ny, int nz, int64_t nc, const double *__re
 {
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // with u given (one call doing both passes), u as float pairs for the sensitivity kernel
-    if (u)
-        for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < ndof; r += stride) {
+    // with u given (one call doing both passes), u as float pairs for the sensitivity
+    // kernel, two dofs per thread and pass (16-byte loads and stores when u allows)
+    if (u) {
+        const bool vec = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(udf)) & 15u) == 0u;
+        const int64_t npair = vec ? ndof / 2 : 0;
+        for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < npair; r += stride) {
+            const double2 x = __ldcs(reinterpret_cast<const double2 *>(u) + r);
+            const df a = df_split(x.x), b = df_split(x.y);
+            reinterpret_cast<float4 *>(udf)[r] = make_float4(a.h, a.l, b.h, b.l);
+        }
+        for (int64_t r = 2 * npair + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < ndof; r += stride) {
             const df v = df_split(u[r]);
             udf[r] = make_float2(v.h, v.l);
         }
+    }
     for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); e0 < nc; e0 += stride) {
         const int64_t e = e0 + lane;
         bool isbad = false;
@@ -664,7 +673,8 @@ static cudaError_t lattice_assemble_u(const soptx_mesh_s &m, const double *rho, 
     const auto &h = m.h;
     const SimpParams sp = simp_params(m.mat);
     const int eb = 256;
-    const int egrid = (int)std::min<int64_t>((h.nc + eb - 1) / eb, 152 * 8);
+    const int64_t items = std::max<int64_t>(h.nc, (u && m.d.udf) ? h.ndof / 2 : 0);
+    const int egrid = (int)std::min<int64_t>((items + eb - 1) / eb, 152 * 8);
     // a fresh nonzero generation per call marks this call's out-of-range flag
     unsigned gen = ++m.lattice_gen;
     if (gen == 0u) gen = ++m.lattice_gen;
