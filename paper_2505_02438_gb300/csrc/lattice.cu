@@ -34,6 +34,15 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Programmatic dependent launch (PTX griddepcontrol, sm_90 and later).  A
+// kernel launched with the programmatic-serialization attribute may be
+// scheduled while the kernel before it in the stream is still running, once
+// every block of that kernel has executed launch_dependents; its wait blocks
+// until that kernel has completed and its writes are visible.  In a kernel
+// launched without the attribute both are no-ops.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ df shfl_df(df v, int src)
 {
     return df{__shfl_sync(kFull, v.h, src), __shfl_sync(kFull, v.l, src)};
@@ -222,6 +231,11 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restric
         kapd_s[t] = ((double)kappa_g[t].x + (double)kappa_g[t].y) * kscale;
     }
     __syncthreads();
+    // the moduli (and the flag) come from k_simp_df, launched just before; once every
+    // block is past this wait, k_simp_df has completed and the sensitivity of a
+    // one-call step, which reads only its outputs, may start on SMs this kernel frees
+    grid_dep_wait();
+    grid_dep_launch();
     // stage constants
     const int ox = lane & 3, oy = (lane >> 2) & 3;
     const int yzx = (lane >> 2) & 3;            // stage X: (cy, cz) of lanes 0..15
@@ -345,6 +359,7 @@ __global__ void k_simp_df(int nx, int ny, int nz, int64_t nc, const double *__re
                           const double *__restrict__ K0, double *__restrict__ vals, unsigned *__restrict__ flag,
                           unsigned gen, int64_t ndof, const double *__restrict__ u, float2 *__restrict__ udf)
 {
+    grid_dep_launch();   // the assembly may be scheduled now; it waits for this kernel before reading
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     // with u given (one call doing both passes), u as float pairs for the sensitivity
@@ -596,13 +611,37 @@ static SectorTable<D> sector_table(const std::vector<float2> &v)
     return B;
 }
 
+// Launch with the programmatic-serialization attribute (see grid_dep_wait).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_dependent(void (*kern)(KArgs...), int grid, int block, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 template <typename UT>
 static cudaError_t lattice_sens_t(const soptx_mesh_s &m, const double *rho, const UT *u, double *out, double *c,
-                                  const double *gscale, cudaStream_t st)
+                                  const double *gscale, cudaStream_t st, bool after_assembly = false)
 {
     const auto &h = m.h;
     const int grid = lattice_sens_grid(h.nc);
     if ((int)h.sectors.size() != (h.dim << h.dim) * h.dim) return cudaErrorInvalidValue;
+    if (after_assembly && h.dim == 3) {
+        // in the one-call step, right after the 3D assembly, whose blocks let it start
+        // once the moduli kernel (the producer of u's pairs) has completed
+        return launch_dependent(k_lattice_sens<3, UT>, grid, kSensThreads, st, h.lat_n[0], h.lat_n[1], h.nc, rho,
+                                u, simp_params(m.mat), sector_table<3>(h.sectors), gscale, out, m.d.scratch,
+                                m.d.counter, c);
+    }
     if (h.dim == 3)
         k_lattice_sens<3, UT><<<grid, kSensThreads, 0, st>>>(h.lat_n[0], h.lat_n[1], h.nc, rho, u,
                                                              simp_params(m.mat), sector_table<3>(h.sectors), gscale,
@@ -688,11 +727,19 @@ static cudaError_t lattice_assemble_u(const soptx_mesh_s &m, const double *rho, 
     if (h.dim == 3) {
         const int64_t chunks = (h.nn + kChunk - 1) / kChunk;
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((chunks + WPB - 1) / WPB, 152 * 4));
-        k_lattice_assemble3<WPB><<<grid, WPB * 32, 0, st>>>(h.lat_n[0], h.lat_n[1], h.lat_n[2], h.nn, m.d.node_off,
-                                                            (const float2 *)m.d.Edf, (const float2 *)m.d.kappa,
-                                                            m.d.K0, rho, sp, vals, m.d.lat_bad, gen,
-                                                            0x38000000u + ((uint32_t)h.lat_kshift << 20),
-                                                            std::ldexp(1.0, h.lat_kshift));
+        if (u && m.d.udf) {
+            // one-call step: scheduled while the moduli kernel runs (see grid_dep_wait)
+            err = launch_dependent(k_lattice_assemble3<WPB>, grid, WPB * 32, st, h.lat_n[0], h.lat_n[1],
+                                   h.lat_n[2], h.nn, m.d.node_off, (const float2 *)m.d.Edf,
+                                   (const float2 *)m.d.kappa, m.d.K0, rho, sp, vals, m.d.lat_bad, gen,
+                                   0x38000000u + ((uint32_t)h.lat_kshift << 20), std::ldexp(1.0, h.lat_kshift));
+            if (err != cudaSuccess) return err;
+        } else {
+            k_lattice_assemble3<WPB><<<grid, WPB * 32, 0, st>>>(
+                h.lat_n[0], h.lat_n[1], h.lat_n[2], h.nn, m.d.node_off, (const float2 *)m.d.Edf,
+                (const float2 *)m.d.kappa, m.d.K0, rho, sp, vals, m.d.lat_bad, gen,
+                0x38000000u + ((uint32_t)h.lat_kshift << 20), std::ldexp(1.0, h.lat_kshift));
+        }
     } else {
         const int64_t groups = (h.nn + 2) / 3;
         const int grid = (int)std::min<int64_t>((groups + WPB - 1) / WPB, 152 * 8);
@@ -720,7 +767,7 @@ cudaError_t launch_lattice_step(const soptx_mesh_s &m, const double *rho, const 
     }
     cudaError_t err = lattice_assemble_u(m, rho, u, vals, st);
     if (err != cudaSuccess) return err;
-    return lattice_sens_t(m, rho, (const float2 *)m.d.udf, dc, c, nullptr, st);
+    return lattice_sens_t(m, rho, (const float2 *)m.d.udf, dc, c, nullptr, st, true);
 }
 
 // kappa_delta[i][j] = K0[(a*, i), (b*, j)] for every offset delta (x fastest),
