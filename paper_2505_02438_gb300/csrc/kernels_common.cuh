@@ -67,6 +67,32 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// Programmatic dependent launch (PTX griddepcontrol, sm_90 and later).  A
+// kernel launched with the programmatic-serialization attribute may be
+// scheduled while the kernel before it in the stream is still running, once
+// every block of that kernel has executed launch_dependents; its wait blocks
+// until that kernel has completed and its writes are visible.  In a kernel
+// launched without the attribute both are no-ops.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launch with the programmatic-serialization attribute (see grid_dep_wait).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dependent(void (*kern)(KArgs...), int grid, int block, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 struct Material;
 SimpParams simp_params(const Material &m);
 

@@ -34,15 +34,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// Programmatic dependent launch (PTX griddepcontrol, sm_90 and later).  A
-// kernel launched with the programmatic-serialization attribute may be
-// scheduled while the kernel before it in the stream is still running, once
-// every block of that kernel has executed launch_dependents; its wait blocks
-// until that kernel has completed and its writes are visible.  In a kernel
-// launched without the attribute both are no-ops.
-__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
 __device__ __forceinline__ df shfl_df(df v, int src)
 {
     return df{__shfl_sync(kFull, v.h, src), __shfl_sync(kFull, v.l, src)};
@@ -609,23 +600,6 @@ static SectorTable<D> sector_table(const std::vector<float2> &v)
     SectorTable<D> B;
     for (int t = 0; t < (1 << D) * D * D; t++) B.b[t] = v[t];
     return B;
-}
-
-// Launch with the programmatic-serialization attribute (see grid_dep_wait).
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_dependent(void (*kern)(KArgs...), int grid, int block, cudaStream_t st, Args... args)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3((unsigned)block);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
 template <typename UT>

@@ -88,6 +88,9 @@ k_spmv(int64_t nn, const int64_t *__restrict__ node_off, const int32_t *__restri
        const uint8_t *__restrict__ fixed, const double *__restrict__ dotv, double *__restrict__ partial,
        unsigned *__restrict__ counter, double *__restrict__ dot_out)
 {
+    // inside the CG loop this kernel is a dependent launch: nothing is read before the wait
+    grid_dep_wait();
+    grid_dep_launch();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 3, c = lane & 7;       // 4 nodes per warp, 8 lanes per node
     double mine = 0.0;
@@ -179,7 +182,7 @@ k_spmv(int64_t nn, const int64_t *__restrict__ node_off, const int32_t *__restri
     }
 }
 
-// diag[row] = K[row][row]: the diagonal sits in the node's own column block;
+// diag[row] = 1 / K[row][row] (1 on constrained rows): the diagonal sits in the node's own column block;
 // a binary search over row 0's sorted columns finds it.  A free row with a
 // non-positive diagonal raises *bad.
 template <int D>
@@ -204,7 +207,9 @@ __global__ void k_diag(int64_t nn, const int64_t *__restrict__ node_off, const i
         double dv = 0.0;
         if (lo < len && cols[lo] == want) dv = vals[base + (int64_t)i * len + lo + i];
         const bool fx = fixed[r] != 0;
-        diag[r] = fx ? 1.0 : dv;
+        // the Jacobi preconditioner is applied as a product with the reciprocal: an
+        // FP64 division per dof per iteration costs more than the rest of the update
+        diag[r] = fx ? 1.0 : (dv > 0.0 ? 1.0 / dv : 0.0);
         if (!fx && !(dv > 0.0)) atomicExch(bad, 1);
     }
 }
@@ -217,17 +222,17 @@ __global__ void k_cg_zero_free(int64_t ndof, const uint8_t *__restrict__ fixed, 
 }
 
 // r = f - K u_D on the free rows (q holds K u_D with constrained rows zeroed),
-// z = r / diag, p = z; sums r.z and r.r
+// z = r / diag (as r times the stored reciprocal), p = z; sums r.z and r.r
 __global__ void __launch_bounds__(kCgThreads)
 k_cg_start(int64_t ndof, const uint8_t *__restrict__ fixed, const double *__restrict__ f,
-           const double *__restrict__ q, const double *__restrict__ diag, double *__restrict__ r,
+           const double *__restrict__ q, const double *__restrict__ dinv, double *__restrict__ r,
            double *__restrict__ z, double *__restrict__ p, double *__restrict__ partial,
            unsigned *__restrict__ counter, double *__restrict__ out)
 {
     double m[2] = {0.0, 0.0};
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < ndof; k += (int64_t)gridDim.x * blockDim.x) {
         const double rv = fixed[k] ? 0.0 : f[k] - q[k];
-        const double zv = rv / diag[k];
+        const double zv = rv * dinv[k];
         r[k] = rv;
         z[k] = zv;
         p[k] = zv;
@@ -237,26 +242,52 @@ k_cg_start(int64_t ndof, const uint8_t *__restrict__ fixed, const double *__rest
     grid_sums<2>(m, partial, counter, out);
 }
 
-// alpha = (r.z) / (p.q); u += alpha p; r -= alpha q; z = r / diag; sums r.z, r.r
+// alpha = (r.z) / (p.q); u += alpha p; r -= alpha q; z = r / diag (times the reciprocal); sums r.z, r.r
 __global__ void __launch_bounds__(kCgThreads)
-k_cg_step(int64_t ndof, const uint8_t *__restrict__ fixed, const double *__restrict__ diag,
+k_cg_step(int64_t ndof, const uint8_t *__restrict__ fixed, const double *__restrict__ dinv,
           const double *__restrict__ p, const double *__restrict__ q, double *__restrict__ u,
           double *__restrict__ r, double *__restrict__ z, const double *__restrict__ rz_old,
           const double *__restrict__ pq, double *__restrict__ partial, unsigned *__restrict__ counter,
           double *__restrict__ out)
 {
-    const double den = *pq;
-    const double alpha = den != 0.0 ? *rz_old / den : 0.0;
+    grid_dep_wait();
+    grid_dep_launch();
+    // one FP64 division per block (a division per thread would cost more than the pass)
+    __shared__ double alpha_s;
+    if (threadIdx.x == 0) {
+        const double den = *pq;
+        alpha_s = den != 0.0 ? *rz_old / den : 0.0;
+    }
+    __syncthreads();
+    const double alpha = alpha_s;
     double m[2] = {0.0, 0.0};
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < ndof; k += (int64_t)gridDim.x * blockDim.x) {
-        if (fixed[k]) continue;
-        u[k] = fma(alpha, p[k], u[k]);
-        const double rv = fma(-alpha, q[k], r[k]);
-        const double zv = rv / diag[k];
-        r[k] = rv;
-        z[k] = zv;
-        m[0] = fma(rv, zv, m[0]);
-        m[1] = fma(rv, rv, m[1]);
+    // four dofs per thread and pass, their loads issued together
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k0 < ndof; k0 += 4 * stride) {
+        double pv[4], qv[4], uv[4], rv[4], dv[4];
+        bool on[4];
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            const int64_t k = k0 + t * stride;
+            on[t] = k < ndof && !fixed[k];
+            pv[t] = on[t] ? p[k] : 0.0;
+            qv[t] = on[t] ? q[k] : 0.0;
+            uv[t] = on[t] ? u[k] : 0.0;
+            rv[t] = on[t] ? r[k] : 0.0;
+            dv[t] = on[t] ? dinv[k] : 0.0;
+        }
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            if (!on[t]) continue;
+            const int64_t k = k0 + t * stride;
+            u[k] = fma(alpha, pv[t], uv[t]);
+            const double rn = fma(-alpha, qv[t], rv[t]);
+            const double zv = rn * dv[t];
+            r[k] = rn;
+            z[k] = zv;
+            m[0] = fma(rn, zv, m[0]);
+            m[1] = fma(rn, rn, m[1]);
+        }
     }
     grid_sums<2>(m, partial, counter, out);
 }
@@ -266,21 +297,46 @@ __global__ void k_cg_direction(int64_t ndof, const uint8_t *__restrict__ fixed, 
                                double *__restrict__ p, const double *__restrict__ rz_new,
                                const double *__restrict__ rz_old)
 {
-    const double den = *rz_old;
-    const double beta = den != 0.0 ? *rz_new / den : 0.0;
+    grid_dep_wait();
+    grid_dep_launch();
+    __shared__ double beta_s;
+    if (threadIdx.x == 0) {
+        const double den = *rz_old;
+        beta_s = den != 0.0 ? *rz_new / den : 0.0;
+    }
+    __syncthreads();
+    const double beta = beta_s;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < ndof; k += (int64_t)gridDim.x * blockDim.x)
         p[k] = fixed[k] ? 0.0 : fma(beta, p[k], z[k]);
 }
 
 int spmv_grid(int64_t nn) { return (int)std::max<int64_t>(1, std::min<int64_t>((nn + 2 * kSpWarps - 1) / (2 * kSpWarps), 152 * 8)); }
-int cg_grid(int64_t ndof) { return (int)std::max<int64_t>(1, std::min<int64_t>((ndof + kCgThreads - 1) / kCgThreads, 152 * 4)); }
+// Passes with a grid sum: two blocks per SM, each thread taking several dofs (the
+// FP64 butterfly of the sum is paid once per thread).  Plain passes: one dof per
+// thread up to 152 x 32 blocks, so that all their loads are in flight at once.
+#ifndef SOPTX_CG_BLOCKS_PER_SM
+#define SOPTX_CG_BLOCKS_PER_SM 2
+#endif
+int cg_grid(int64_t ndof) { return (int)std::max<int64_t>(1, std::min<int64_t>((ndof + kCgThreads - 1) / kCgThreads, 152 * SOPTX_CG_BLOCKS_PER_SM)); }
+static int cg_grid_wide(int64_t ndof)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>((ndof + kCgThreads - 1) / kCgThreads, 152 * 32));
+}
 
 cudaError_t launch_spmv(const soptx_mesh_s &m, const double *vals, const double *x, double *y, const uint8_t *fixed,
-                        const double *dotv, double *partial, unsigned *counter, double *dot_out, cudaStream_t st)
+                        const double *dotv, double *partial, unsigned *counter, double *dot_out, cudaStream_t st,
+                        bool dependent = false)
 {
     const auto &h = m.h;
     if (h.nn == 0) return cudaSuccess;
     const int grid = spmv_grid(h.nn);
+    if (dependent) {
+        if (h.dim == 3)
+            return launch_dependent(k_spmv<3>, grid, kSpWarps * 32, st, h.nn, m.d.node_off, m.d.indices, vals, x, y,
+                                    fixed, dotv, partial, counter, dot_out);
+        return launch_dependent(k_spmv<2>, grid, kSpWarps * 32, st, h.nn, m.d.node_off, m.d.indices, vals, x, y,
+                                fixed, dotv, partial, counter, dot_out);
+    }
     if (h.dim == 3)
         k_spmv<3><<<grid, kSpWarps * 32, 0, st>>>(h.nn, m.d.node_off, m.d.indices, vals, x, y, fixed, dotv, partial,
                                                   counter, dot_out);
@@ -331,7 +387,7 @@ soptx_status soptx_solve_cg(soptx_mesh m, const double *d_vals, const uint8_t *d
     auto &d = m->d;
     const int sgrid = spmv_grid(h.nn), cgrid = cg_grid(h.ndof);
     const int pmax = std::max(sgrid, cgrid);
-    // workspace: r z p q diag [ndof], scalars [8], partials [2][pmax], counters, flag
+    // workspace: r z p q 1/diag [ndof], scalars [8], partials [2][pmax], counters, flag
     if (!d.cg) {
         const size_t bytes = ((size_t)5 * h.ndof + 8 + 2 * (size_t)pmax) * sizeof(double) + 64;
         void *p = nullptr;
@@ -346,7 +402,8 @@ soptx_status soptx_solve_cg(soptx_mesh m, const double *d_vals, const uint8_t *d
         m->device_bytes += (int64_t)bytes;
     }
     double *r = d.cg, *z = r + h.ndof, *pv = z + h.ndof, *q = pv + h.ndof, *diag = q + h.ndof;
-    double *S = diag + h.ndof;              // 0,1: r.z (ping-pong)  2: p.q  3: r.r
+    // scalars: 2: p.q; 4,5 and 6,7: (r.z, r.r) of the even and odd iterates (ping-pong)
+    double *S = diag + h.ndof;
     double *partial = S + 8;
     unsigned *counter = (unsigned *)(partial + 2 * (size_t)pmax);
     int *bad = (int *)(counter + 4);
@@ -374,10 +431,10 @@ soptx_status soptx_solve_cg(soptx_mesh m, const double *d_vals, const uint8_t *d
     }
     if (e == cudaSuccess) e = launch_spmv(*m, d_vals, z, q, d_fixed, nullptr, nullptr, nullptr, nullptr, st);
     if (e == cudaSuccess) {
-        k_cg_start<<<cgrid, kCgThreads, 0, st>>>(h.ndof, d_fixed, d_f, q, diag, r, z, pv, partial, counter, S + 2);
+        k_cg_start<<<cgrid, kCgThreads, 0, st>>>(h.ndof, d_fixed, d_f, q, diag, r, z, pv, partial, counter, S + 4);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&rr0, S + 3, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&rr0, S + 5, sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "soptx_solve_cg");
     // start: u = u_D and 0 (or the given guess) on the free rows, r = f - K u, z = p = r / diag
@@ -387,13 +444,11 @@ soptx_status soptx_solve_cg(soptx_mesh m, const double *d_vals, const uint8_t *d
     }
     if (e == cudaSuccess) e = launch_spmv(*m, d_vals, d_u, q, d_fixed, nullptr, nullptr, nullptr, nullptr, st);
     if (e == cudaSuccess) {
-        k_cg_start<<<cgrid, kCgThreads, 0, st>>>(h.ndof, d_fixed, d_f, q, diag, r, z, pv, partial, counter, S + 2);
+        k_cg_start<<<cgrid, kCgThreads, 0, st>>>(h.ndof, d_fixed, d_f, q, diag, r, z, pv, partial, counter, S + 4);
         e = cudaGetLastError();
     }
-    // k_cg_start wrote (r.z, r.r) to S[2], S[3]; move r.z into the ping-pong slot 0
-    if (e == cudaSuccess) e = cudaMemcpyAsync(S, S + 2, sizeof(double), cudaMemcpyDeviceToDevice, st);
     double rr = 0.0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&rr, S + 3, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&rr, S + 5, sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "soptx_solve_cg");
     const double r0 = std::sqrt(rr0);
@@ -405,24 +460,22 @@ soptx_status soptx_solve_cg(soptx_mesh m, const double *d_vals, const uint8_t *d
     int it = 0;
     while (it < o->max_iter) {
         const int par = it & 1;
-        double *rz_old = S + par, *rz_new = S + (par ^ 1);
+        double *old_pair = S + 4 + 2 * par, *new_pair = S + 4 + 2 * (par ^ 1);
+        // Each kernel of the iteration is a dependent launch: it is scheduled while the
+        // one before it finishes and waits for it before reading anything.
         // q = K p (constrained rows zero), p.q -> S[2]
-        e = launch_spmv(*m, d_vals, pv, q, d_fixed, pv, partial, counter, S + 2, st);
+        e = launch_spmv(*m, d_vals, pv, q, d_fixed, pv, partial, counter, S + 2, st, true);
         if (e != cudaSuccess) break;
-        // u, r, z; (r.z, r.r) -> rz_new, S[3] through a two-slot sum
-        k_cg_step<<<cgrid, kCgThreads, 0, st>>>(h.ndof, d_fixed, diag, pv, q, d_u, r, z, rz_old, S + 2, partial,
-                                                counter, S + 4);
-        e = cudaGetLastError();
+        // u, r, z; (r.z, r.r) -> the other pair
+        e = launch_dependent(k_cg_step, cgrid, kCgThreads, st, h.ndof, d_fixed, diag, pv, q, d_u, r, z, old_pair,
+                             S + 2, partial, counter, new_pair);
         if (e != cudaSuccess) break;
-        e = cudaMemcpyAsync(rz_new, S + 4, sizeof(double), cudaMemcpyDeviceToDevice, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(S + 3, S + 5, sizeof(double), cudaMemcpyDeviceToDevice, st);
-        if (e != cudaSuccess) break;
-        k_cg_direction<<<cgrid, kCgThreads, 0, st>>>(h.ndof, d_fixed, z, pv, rz_new, rz_old);
-        e = cudaGetLastError();
+        e = launch_dependent(k_cg_direction, cg_grid_wide(h.ndof), kCgThreads, st, h.ndof, d_fixed, z, pv,
+                             new_pair, old_pair);
         if (e != cudaSuccess) break;
         it++;
         if (it % o->check_every == 0 || it == o->max_iter) {
-            e = cudaMemcpyAsync(&rr, S + 3, sizeof(double), cudaMemcpyDeviceToHost, st);
+            e = cudaMemcpyAsync(&rr, new_pair + 1, sizeof(double), cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) break;
             if (std::sqrt(rr) <= o->rtol * r0) {
