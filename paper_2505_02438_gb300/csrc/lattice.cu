@@ -345,7 +345,11 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restric
 // cell in plain FP64, lanes over the offsets; the assembly kernel then skips
 // those nodes.  A node next to several such cells is written again with the
 // same values.
-__global__ void k_simp_df(int nx, int ny, int nz, int64_t nc, const double *__restrict__ rho, SimpParams sp,
+#ifndef SOPTX_SIMP_MINB
+#define SOPTX_SIMP_MINB 8
+#endif
+__global__ void __launch_bounds__(256, SOPTX_SIMP_MINB)
+k_simp_df(int nx, int ny, int nz, int64_t nc, const double *__restrict__ rho, SimpParams sp,
                           float2 *__restrict__ Edf, const int64_t *__restrict__ node_off,
                           const double *__restrict__ K0, double *__restrict__ vals, unsigned *__restrict__ flag,
                           unsigned gen, int64_t ndof, const double *__restrict__ u, float2 *__restrict__ udf)
