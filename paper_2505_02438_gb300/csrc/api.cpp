@@ -37,6 +37,8 @@ static void free_device(DeviceMesh &d)
                     d.inc_e, d.inc_a, d.counter, d.xcell, d.qw, d.qdphi, d.qdgeo, d.cg, d.lat_bad};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (d.cg_exec) cudaGraphExecDestroy(d.cg_exec);
+    if (d.cg_cap) cudaStreamDestroy(d.cg_cap);
     d = DeviceMesh{};
 }
 

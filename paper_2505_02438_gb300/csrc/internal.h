@@ -117,6 +117,9 @@ struct DeviceMesh {
     double *part = nullptr;        // [nc][nb] per-(cell, node) partials of u_e^T K_e^0 u_e
     // equilibrium solve (allocated by the first soptx_solve_cg)
     double *cg = nullptr;          // r z p q diag [ndof], scalars, partials, counters
+    cudaGraphExec_t cg_exec = nullptr; // the CG iterations between two checks, as a graph
+    cudaStream_t cg_cap = nullptr;     // its capture stream
+    const void *cg_key[4] = {};        // vals, fixed, u and the iteration count it was made for
 };
 
 struct Material {

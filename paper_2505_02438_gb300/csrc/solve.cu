@@ -457,25 +457,77 @@ soptx_status soptx_solve_cg(soptx_mesh m, const double *d_vals, const uint8_t *d
         res->rel_residual = r0 == 0.0 ? 0.0 : std::sqrt(rr) / r0;
         return SOPTX_OK;
     }
+    // One CG iteration: three dependent launches (each is scheduled while the one
+    // before it finishes and waits for it before reading anything).
+    auto iteration = [&](int it_, cudaStream_t s_) -> cudaError_t {
+        const int par = it_ & 1;
+        double *old_pair = S + 4 + 2 * par, *new_pair = S + 4 + 2 * (par ^ 1);
+        // q = K p (constrained rows zero), p.q -> S[2]
+        cudaError_t err = launch_spmv(*m, d_vals, pv, q, d_fixed, pv, partial, counter, S + 2, s_, true);
+        // u, r, z; (r.z, r.r) -> the other pair
+        if (err == cudaSuccess)
+            err = launch_dependent(k_cg_step, cgrid, kCgThreads, s_, h.ndof, d_fixed, diag, pv, q, d_u, r, z,
+                                   old_pair, S + 2, partial, counter, new_pair);
+        if (err == cudaSuccess)
+            err = launch_dependent(k_cg_direction, cg_grid_wide(h.ndof), kCgThreads, s_, h.ndof, d_fixed, z, pv,
+                                   new_pair, old_pair);
+        return err;
+    };
+    // Between two convergence checks (an even number of iterations, at most 100) the
+    // launches are replayed as one CUDA graph: the same kernels in the same order, so
+    // the iterates are bitwise those of the launch-by-launch loop, without the host's
+    // launch cost per kernel (the bound of small meshes).  The graph is kept with the
+    // mesh and updated in place when the call's vectors change.
+    const int G = (o->check_every % 2 == 0 && o->check_every <= 100) ? o->check_every : 0;
+    bool graph = G > 0 && o->max_iter >= G;
+    if (graph) {
+        const void *key[4] = {d_vals, d_fixed, d_u, (const void *)(intptr_t)G};
+        bool same = d.cg_exec != nullptr;
+        for (int k = 0; k < 4; k++) same = same && d.cg_key[k] == key[k];
+        if (!same) {
+            cudaError_t ge = d.cg_cap ? cudaSuccess : cudaStreamCreateWithFlags(&d.cg_cap, cudaStreamNonBlocking);
+            cudaGraph_t g = nullptr;
+            if (ge == cudaSuccess) ge = cudaStreamBeginCapture(d.cg_cap, cudaStreamCaptureModeThreadLocal);
+            if (ge == cudaSuccess) {
+                cudaError_t ce = cudaSuccess;
+                for (int k = 0; k < G && ce == cudaSuccess; k++) ce = iteration(k, d.cg_cap);
+                ge = cudaStreamEndCapture(d.cg_cap, &g);
+                if (ce != cudaSuccess) ge = ce;
+            }
+            if (ge == cudaSuccess && d.cg_exec) {
+                cudaGraphExecUpdateResultInfo info;
+                if (cudaGraphExecUpdate(d.cg_exec, g, &info) != cudaSuccess) {
+                    cudaGetLastError();
+                    cudaGraphExecDestroy(d.cg_exec);
+                    d.cg_exec = nullptr;
+                }
+            }
+            if (ge == cudaSuccess && !d.cg_exec) ge = cudaGraphInstantiate(&d.cg_exec, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (ge == cudaSuccess) {
+                for (int k = 0; k < 4; k++) d.cg_key[k] = key[k];
+            } else {
+                cudaGetLastError();
+                if (d.cg_exec) cudaGraphExecDestroy(d.cg_exec);
+                d.cg_exec = nullptr;
+                graph = false;          // fall back to launching the kernels one by one
+            }
+        }
+    }
     int it = 0;
     while (it < o->max_iter) {
-        const int par = it & 1;
-        double *old_pair = S + 4 + 2 * par, *new_pair = S + 4 + 2 * (par ^ 1);
-        // Each kernel of the iteration is a dependent launch: it is scheduled while the
-        // one before it finishes and waits for it before reading anything.
-        // q = K p (constrained rows zero), p.q -> S[2]
-        e = launch_spmv(*m, d_vals, pv, q, d_fixed, pv, partial, counter, S + 2, st, true);
-        if (e != cudaSuccess) break;
-        // u, r, z; (r.z, r.r) -> the other pair
-        e = launch_dependent(k_cg_step, cgrid, kCgThreads, st, h.ndof, d_fixed, diag, pv, q, d_u, r, z, old_pair,
-                             S + 2, partial, counter, new_pair);
-        if (e != cudaSuccess) break;
-        e = launch_dependent(k_cg_direction, cg_grid_wide(h.ndof), kCgThreads, st, h.ndof, d_fixed, z, pv,
-                             new_pair, old_pair);
-        if (e != cudaSuccess) break;
-        it++;
+        if (graph && it + G <= o->max_iter) {
+            e = cudaGraphLaunch(d.cg_exec, st);
+            if (e != cudaSuccess) break;
+            it += G;
+        } else {
+            e = iteration(it, st);
+            if (e != cudaSuccess) break;
+            it++;
+        }
         if (it % o->check_every == 0 || it == o->max_iter) {
-            e = cudaMemcpyAsync(&rr, new_pair + 1, sizeof(double), cudaMemcpyDeviceToHost, st);
+            double *latest = S + 4 + 2 * (it & 1);
+            e = cudaMemcpyAsync(&rr, latest + 1, sizeof(double), cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) break;
             if (std::sqrt(rr) <= o->rtol * r0) {

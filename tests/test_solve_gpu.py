@@ -40,13 +40,16 @@ def cantilever(nx, ny, nz, jitter=0.0):
     return coords, cells
 
 
+@pytest.mark.parametrize("check_every", [5, 10], ids=["launches", "graph"])
 @pytest.mark.parametrize("cell,k,mk", [
     ("hex", 1, lambda: cantilever(12, 4, 4)),
     ("hex", 1, lambda: cantilever(10, 4, 3, jitter=0.15)),
     ("tet", 2, lambda: W.kuhn_tets(6, 2, 2, 0.15, np.random.default_rng(4))),
     ("quad", 2, lambda: W.quad_grid(12, 5, 0.2, np.random.default_rng(5))),
 ])
-def test_cg_matches_direct_solve(lib, cell, k, mk):
+def test_cg_matches_direct_solve(lib, cell, k, mk, check_every):
+    """Both loops: kernel by kernel (odd check interval) and replayed as a graph
+    between checks (even interval)."""
     coords, cells = mk()
     m = lib.Mesh(cell, k, coords, cells, *MAT)
     d = m.dim
@@ -58,7 +61,7 @@ def test_cg_matches_direct_solve(lib, cell, k, mk):
     f = np.zeros(m.ndof)
     tip = np.where(xn[:, 0] > L - 1e-9)[0]
     f[d * tip + (d - 1)] = -1.0 / len(tip)
-    u, info = m.solve(vals, dev(fixed), dev(f), rtol=1e-12, max_iter=20000, check_every=5)
+    u, info = m.solve(vals, dev(fixed), dev(f), rtol=1e-12, max_iter=20000, check_every=check_every)
     assert info["converged"] and info["rel_residual"] <= 1e-12
     rp, ci, v, ndof = oracle.assemble(cell, k, coords, cells, MAT, rho)
     ref = oracle.solve_dirichlet(rp, ci, v, fixed, f, np.zeros(ndof))
@@ -66,8 +69,33 @@ def test_cg_matches_direct_solve(lib, cell, k, mk):
     assert np.linalg.norm(un - ref) <= 1e-8 * np.linalg.norm(ref)
     assert np.all(un[fixed] == 0.0)
     # same bits on a second solve
-    u2, info2 = m.solve(vals, dev(fixed), dev(f), rtol=1e-12, max_iter=20000, check_every=5)
+    u2, info2 = m.solve(vals, dev(fixed), dev(f), rtol=1e-12, max_iter=20000, check_every=check_every)
     assert torch.equal(u, u2) and info2["iterations"] == info["iterations"]
+
+
+def test_cg_graph_replay_is_bitwise_the_launch_loop(lib):
+    """A fixed number of iterations (the tolerance is never met) gives the same
+    bits whether the iterations are replayed as a graph (check interval 10, also
+    with a remainder of 7 launched one by one) or launched one by one (interval 3),
+    and a new right-hand side reuses the kept graph with the new vectors."""
+    coords, cells = cantilever(9, 3, 3)
+    m = lib.Mesh("hex", 1, coords, cells, *MAT)
+    rho = np.random.default_rng(7).uniform(0.3, 1.0, len(cells))
+    vals = m.assemble_K(dev(rho))
+    xn = oracle.node_coords("hex", 1, coords, cells)
+    fixed = np.repeat(xn[:, 0] < 1e-9, 3)
+    f = np.zeros(m.ndof)
+    tip = np.where(xn[:, 0] > xn[:, 0].max() - 1e-9)[0]
+    f[3 * tip + 2] = -1.0 / len(tip)
+    for n in (40, 47):
+        ug, ig = m.solve(vals, dev(fixed), dev(f), rtol=1e-300, max_iter=n, check_every=10)
+        ul, il = m.solve(vals, dev(fixed), dev(f), rtol=1e-300, max_iter=n, check_every=3)
+        assert ig["iterations"] == il["iterations"] == n
+        assert torch.equal(ug, ul)
+    f2 = 2.0 * f
+    ug2, _ = m.solve(vals, dev(fixed), dev(f2), rtol=1e-300, max_iter=40, check_every=10)
+    ul2, _ = m.solve(vals, dev(fixed), dev(f2), rtol=1e-300, max_iter=40, check_every=3)
+    assert torch.equal(ug2, ul2)
 
 
 def test_cg_patch_test_prescribed_affine_field(lib):
