@@ -425,17 +425,24 @@ __global__ void __launch_bounds__(kGW * 32, 2) k_gather_rows(const GatherArgs<KT
                 bad |= isnan(cur.E.y);
                 const df E = df{cur.E.x, cur.E.y};
                 float2 *arow = acc + i * rowlen;
+                // a lane's R slots are distinct (distinct columns of one cell), so all
+                // of them are read before any is written back: one shared-memory round
+                // trip per cell instead of R dependent ones
+                if (A.vals) {
+                    float2 v[R];
 #pragma unroll
-                for (int r = 0; r < R; r++) {
-                    if (A.vals) {
-                        float2 v = arow[s[r]];
-                        acc_add(v.x, v.y, KE::mul(E, cur.k[r]));
-                        arow[s[r]] = v;
-                    }
-                    if (SENS) {
-                        const float2 ub = un[s[r]];
-                        acc_add(S, C, KE::mul(df{ub.x, ub.y}, cur.k[r]));
-                    }
+                    for (int r = 0; r < R; r++) v[r] = arow[s[r]];
+#pragma unroll
+                    for (int r = 0; r < R; r++) acc_add(v[r].x, v[r].y, KE::mul(E, cur.k[r]));
+#pragma unroll
+                    for (int r = 0; r < R; r++) arow[s[r]] = v[r];
+                }
+                if (SENS) {
+                    float2 ub[R];
+#pragma unroll
+                    for (int r = 0; r < R; r++) ub[r] = un[s[r]];
+#pragma unroll
+                    for (int r = 0; r < R; r++) acc_add(S, C, KE::mul(df{ub[r].x, ub[r].y}, cur.k[r]));
                 }
             }
             __syncwarp();
