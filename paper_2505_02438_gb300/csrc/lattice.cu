@@ -14,9 +14,9 @@
 // separable per axis (low L, high H, H+L, H-L), so all 4^d of them come from
 // the 2^d moduli around n in d stages of one float-float add per lane.
 //
-// Each warp owns one node (3D) or three nodes (2D), one lane per neighbour
-// offset delta, and writes the node's d rows (d * d * deg(n) contiguous CSR
-// values) with coalesced stores.  The element moduli arrive from k_simp_df
+// In 3D each warp takes two consecutive nodes at a time, one lane per
+// neighbour offset delta, and hands their 2 d rows (contiguous CSR values) to
+// the copy engine; in 2D a warp owns three nodes and stores them coalesced.  The element moduli arrive from k_simp_df
 // as float pairs; a node touching a modulus outside [2^-60, 2^60] (flagged by
 // a NaN low word) is done in plain FP64 instead: in 2D by its warp at once, in
 // 3D by k_simp_df before the assembly (whose warps then skip the node), which
@@ -51,8 +51,8 @@ __device__ __forceinline__ void bulk_store(double *gdst, const double *ssrc, uin
                  : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-// wait until at most one committed group is still reading its shared source
-__device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+// wait until no committed group is still reading its shared source
+__device__ __forceinline__ void bulk_wait_read_0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 // wait until every committed group has completed
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 // order this thread's generic-proxy shared-memory writes before later async-proxy reads
@@ -175,12 +175,16 @@ struct NodeIter {
     }
 };
 
-__device__ __forceinline__ float2 load_corner(const float2 *__restrict__ Edf, const int idx[3], int lane, int nx,
-                                              int ny, int nz)
+// Corner moduli of two nodes: lanes 0..7 those of node a, lanes 8..15 those of node b.
+__device__ __forceinline__ float2 load_corner_pair(const float2 *__restrict__ Edf, const int ia[3], const int ib[3],
+                                                   bool has_b, int lane, int nx, int ny, int nz)
 {
     float2 v = make_float2(0.f, 0.f);
-    if (lane < 8) {
-        const int ex = idx[0] - 1 + (lane & 1), ey = idx[1] - 1 + ((lane >> 1) & 1), ez = idx[2] - 1 + (lane >> 2);
+    const bool second = lane >= 8;
+    if (lane < 8 || (lane < 16 && has_b)) {
+        const int l = lane & 7;
+        const int *idx = second ? ib : ia;
+        const int ex = idx[0] - 1 + (l & 1), ey = idx[1] - 1 + ((l >> 1) & 1), ez = idx[2] - 1 + (l >> 2);
         if (ex >= 0 && ex < nx && ey >= 0 && ey < ny && ez >= 0 && ez < nz)
             v = __ldg(&Edf[((int64_t)ez * ny + ey) * nx + ex]);
     }
@@ -190,154 +194,6 @@ __device__ __forceinline__ float2 load_corner(const float2 *__restrict__ Edf, co
 #ifndef SOPTX_LATTICE_MINBLOCKS
 #define SOPTX_LATTICE_MINBLOCKS 4
 #endif
-template <int WPB>
-__global__ void __launch_bounds__(WPB * 32, SOPTX_LATTICE_MINBLOCKS)
-k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restrict__ node_off,
-                    const float2 *__restrict__ Edf, const float2 *__restrict__ kappa_g,
-                    const double *__restrict__ K0, const double *__restrict__ rho, SimpParams sp,
-                    double *__restrict__ vals, const unsigned *__restrict__ flag, unsigned gen,
-                    uint32_t pbias, double kscale)
-{
-    const int lane = threadIdx.x & 31;
-    const int dl = lane < 27 ? lane : 26;
-    const int dx = dl % 3 - 1, dy = (dl / 3) % 3 - 1, dz = dl / 9 - 1;
-    // table entries t = ox + 4 oy + 16 oz of the four sign classes of (i, j)
-    int tq[4];
-    tq[0] = axis_opt(dx, false) + 4 * axis_opt(dy, false) + 16 * axis_opt(dz, false);   // i == j
-    tq[1] = axis_opt(dx, true) + 4 * axis_opt(dy, true) + 16 * axis_opt(dz, false);     // {0, 1}
-    tq[2] = axis_opt(dx, true) + 4 * axis_opt(dy, false) + 16 * axis_opt(dz, true);     // {0, 2}
-    tq[3] = axis_opt(dx, false) + 4 * axis_opt(dy, true) + 16 * axis_opt(dz, true);     // {1, 2}
-    __shared__ float2 kap_s[27 * 9];
-    __shared__ double kapd_s[27 * 9];
-    // two staging buffers per warp (a node's d rows), 16-byte aligned, one
-    // spare slot so that a value sits at the same 16-byte phase as its
-    // destination; the copy engine writes a buffer out while the warp fills
-    // the other one
-    __shared__ __align__(16) double stage_s[WPB][2][27 * 9 + 1];
-    // the 64 signed sums of the node being done (stage Z's output), per warp
-    __shared__ float2 tab_s[WPB][64];
-    int buf = 0;
-    for (int t = threadIdx.x; t < 27 * 9; t += blockDim.x) {
-        kap_s[t] = kappa_g[t];
-        kapd_s[t] = ((double)kappa_g[t].x + (double)kappa_g[t].y) * kscale;
-    }
-    __syncthreads();
-    // the moduli (and the flag) come from k_simp_df, launched just before; once every
-    // block is past this wait, k_simp_df has completed and the sensitivity of a
-    // one-call step, which reads only its outputs, may start on SMs this kernel frees
-    grid_dep_wait();
-    grid_dep_launch();
-    // stage constants
-    const int ox = lane & 3, oy = (lane >> 2) & 3;
-    const int yzx = (lane >> 2) & 3;            // stage X: (cy, cz) of lanes 0..15
-    const int czy = (lane >> 4) & 1;            // stage Y: cz of lane
-    const int oz0 = (lane < 16) ? 0 : 1, oz1 = oz0 + 2;
-    const float cx_ = opt_coef(ox), cy_ = opt_coef(oy), cz0_ = opt_coef(oz0), cz1_ = opt_coef(oz1);
-    const int N[3] = {nx, ny, nz};
-
-    // k_simp_df of this call stored `gen` in *flag if some modulus is out of
-    // range (and wrote the rows of the nodes around those cells in FP64)
-    const bool anybad = __ldcg(flag) == gen;
-
-    const int64_t nchunks = (nn + kChunk - 1) / kChunk;
-    const int64_t warps = (int64_t)gridDim.x * WPB;
-    for (int64_t ch = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5); ch < nchunks; ch += warps) {
-        const int64_t n_begin = ch * kChunk;
-        const int64_t n_end = min(n_begin + (int64_t)kChunk, nn);
-        NodeIter it;
-        it.decode((uint32_t)n_begin, nx, ny);
-        float2 cur = load_corner(Edf, it.idx, lane, nx, ny, nz);
-        int64_t off = node_off[n_begin];
-        for (int64_t n = n_begin; n < n_end; n++) {
-            const int idx[3] = {it.idx[0], it.idx[1], it.idx[2]};
-            // prefetch the next node's corner modulus and CSR offset
-            it.step(nx, ny);
-            float2 nxt = make_float2(0.f, 0.f);
-            int64_t off_next = 0;
-            if (n + 1 < n_end) {
-                nxt = load_corner(Edf, it.idx, lane, nx, ny, nz);
-                off_next = node_off[n + 1];
-            }
-            const df Ec = df{cur.x, cur.y};
-            // a corner modulus outside the float-pair range: k_simp_df has
-            // written this node's rows in FP64, so nothing is stored here
-            unsigned badnode = 0u;
-            if (anybad) badnode = __ballot_sync(kFull, lane < 8 && isnan(cur.y));
-            bool valid;
-            int mi, rowlen;
-            node_layout3(idx, N, dx, dy, dz, lane, valid, mi, rowlen);
-            double *base = vals + 9 * off;
-            {
-                // stage X: lanes 0..15 -> (ox, cy, cz)
-                const df xL = shfl_df(Ec, 2 * yzx), xH = shfl_df(Ec, 2 * yzx + 1);
-                const df X = combine_lazy(ox == 0, cx_, xL, xH);
-                // stage Y: lanes 0..31 -> (ox, oy, cz)
-                const df yL = shfl_df(X, ox + 4 * (2 * czy)), yH = shfl_df(X, ox + 4 * (1 + 2 * czy));
-                const df Y = combine_lazy(oy == 0, cy_, yL, yH);
-                // stage Z: lane holds entries lane (A) and lane + 32 (B)
-                const df zL = shfl_df(Y, lane & 15), zH = shfl_df(Y, (lane & 15) + 16);
-                const df A = combine(oz0 == 0, cz0_, zL, zH), B = combine(false, cz1_, zL, zH);
-                float2 *tab = tab_s[threadIdx.x >> 5];
-                tab[lane] = make_float2(A.h, A.l);
-                tab[lane + 32] = make_float2(B.h, B.l);
-                __syncwarp();
-                df T[4];
-#pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const float2 t = tab[tq[q]];
-                    T[q] = df{t.x, t.y};
-                }
-                // the buffer about to be filled was handed to the copy engine two
-                // nodes ago: wait until that copy has read it
-                if (lane == 0) bulk_wait_read_1();
-                __syncwarp();
-                // value t of the node's block goes to slot ph + t, ph the 16-byte phase of base
-                const int ph = (int)((reinterpret_cast<uintptr_t>(base) >> 3) & 1);
-                double *stage = stage_s[threadIdx.x >> 5][buf];
-                if (valid) {
-                    // Two routes to an FP64 value, balancing the FP32/integer
-                    // pipes against the otherwise idle FP64 pipe: classes below
-                    // kFp64Classes convert T once and take one DMUL per entry;
-                    // the others multiply in float pairs and convert each entry.
-                    double Td[kFp64Classes];
-#pragma unroll
-                    for (int q = 0; q < kFp64Classes; q++) Td[q] = df_to_double_biased(T[q].h, T[q].l, 0x38000000u);
-#pragma unroll
-                    for (int i = 0; i < 3; i++) {
-                        double *row = stage + ph + i * rowlen + 3 * mi;
-#pragma unroll
-                        for (int j = 0; j < 3; j++) {
-                            const int q = (i == j) ? 0 : (i + j == 1 ? 1 : (i + j == 2 ? 2 : 3));
-                            if (q < kFp64Classes) {
-                                row[j] = kapd_s[dl * 9 + i * 3 + j] * Td[q < kFp64Classes ? q : 0];
-                            } else {
-                                const float2 kv = kap_s[dl * 9 + i * 3 + j];
-                                const df v = df_mul_raw(df{kv.x, kv.y}, T[q]);
-                                row[j] = df_to_double_biased(v.h, v.l, pbias);
-                            }
-                        }
-                    }
-                }
-                fence_proxy_async_smem();
-                __syncwarp();
-                // a value at an odd 8-byte phase at either end goes out by a plain store
-                const int blk = 3 * rowlen;
-                const int head = ph, mid = (blk - head) & ~1, tail = blk - head - mid;
-                if (lane == 0 && mid > 0 && !badnode) {
-                    bulk_store(base + head, stage + ph + head, (uint32_t)(8 * mid));
-                    bulk_commit();
-                }
-                if (lane == 1 && head && !badnode) __stcs(base, stage[ph]);
-                if (lane == 2 && tail && !badnode) __stcs(base + blk - 1, stage[ph + blk - 1]);
-                buf ^= 1;
-            }
-            cur = nxt;
-            off = off_next;
-        }
-    }
-    if (lane == 0) bulk_wait_all();
-}
-
 // Element moduli as float pairs (and, with u given, u as float pairs).  With
 // `flag` given (3D lattice), a warp
 // whose cells include moduli outside the float-pair range (NaN low word)
@@ -403,6 +259,167 @@ k_simp_df(int nx, int ny, int nz, int64_t nc, const double *__restrict__ rho, Si
             }
         }
     }
+}
+
+// 3D assembly, two nodes at a time (n, n+1 of a chunk): one corner load, one X
+// stage and one hand-off to the copy engine serve both (their rows are
+// contiguous in the CSR values); the Y and Z stages and the entries run once
+// per node.  Each lane forms its 9 entries: the classes below kFp64Classes
+// convert T once and take one FP64 multiply per entry on the otherwise idle
+// FP64 pipe, the others multiply in float pairs and convert each entry.  One
+// staging buffer per warp holds both nodes' rows, each value at the 16-byte
+// phase of its destination; before it is refilled the warp waits until the
+// copy engine has read the previous pair (one node at a time with two
+// buffers was 12% more instructions: 409 against 358 per node).
+template <int WPB>
+__global__ void __launch_bounds__(WPB * 32, SOPTX_LATTICE_MINBLOCKS)
+k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restrict__ node_off,
+                          const float2 *__restrict__ Edf, const float2 *__restrict__ kappa_g,
+                          const double *__restrict__ K0, const double *__restrict__ rho, SimpParams sp,
+                          double *__restrict__ vals, const unsigned *__restrict__ flag, unsigned gen,
+                          uint32_t pbias, double kscale)
+{
+    const int lane = threadIdx.x & 31;
+    const int dl = lane < 27 ? lane : 26;
+    const int dx = dl % 3 - 1, dy = (dl / 3) % 3 - 1, dz = dl / 9 - 1;
+    int tq[4];
+    tq[0] = axis_opt(dx, false) + 4 * axis_opt(dy, false) + 16 * axis_opt(dz, false);   // i == j
+    tq[1] = axis_opt(dx, true) + 4 * axis_opt(dy, true) + 16 * axis_opt(dz, false);     // {0, 1}
+    tq[2] = axis_opt(dx, true) + 4 * axis_opt(dy, false) + 16 * axis_opt(dz, true);     // {0, 2}
+    tq[3] = axis_opt(dx, false) + 4 * axis_opt(dy, true) + 16 * axis_opt(dz, true);     // {1, 2}
+    __shared__ float2 kap_s[27 * 9];
+    __shared__ double kapd_s[27 * 9];
+    __shared__ __align__(16) double stage_s[WPB][2 * 27 * 9 + 2];
+    __shared__ float2 tab_s[WPB][2][64];
+    for (int t = threadIdx.x; t < 27 * 9; t += blockDim.x) {
+        kap_s[t] = kappa_g[t];
+        kapd_s[t] = ((double)kappa_g[t].x + (double)kappa_g[t].y) * kscale;
+    }
+    __syncthreads();
+    grid_dep_wait();
+    grid_dep_launch();
+    const int ox = lane & 3, oy = (lane >> 2) & 3;
+    const int yzx = (lane >> 2) & 3;            // stage X: (cy, cz) of lanes 0..15 (and 16..31)
+    const int xsrc = lane & 16 ? 8 : 0;         // stage X: lanes 16..31 take the second node's corners
+    const int czy = (lane >> 4) & 1;            // stage Y: cz of lane
+    const int oz0 = (lane < 16) ? 0 : 1, oz1 = oz0 + 2;
+    const float cx_ = opt_coef(ox), cy_ = opt_coef(oy), cz0_ = opt_coef(oz0), cz1_ = opt_coef(oz1);
+    const int N[3] = {nx, ny, nz};
+    const bool anybad = __ldcg(flag) == gen;
+    double *stage = stage_s[threadIdx.x >> 5];
+    float2(*tab)[64] = tab_s[threadIdx.x >> 5];
+
+    const int64_t nchunks = (nn + kChunk - 1) / kChunk;
+    const int64_t warps = (int64_t)gridDim.x * WPB;
+    for (int64_t ch = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5); ch < nchunks; ch += warps) {
+        const int64_t n_begin = ch * kChunk;
+        const int64_t n_end = min(n_begin + (int64_t)kChunk, nn);
+        NodeIter ia;
+        ia.decode((uint32_t)n_begin, nx, ny);
+        NodeIter ib = ia;
+        ib.step(nx, ny);
+        float2 cur = load_corner_pair(Edf, ia.idx, ib.idx, n_begin + 1 < n_end, lane, nx, ny, nz);
+        int64_t off = node_off[n_begin];
+        for (int64_t n = n_begin; n < n_end; n += 2) {
+            const bool has_b = n + 1 < n_end;
+            const int idxa[3] = {ia.idx[0], ia.idx[1], ia.idx[2]};
+            const int idxb[3] = {ib.idx[0], ib.idx[1], ib.idx[2]};
+            // prefetch the next pair's corner moduli and CSR offset
+            ia = ib;
+            ia.step(nx, ny);
+            ib = ia;
+            ib.step(nx, ny);
+            float2 nxt = make_float2(0.f, 0.f);
+            int64_t off_next = 0;
+            if (n + 2 < n_end) {
+                nxt = load_corner_pair(Edf, ia.idx, ib.idx, n + 3 < n_end, lane, nx, ny, nz);
+                off_next = node_off[n + 2];
+            }
+            const df Ec = df{cur.x, cur.y};
+            unsigned bad_a = 0u, bad_b = 0u;
+            if (anybad) {
+                bad_a = __ballot_sync(kFull, lane < 8 && isnan(cur.y));
+                bad_b = __ballot_sync(kFull, lane >= 8 && lane < 16 && isnan(cur.y));
+            }
+            bool valid_a, valid_b;
+            int mi_a, mi_b, rl_a, rl_b;
+            node_layout3(idxa, N, dx, dy, dz, lane, valid_a, mi_a, rl_a);
+            node_layout3(idxb, N, dx, dy, dz, lane, valid_b, mi_b, rl_b);
+            valid_b = valid_b && has_b;
+            double *base = vals + 9 * off;
+            // stage X for both nodes: lanes 0..15 node a, 16..31 node b -> (ox, cy, cz)
+            const df xL = shfl_df(Ec, xsrc + 2 * yzx), xH = shfl_df(Ec, xsrc + 2 * yzx + 1);
+            const df X = combine_lazy(ox == 0, cx_, xL, xH);
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                // stage Y: lanes 0..31 -> (ox, oy, cz) of node k
+                const df yL = shfl_df(X, 16 * k + ox + 4 * (2 * czy)), yH = shfl_df(X, 16 * k + ox + 4 * (1 + 2 * czy));
+                const df Y = combine_lazy(oy == 0, cy_, yL, yH);
+                // stage Z: lane holds entries lane (A) and lane + 32 (B) of node k
+                const df zL = shfl_df(Y, lane & 15), zH = shfl_df(Y, (lane & 15) + 16);
+                const df A = combine(oz0 == 0, cz0_, zL, zH), B = combine(false, cz1_, zL, zH);
+                tab[k][lane] = make_float2(A.h, A.l);
+                tab[k][lane + 32] = make_float2(B.h, B.l);
+            }
+            // the buffer is free once the copy engine has read the previous pair
+            if (lane == 0) bulk_wait_read_0();
+            __syncwarp();
+            const int ph = (int)((reinterpret_cast<uintptr_t>(base) >> 3) & 1);
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const bool valid = k ? valid_b : valid_a;
+                const int mi = k ? mi_b : mi_a, rowlen = k ? rl_b : rl_a;
+                double *st = stage + ph + (k ? 3 * rl_a : 0);
+                if (valid) {
+                    df T[4];
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const float2 t = tab[k][tq[q]];
+                        T[q] = df{t.x, t.y};
+                    }
+                    double Td[kFp64Classes];
+#pragma unroll
+                    for (int q = 0; q < kFp64Classes; q++) Td[q] = df_to_double_biased(T[q].h, T[q].l, 0x38000000u);
+#pragma unroll
+                    for (int i = 0; i < 3; i++) {
+                        double *row = st + i * rowlen + 3 * mi;
+#pragma unroll
+                        for (int j = 0; j < 3; j++) {
+                            const int q = (i == j) ? 0 : (i + j == 1 ? 1 : (i + j == 2 ? 2 : 3));
+                            if (q < kFp64Classes) {
+                                row[j] = kapd_s[dl * 9 + i * 3 + j] * Td[q < kFp64Classes ? q : 0];
+                            } else {
+                                const float2 kv = kap_s[dl * 9 + i * 3 + j];
+                                const df v = df_mul_raw(df{kv.x, kv.y}, T[q]);
+                                row[j] = df_to_double_biased(v.h, v.l, pbias);
+                            }
+                        }
+                    }
+                }
+            }
+            fence_proxy_async_smem();
+            __syncwarp();
+            const int blk_a = 3 * rl_a, blk = blk_a + (has_b ? 3 * rl_b : 0);
+            if (!bad_a && !bad_b) {
+                // a value at an odd 8-byte phase at either end goes out by a plain store
+                const int head = ph, mid = (blk - head) & ~1, tail = blk - head - mid;
+                if (lane == 0 && mid > 0) {
+                    bulk_store(base + head, stage + ph + head, (uint32_t)(8 * mid));
+                    bulk_commit();
+                }
+                if (lane == 1 && head) __stcs(base, stage[ph]);
+                if (lane == 2 && tail) __stcs(base + blk - 1, stage[ph + blk - 1]);
+            } else {
+                // a node next to an out-of-range modulus was written by k_simp_df: only
+                // the other node's rows go out, by plain stores
+                const int t0 = bad_a ? blk_a : 0, t1 = (bad_b || !has_b) ? blk_a : blk;
+                for (int t = t0 + lane; t < t1; t += 32) __stcs(base + t, stage[ph + t]);
+            }
+            cur = nxt;
+            off = off_next;
+        }
+    }
+    if (lane == 0) bulk_wait_all();
 }
 
 // 2D: three nodes per warp, lanes 9g .. 9g+8 serve node g, one lane per offset.
