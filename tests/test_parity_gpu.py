@@ -181,6 +181,16 @@ def test_extreme_box_aspect_takes_general_path(P):
     assert m.path == "uniform"
 
 
+@pytest.mark.parametrize("n", [(2, 2, 2), (4, 2, 2), (4, 4, 2), (16, 3, 2)])
+def test_lattice_node_pairs_with_odd_tails(P, n):
+    """The 3D lattice assembly takes two nodes per pass within chunks of 16:
+    node counts 27, 45 and 75 leave a lone node at the end, and with an odd
+    number of nodes per row (3, 5, 17) some pairs straddle two rows."""
+    c, cl = W.structured_hex(*n)
+    m, *_ = check_assembly(P, "hex", 1, c, cl, "fp64", seed=11)
+    assert m.path == "lattice"
+
+
 def test_lattice_anisotropic_boxes(P):
     """Box cells with different edge lengths per axis and a shifted origin."""
     c, cl = W.structured_hex(6, 4, 3)
