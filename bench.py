@@ -50,6 +50,8 @@ def workload(name):
         return W.jittered_tri(400, 200)
     if name == "q4":
         return W.mbb_q4(60, 20)
+    if name == "q4max":
+        return W.mbb_q4(800, 400)
     if name == "hexj":
         return W.jittered_hex(120, 40, 40)
     raise ValueError(name)
@@ -451,6 +453,7 @@ WORKLOAD_DESC = {
     "tet": "Kuhn P2 tetrahedra 60x20x20x6 (144,000 cells), jittered, FP64 K(rho) CSR + dc + c",
     "tri": "P3 triangles 400x200x2 (160,000 cells), jittered, FP64 K(rho) CSR + dc + c",
     "q4": "Q4 plane stress 60x20 (1,200 cells), FP64 K(rho) CSR + dc + c",
+    "q4max": "Q4 plane stress 800x400 (320,000 cells, the largest serving mesh), FP64 K(rho) CSR + dc + c",
     "hexj": "3D cantilever box 120x40x40 trilinear hex Q1, interior vertices jittered (192,000 general hexahedra), "
             "FP64 K(rho) CSR + dc + c",
 }

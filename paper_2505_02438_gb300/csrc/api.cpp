@@ -217,11 +217,11 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
             s = cuda_status(cudaMemcpy(Kp.data(), d.K, n2 * sizeof(float2), cudaMemcpyDeviceToHost), "K0");
             for (size_t q = 0; q < n2; q++) K0[q] = (double)Kp[q].x + (double)Kp[q].y;
         }
-        if (s == SOPTX_OK && h.dim == 3 && !lattice_kappa_shift(h.dim, K0, h.lat_kshift)) m->path = SOPTX_PATH_UNIFORM;
+        if (s == SOPTX_OK && !lattice_kappa_shift(h.dim, K0, h.lat_kshift)) m->path = SOPTX_PATH_UNIFORM;
     }
     if (s == SOPTX_OK && m->path == SOPTX_PATH_LATTICE) {
         std::vector<float2> kappa;
-        build_lattice_kappa(h.dim, K0, h.dim == 3 ? h.lat_kshift : 0, kappa);
+        build_lattice_kappa(h.dim, K0, h.lat_kshift, kappa);
         if (s == SOPTX_OK) s = upload(&d.K0, K0, st, B, "K0");
         if (s == SOPTX_OK) s = upload(&d.kappa, kappa, st, B, "kappa");
         std::vector<float2> sectors;
@@ -236,7 +236,7 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
             if (e != cudaSuccess) { cudaGetLastError(); s = cuda_status(e, "element moduli"); }
             else B += std::max<int64_t>(h.nc, 1) * (int64_t)sizeof(float2);
         }
-        if (s == SOPTX_OK && h.dim == 3) {
+        if (s == SOPTX_OK) {
             const size_t bytes = 16;
             cudaError_t e = dev_alloc((void **)&d.lat_bad, bytes);
             if (e == cudaSuccess) e = cudaMemsetAsync(d.lat_bad, 0, bytes, st);

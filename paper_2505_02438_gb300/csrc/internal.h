@@ -76,7 +76,7 @@ struct HostMesh {
     bool lattice = false;               // order-1 box lattice in canonical numbering
     int lat_n[3] = {1, 1, 1};           // cells per axis
     std::vector<float2> sectors;        // [2^d][d][d] Walsh-sector blocks of K^0 (empty: no split)
-    int lat_kshift = 0;                 // 3D: the kappa pairs hold kappa 2^-lat_kshift
+    int lat_kshift = 0;                 // the kappa pairs hold kappa 2^-lat_kshift
     int max_deg = 0;
 };
 
@@ -111,7 +111,7 @@ struct DeviceMesh {
     float2 *kappa = nullptr;       // [3^d][d][d] reference blocks as float pairs
     double *K0 = nullptr;          // [ldof][ldof] unit-modulus matrix in FP64
     float2 *sectors = nullptr;     // [2^d][d][d] Walsh-sector blocks of K^0 (nullptr: no split)
-    unsigned *lat_bad = nullptr;   // 3D: generation of the last call that met out-of-range moduli
+    unsigned *lat_bad = nullptr;   // generation of the last call that met out-of-range moduli
     // general path
     float2 *udf = nullptr;         // [ndof] u as float pairs (general path; lattice: one-call step)
     double *part = nullptr;        // [nc][nb] per-(cell, node) partials of u_e^T K_e^0 u_e

@@ -154,6 +154,17 @@ __device__ __forceinline__ void node_layout3(const int idx[3], const int N[3], i
     rowlen = 3 * cnt[0] * cnt[1] * cnt[2];
 }
 
+// The same for a 2D node (lanes 0..8 are the offsets delta).
+__device__ __forceinline__ void node_layout2(const int idx[2], int nx, int ny, int dx, int dy, bool lane_ok,
+                                             bool &valid, int &mi, int &rowlen)
+{
+    const int lo0 = idx[0] > 0 ? -1 : 0, lo1 = idx[1] > 0 ? -1 : 0;
+    const int c0 = (idx[0] < nx ? 1 : 0) - lo0 + 1, c1 = (idx[1] < ny ? 1 : 0) - lo1 + 1;
+    valid = lane_ok && dx >= lo0 && dx < lo0 + c0 && dy >= lo1 && dy < lo1 + c1;
+    mi = (dx - lo0) + c0 * (dy - lo1);
+    rowlen = 2 * c0 * c1;
+}
+
 struct NodeIter {
     int idx[3];
     __device__ void decode(uint32_t n, int nx, int ny)
@@ -195,7 +206,7 @@ __device__ __forceinline__ float2 load_corner_pair(const float2 *__restrict__ Ed
 #define SOPTX_LATTICE_MINBLOCKS 4
 #endif
 // Element moduli as float pairs (and, with u given, u as float pairs).  With
-// `flag` given (3D lattice), a warp
+// `flag` given, a warp
 // whose cells include moduli outside the float-pair range (NaN low word)
 // stores `gen` in *flag and writes the rows of the nodes around each such
 // cell in plain FP64, lanes over the offsets; the assembly kernel then skips
@@ -205,7 +216,7 @@ __device__ __forceinline__ float2 load_corner_pair(const float2 *__restrict__ Ed
 #define SOPTX_SIMP_MINB 8
 #endif
 __global__ void __launch_bounds__(256, SOPTX_SIMP_MINB)
-k_simp_df(int nx, int ny, int nz, int64_t nc, const double *__restrict__ rho, SimpParams sp,
+k_simp_df(int dim, int nx, int ny, int nz, int64_t nc, const double *__restrict__ rho, SimpParams sp,
                           float2 *__restrict__ Edf, const int64_t *__restrict__ node_off,
                           const double *__restrict__ K0, double *__restrict__ vals, unsigned *__restrict__ flag,
                           unsigned gen, int64_t ndof, const double *__restrict__ u, float2 *__restrict__ udf)
@@ -240,6 +251,25 @@ k_simp_df(int nx, int ny, int nz, int64_t nc, const double *__restrict__ rho, Si
         unsigned m = __ballot_sync(kFull, isbad);
         if (!m) continue;
         if (lane == 0) *flag = gen;
+        if (dim == 2) {
+            const int dl = lane < 9 ? lane : 8;
+            const int dx = dl % 3 - 1, dy = dl / 3 - 1;
+            while (m) {
+                const unsigned k = __ffs(m) - 1;
+                m &= m - 1u;
+                const uint32_t ce = (uint32_t)(e0 + k);
+                for (int corner = 0; corner < 4; corner++) {
+                    const int idx[2] = {(int)(ce % (uint32_t)nx) + (corner & 1), (int)(ce / (uint32_t)nx) + (corner >> 1)};
+                    const int64_t n = idx[0] + (int64_t)(nx + 1) * idx[1];
+                    bool valid;
+                    int mi, rowlen;
+                    node_layout2(idx, nx, ny, dx, dy, lane < 9, valid, mi, rowlen);
+                    lattice_node_fp64<2>(nx, ny, 1, idx[0], idx[1], 0, dl, valid, mi, rowlen, vals + 4 * node_off[n],
+                                         K0, rho, sp);
+                }
+            }
+            continue;
+        }
         const int dl = lane < 27 ? lane : 26;
         const int dx = dl % 3 - 1, dy = (dl / 3) % 3 - 1, dz = dl / 9 - 1;
         const int N[3] = {nx, ny, nz};
@@ -422,92 +452,115 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restric
     if (lane == 0) bulk_wait_all();
 }
 
-// 2D: three nodes per warp, lanes 9g .. 9g+8 serve node g, one lane per offset.
+// 2D: a warp takes chunks of up to 48 consecutive nodes, three at a time, lanes
+// 9g .. 9g+8 serving node g (one lane per offset delta).  Lanes 9g .. 9g+3 load
+// node g's corner moduli, which reach its lanes by shuffles; each lane forms
+// the diagonal-class and the {0,1}-class signed sums directly (one combine per
+// axis and row), its two diagonal entries with one FP64 multiply each and its
+// two others in float pairs (kappa pairs scaled as in 3D), stages the three
+// nodes' rows (contiguous in the CSR values) and the warp stores them
+// coalesced.  Nodes next to an out-of-range modulus were written by k_simp_df
+// and are skipped.
+// The corner moduli of the node of lane 9g + c (c < 4) at lattice index (ix, iy).
+__device__ __forceinline__ float2 corner2(const float2 *__restrict__ Edf, int ix, int iy, int cl, bool live, int nx,
+                                          int ny)
+{
+    float2 v = make_float2(0.f, 0.f);
+    if (live && cl < 4) {
+        const int ex = ix - 1 + (cl & 1), ey = iy - 1 + (cl >> 1);
+        if (ex >= 0 && ex < nx && ey >= 0 && ey < ny) v = __ldg(&Edf[(int64_t)ey * nx + ex]);
+    }
+    return v;
+}
+
 template <int WPB>
 __global__ void __launch_bounds__(WPB * 32)
-k_lattice_assemble2(int nx, int ny, int64_t nn, const int64_t *__restrict__ node_off,
+k_lattice_assemble2(int nx, int ny, int64_t nn, int chunk, const int64_t *__restrict__ node_off,
                     const float2 *__restrict__ Edf, const float2 *__restrict__ kappa_g,
-                    const double *__restrict__ K0, const double *__restrict__ rho, SimpParams sp,
-                    double *__restrict__ vals)
+                    double *__restrict__ vals, const unsigned *__restrict__ flag, unsigned gen, uint32_t pbias,
+                    double kscale)
 {
-    __shared__ float2 kap_s[9 * 4];
-    __shared__ double stage_s[WPB][3 * 9 * 4];   // three nodes' rows, written back coalesced
-    for (int t = threadIdx.x; t < 9 * 4; t += blockDim.x) kap_s[t] = kappa_g[t];
-    __syncthreads();
-    double *stage = stage_s[threadIdx.x >> 5];
+    __shared__ double stage_s[WPB][3 * 9 * 4];   // three nodes' rows
     const int lane = threadIdx.x & 31;
     const int g = lane < 27 ? lane / 9 : 2;
-    const int dl = lane < 27 ? lane % 9 : 8;
+    const int cl = lane < 27 ? lane - 9 * g : 8;
+    const int dl = cl;
     const int dx = dl % 3 - 1, dy = dl / 3 - 1;
-    df kap[4];
-    for (int q = 0; q < 4; q++) kap[q] = df{kap_s[dl * 4 + q].x, kap_s[dl * 4 + q].y};
-    const int N[3] = {nx, ny, 1};
+    // the lane's kappa: diagonal entries in FP64, the others as (scaled) float pairs
+    const float2 k01 = kappa_g[dl * 4 + 1], k10 = kappa_g[dl * 4 + 2];
+    const double k00 = ((double)kappa_g[dl * 4].x + (double)kappa_g[dl * 4].y) * kscale;
+    const double k11 = ((double)kappa_g[dl * 4 + 3].x + (double)kappa_g[dl * 4 + 3].y) * kscale;
+    // axis options: the low cell (L), the high one (H), or both: H + L on the
+    // diagonal class, H - L on the {0,1} class (axes with delta 0)
+    const bool lx = dx < 0, ly = dy < 0;
+    const float cdx = dx == 0 ? 1.f : 0.f, cdy = dy == 0 ? 1.f : 0.f;
+    grid_dep_wait();
+    grid_dep_launch();
+    const bool anybad = __ldcg(flag) == gen;
+    double *stage = stage_s[threadIdx.x >> 5];
+    const int64_t nchunks = (nn + chunk - 1) / chunk;
     const int64_t warps = (int64_t)gridDim.x * WPB;
-    for (int64_t n0 = ((int64_t)blockIdx.x * WPB + (threadIdx.x >> 5)) * 3; n0 < nn; n0 += warps * 3) {
-        const int64_t n = n0 + g;
-        const bool live = lane < 27 && n < nn;
-        int idx[3] = {0, 0, 0};
-        if (live) {
-            idx[0] = (int)(n % (nx + 1));
-            idx[1] = (int)(n / (nx + 1));
-        }
-        df E[4];
-        bool bad = false;
-#pragma unroll
-        for (int c = 0; c < 4; c++) {
-            E[c] = df{0.f, 0.f};
-            const int ex = idx[0] - 1 + (c & 1), ey = idx[1] - 1 + (c >> 1);
-            if (live && ex >= 0 && ex < nx && ey >= 0 && ey < ny) {
-                const float2 v = Edf[(int64_t)ey * nx + ex];
-                E[c] = df{v.x, v.y};
-                bad |= isnan(v.y);
+    for (int64_t ch = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5); ch < nchunks; ch += warps) {
+        const int64_t nb = ch * chunk, ne = min(nb + (int64_t)chunk, nn);
+        int ix = (int)((nb + g) % (nx + 1)), iy = (int)((nb + g) / (nx + 1));
+        int64_t vbase = 4 * node_off[nb];
+        // node g's corner moduli from lanes 9g .. 9g+3, fetched one pass ahead
+        float2 vn = corner2(Edf, ix, iy, cl, lane < 27 && nb + g < ne, nx, ny);
+        for (int64_t n0 = nb; n0 < ne; n0 += 3) {
+            const int64_t n = n0 + g;
+            const bool live = lane < 27 && n < ne;
+            const float2 v = vn;
+            const int idx[2] = {ix, iy};
+            ix += 3;
+            while (ix > nx) {
+                ix -= nx + 1;
+                iy++;
             }
-        }
-        int lo[2], cnt[2];
-        for (int m = 0; m < 2; m++) {
-            lo[m] = idx[m] > 0 ? -1 : 0;
-            cnt[m] = (idx[m] < N[m] ? 1 : 0) - lo[m] + 1;
-        }
-        const bool valid = live && dx >= lo[0] && dx < lo[0] + cnt[0] && dy >= lo[1] && dy < lo[1] + cnt[1];
-        const int mi = (dx - lo[0]) + cnt[0] * (dy - lo[1]);
-        const int rowlen = 2 * cnt[0] * cnt[1];
-        double *base = live ? vals + 4 * node_off[n] : vals;
-        if (__any_sync(kFull, bad)) {
-            // the whole warp takes the FP64 route for its (up to) three nodes
-            lattice_node_fp64<2>(nx, ny, 1, idx[0], idx[1], 0, dl, valid, mi, rowlen, base, K0, rho, sp);
-            continue;
-        }
-        // signed sums over the shared cells: diagonal class and the {0,1} class
-        df Td = df{0.f, 0.f}, Tp = df{0.f, 0.f};
+            vn = corner2(Edf, ix, iy, cl, lane < 27 && n + 3 < ne, nx, ny);
+            unsigned badm = 0u;
+            if (anybad) badm = __ballot_sync(kFull, live && cl < 4 && isnan(v.y));
+            df E[4];
 #pragma unroll
-        for (int c = 0; c < 4; c++) {
-            const int cx = c & 1, cy = c >> 1;
-            // cell c is shared with the neighbour iff the neighbour's corner stays in {0, 1}
-            const bool shared = (1 - cx + dx >= 0) && (1 - cx + dx <= 1) && (1 - cy + dy >= 0) && (1 - cy + dy <= 1);
-            if (!shared) continue;
-            const bool flip = ((dx == 0 && cx == 0) != (dy == 0 && cy == 0));
-            Td = df_add(Td, E[c]);
-            Tp = df_add(Tp, flip ? df_neg(E[c]) : E[c]);
-        }
-        // the (up to) three nodes' blocks are consecutive in the CSR values
-        const int64_t n_last = min(n0 + 2, nn - 1);
-        const int64_t off0 = node_off[n0];
-        const int span = (int)(4 * (node_off[n_last + 1] - off0));
-        const int sbase = live ? (int)(4 * (node_off[n] - off0)) : 0;
-        if (valid) {
-#pragma unroll
-            for (int i = 0; i < 2; i++) {
-                double *row = stage + sbase + i * rowlen + 2 * mi;
-#pragma unroll
-                for (int j = 0; j < 2; j++) {
-                    const df v = df_mul_raw(kap[i * 2 + j], i == j ? Td : Tp);
-                    row[j] = df_to_double(v.h, v.l);
+            for (int c = 0; c < 4; c++) {
+                E[c] = df{__shfl_sync(kFull, v.x, 9 * g + c), __shfl_sync(kFull, v.y, 9 * g + c)};
+            }
+            bool valid;
+            int mi, rowlen;
+            node_layout2(idx, nx, ny, dx, dy, live, valid, mi, rowlen);
+            const int blk = live ? 2 * rowlen : 0;
+            // offsets of the three nodes' blocks in the staged span
+            const int b0 = __shfl_sync(kFull, blk, 0), b1 = __shfl_sync(kFull, blk, 9), b2 = __shfl_sync(kFull, blk, 18);
+            const int sbase = g == 0 ? 0 : (g == 1 ? b0 : b0 + b1);
+            const int span = b0 + b1 + b2;
+            if (valid) {
+                // along x in each row (cy = 0: cells 0, 1; cy = 1: cells 2, 3), then along y
+                const df d0 = df_add(lx ? E[0] : E[1], df{cdx * E[0].h, cdx * E[0].l});
+                const df d1 = df_add(lx ? E[2] : E[3], df{cdx * E[2].h, cdx * E[2].l});
+                const df p0 = df_add(lx ? E[0] : E[1], df{-cdx * E[0].h, -cdx * E[0].l});
+                const df p1 = df_add(lx ? E[2] : E[3], df{-cdx * E[2].h, -cdx * E[2].l});
+                const df Td = df_add(ly ? d0 : d1, df{cdy * d0.h, cdy * d0.l});
+                const df Tp = df_add(ly ? p0 : p1, df{-cdy * p0.h, -cdy * p0.l});
+                const double tdd = df_to_double_biased(Td.h, Td.l, 0x38000000u);
+                double *r0 = stage + sbase + 2 * mi, *r1 = r0 + rowlen;
+                r0[0] = k00 * tdd;
+                r1[1] = k11 * tdd;
+                const df v01 = df_mul_raw(df{k01.x, k01.y}, Tp), v10 = df_mul_raw(df{k10.x, k10.y}, Tp);
+                r0[1] = df_to_double_biased(v01.h, v01.l, pbias);
+                r1[0] = df_to_double_biased(v10.h, v10.l, pbias);
+            }
+            __syncwarp();
+            if (!badm) {
+                for (int t = lane; t < span; t += 32) __stcs(vals + vbase + t, stage[t]);
+            } else {
+                // skip the rows of nodes whose corner lanes saw an out-of-range modulus
+                for (int t = lane; t < span; t += 32) {
+                    const int gg = t < b0 ? 0 : (t < b0 + b1 ? 1 : 2);
+                    if (!(badm & (0xfu << (9 * gg)))) __stcs(vals + vbase + t, stage[t]);
                 }
             }
+            __syncwarp();
+            vbase += span;
         }
-        __syncwarp();
-        for (int t = lane; t < span; t += 32) __stcs(vals + 4 * off0 + t, stage[t]);
-        __syncwarp();
     }
 }
 
@@ -712,9 +765,9 @@ static cudaError_t lattice_assemble_u(const soptx_mesh_s &m, const double *rho, 
     // a fresh nonzero generation per call marks this call's out-of-range flag
     unsigned gen = ++m.lattice_gen;
     if (gen == 0u) gen = ++m.lattice_gen;
-    k_simp_df<<<std::max(egrid, 1), eb, 0, st>>>(h.lat_n[0], h.lat_n[1], h.lat_n[2], h.nc, rho, sp,
-                                                 (float2 *)m.d.Edf, m.d.node_off, m.d.K0, vals,
-                                                 h.dim == 3 ? m.d.lat_bad : nullptr, gen, h.ndof,
+    k_simp_df<<<std::max(egrid, 1), eb, 0, st>>>(h.dim, h.lat_n[0], h.lat_n[1], h.lat_n[2], h.nc, rho, sp,
+                                                 (float2 *)m.d.Edf, m.d.node_off, m.d.K0, vals, m.d.lat_bad, gen,
+                                                 h.ndof,
                                                  m.d.udf ? u : nullptr, m.d.udf);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
@@ -736,11 +789,17 @@ static cudaError_t lattice_assemble_u(const soptx_mesh_s &m, const double *rho, 
                 0x38000000u + ((uint32_t)h.lat_kshift << 20), std::ldexp(1.0, h.lat_kshift));
         }
     } else {
+        // chunks of 3 .. 48 nodes: long enough to amortise a chunk's set-up, short
+        // enough to give every warp slot of the GPU work on small meshes
         const int64_t groups = (h.nn + 2) / 3;
-        const int grid = (int)std::min<int64_t>((groups + WPB - 1) / WPB, 152 * 8);
-        k_lattice_assemble2<WPB><<<grid, WPB * 32, 0, st>>>(h.lat_n[0], h.lat_n[1], h.nn, m.d.node_off,
+        const int chunk = 3 * (int)std::max<int64_t>(1, std::min<int64_t>(16, groups / (152 * 4 * WPB)));
+        const int64_t chunks = (h.nn + chunk - 1) / chunk;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((chunks + WPB - 1) / WPB, 152 * 8));
+        k_lattice_assemble2<WPB><<<grid, WPB * 32, 0, st>>>(h.lat_n[0], h.lat_n[1], h.nn, chunk, m.d.node_off,
                                                             (const float2 *)m.d.Edf, (const float2 *)m.d.kappa,
-                                                            m.d.K0, rho, sp, vals);
+                                                            vals, m.d.lat_bad, gen,
+                                                            0x38000000u + ((uint32_t)h.lat_kshift << 20),
+                                                            std::ldexp(1.0, h.lat_kshift));
     }
     return cudaGetLastError();
 }
