@@ -520,7 +520,8 @@ def run_ours(args, rank, world, local_rank):
         if world > 1:
             torch.distributed.barrier()
         wall = time.perf_counter() - wall0
-    step_ms = sum(e[0].elapsed_time(e[1]) for e in ev)
+    per_step = np.array([e[0].elapsed_time(e[1]) for e in ev])
+    step_ms = float(per_step.sum())
     step_ms = max_over_ranks([step_ms], world, dev)[0]
     clocks = sampler.summary()
 
@@ -583,6 +584,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD_DESC[args.workload], "path": mesh.path, "nnz": nnz, "ndof": ndof,
                    "n_cells": nc, "elem_prec": args.elem_prec, "l2": "flushed (256 MiB write) between steps",
                    "parallelism": "replicas" if world > 1 else "single"},
+        "step_us_p10_p50_p90": [float(np.percentile(per_step, q)) * 1e3 for q in (10, 50, 90)],
         "sens_elems_per_s": job_rate(nc, world, K, step_ms),
         "setup_s": setup_s,
         "separate_calls": {"assemble_ms": asm_ms / n_split, "sensitivity_ms": sens_ms / n_split,

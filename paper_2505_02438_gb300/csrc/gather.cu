@@ -29,6 +29,11 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kGW = 8;   // warps per CTA
 
+// Resident CTAs per SM the generic gather is compiled for (the row gathers
+// take theirs as a template argument): it caps the registers and, through the
+// per-warp accumulator buffers, the warps a CTA gets.
+constexpr int kGatherMinB = 2;
+
 __global__ void k_prep(int64_t nc, const double *__restrict__ rho, SimpParams sp, float2 *__restrict__ Edf,
                        int64_t ndof, const double *__restrict__ u, float2 *__restrict__ udf)
 {
@@ -151,7 +156,7 @@ __device__ __noinline__ void gather_node_fp64_warp(const GatherArgs<KT> &A, bool
 // accumulated (its index two cells ahead).  Rows longer than R LPR columns
 // take nck chunks (CH).
 template <int D, typename KT, bool SENS, int NPW, int R, bool CH>
-__global__ void __launch_bounds__(kGW * 32, 2) k_gather_nodes(const GatherArgs<KT> A)
+__global__ void __launch_bounds__(kGW * 32, kGatherMinB) k_gather_nodes(const GatherArgs<KT> A)
 {
     using KE = KEntry<KT>;
     using KV = typename KE::T;
@@ -324,8 +329,8 @@ __global__ void __launch_bounds__(kGW * 32, 2) k_gather_nodes(const GatherArgs<K
 // a cell's nodes arrive once per cell (lane b of the group loads pos(e, b))
 // and reach the lanes that need them by shuffles; the item loop is unrolled
 // by two so the prefetched item never has to be copied.
-template <int D, int NB, typename KT, bool SENS, int NPW, int R, int LPR>
-__global__ void __launch_bounds__(kGW * 32, 2) k_gather_rows(const GatherArgs<KT> A)
+template <int D, int NB, typename KT, bool SENS, int NPW, int R, int LPR, int MINB>
+__global__ void __launch_bounds__(kGW * 32, MINB) k_gather_rows(const GatherArgs<KT> A)
 {
     using KE = KEntry<KT>;
     using KV = typename KE::T;
@@ -528,13 +533,12 @@ __global__ void __launch_bounds__(256) k_sens_finalize(int64_t nc, int nb, const
 
 int ggrid(int64_t items, int per) { return (int)std::max<int64_t>(1, std::min<int64_t>((items + per - 1) / per, 152 * 16)); }
 
-// Lane layout per mesh type: (nodes per warp, lanes per row, rounds per
-// chunk).  P2 tetrahedra (30 columns): 2 nodes x 3 rows x 5 lanes, 6 rounds;
-// P3 triangles (20 columns): 4 nodes x 2 rows x 4 lanes, 5 rounds; anything
-// else one node per warp, 10 (3D) or 16 (2D) lanes per row, chunks of 4 rounds.
+// Launch of one gather: NPW nodes per warp, lpr lanes per row, R rounds per
+// chunk, and as many warps per CTA as let minb CTAs share an SM's shared
+// memory (the layouts per cell type are chosen in gather_t).
 template <int D, typename KT, int NPW, typename Kern>
 cudaError_t gather_launch(const soptx_mesh_s &m, const double *rho, double *vals, bool sens, int R, int lpr,
-                          Kern kern, cudaStream_t st)
+                          int minb, Kern kern, cudaStream_t st)
 {
     const auto &h = m.h;
     GatherArgs<KT> A;
@@ -559,7 +563,9 @@ cudaError_t gather_launch(const soptx_mesh_s &m, const double *rho, double *vals
     A.vals = vals;
     A.part = sens ? m.d.part : nullptr;
     const size_t per_warp = (size_t)NPW * (D * D + (sens ? D : 0)) * h.max_deg * sizeof(float2);
-    const int wpb = (int)std::max<size_t>(1, std::min<size_t>(kGW, (size_t)(200 * 1024) / per_warp));
+    // minb CTAs must fit in the SM's 228 KiB of shared memory (1 KiB of it reserved per CTA)
+    const size_t cta_smem = std::min<size_t>(200 * 1024, (228 * 1024) / minb - 1024);
+    const int wpb = (int)std::max<size_t>(1, std::min<size_t>(kGW, cta_smem / per_warp));
     const size_t smem = per_warp * wpb;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
@@ -573,20 +579,33 @@ template <int D, typename KT>
 cudaError_t gather_t(const soptx_mesh_s &m, const double *rho, double *vals, bool sens, cudaStream_t st)
 {
     const int nb = m.h.nb;
-#define SOPTX_ROWS(NB, NPW, R, LPR)                                                                            \
-    return gather_launch<D, KT, NPW>(m, rho, vals, sens, R, LPR,                                              \
-                                     sens ? k_gather_rows<D, NB, KT, true, NPW, R, LPR>                        \
-                                          : k_gather_rows<D, NB, KT, false, NPW, R, LPR>,                      \
-                                     st)
+#define SOPTX_ROWS(NB, SENS, NPW, R, LPR, MINB)                                                                \
+    return gather_launch<D, KT, NPW>(m, rho, vals, sens, R, LPR, MINB,                                        \
+                                     k_gather_rows<D, NB, KT, SENS, NPW, R, LPR, MINB>, st)
+    // Per cell type the lane layout and the CTAs per SM, measured: with the
+    // sensitivity the kernels hold more registers and run at 3 CTAs per SM
+    // (80 registers); the assembly alone fits in 64 registers at 4 CTAs per SM.
     if constexpr (D == 3) {
-        if (nb == 10) SOPTX_ROWS(10, 2, 6, 5);   // P2 tetrahedra: 2 nodes x 3 rows x 5 lanes, 6 rounds
-        if (nb == 8) SOPTX_ROWS(8, 2, 6, 4);     // Q1 hexahedra: 2 nodes x 3 rows x 4 lanes, 6 rounds
+        if (nb == 10) {   // P2 tetrahedra
+            if (sens) SOPTX_ROWS(10, true, 2, 6, 5, 3);   // 2 nodes x 3 rows x 5 lanes, 6 rounds
+            SOPTX_ROWS(10, false, 1, 3, 10, 4);           // 1 node x 3 rows x 10 lanes, 3 rounds
+        }
+        if (nb == 8) {    // Q1 hexahedra
+            if (sens) SOPTX_ROWS(8, true, 2, 6, 4, 3);    // 2 nodes x 3 rows x 4 lanes, 6 rounds
+            SOPTX_ROWS(8, false, 1, 3, 8, 4);             // 1 node x 3 rows x 8 lanes, 3 rounds
+        }
     } else {
-        if (nb == 10) SOPTX_ROWS(10, 4, 5, 4);   // P3 triangles: 4 nodes x 2 rows x 4 lanes, 5 rounds
-        if (nb == 4) SOPTX_ROWS(4, 4, 2, 4);     // Q1 quadrilaterals: 4 nodes x 2 rows x 4 lanes, 2 rounds
+        if (nb == 10) {   // P3 triangles: 4 nodes x 2 rows x 4 lanes, 5 rounds
+            if (sens) SOPTX_ROWS(10, true, 4, 5, 4, 3);
+            SOPTX_ROWS(10, false, 4, 5, 4, 4);
+        }
+        if (nb == 4) {    // Q1 quadrilaterals: 4 nodes x 2 rows x 4 lanes, 2 rounds
+            if (sens) SOPTX_ROWS(4, true, 4, 2, 4, 3);
+            SOPTX_ROWS(4, false, 4, 2, 4, 4);
+        }
     }
 #undef SOPTX_ROWS
-    return gather_launch<D, KT, 1>(m, rho, vals, sens, 4, 32 / D,
+    return gather_launch<D, KT, 1>(m, rho, vals, sens, 4, 32 / D, kGatherMinB,
                                    sens ? k_gather_nodes<D, KT, true, 1, 4, true> : k_gather_nodes<D, KT, false, 1, 4, true>, st);
 }
 
