@@ -168,9 +168,10 @@ def kernel_source_sha(kernel_file):
     return h.hexdigest()[:16]
 
 
-def traffic_record(kernel_file, kernel_name):
-    """dram bytes per launch of `kernel_name` from the committed ncu summary,
-    valid only while the kernel source is unchanged (kernel_source_sha matches)."""
+def traffic_record(kernel_file, kernel_name, workload, prec="fp64"):
+    """dram bytes per launch of `kernel_name` on `workload` (element matrices in
+    `prec`) from the committed ncu summary, valid only while the kernel source
+    is unchanged (kernel_source_sha matches)."""
     src = os.path.join(ROOT, "paper_2505_02438_gb300", "csrc", kernel_file)
     rec = os.path.join(ROOT, "profiles", "traffic.txt")
     if not (os.path.exists(src) and os.path.exists(rec)):
@@ -178,7 +179,8 @@ def traffic_record(kernel_file, kernel_name):
     h = kernel_source_sha(kernel_file)
     for line in open(rec):
         kv = dict(x.split("=", 1) for x in line.split() if "=" in x)
-        if kv.get("kernel") == kernel_name and kv.get("source_sha") == h:
+        if kv.get("kernel") == kernel_name and kv.get("source_sha") == h and kv.get("workload") == workload \
+                and kv.get("prec", "fp64") == prec:
             return float(kv["dram_bytes_per_launch"])
     return None
 
@@ -393,7 +395,8 @@ def run_solve(args, rank, world, local_rank):
             "config": {"workload": WORKLOAD_DESC["hex"], "nnz": nnz, "ndof": ndof,
                        "l2": "flushed (256 MiB write) between steps"},
             "roofline": {"bound": "hbm", "kernel": "k_spmv", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": None, "alg_bytes_per_launch": alg},
+                         "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic_record("solve.cu", "k_spmv", wl.name), "alg_bytes_per_launch": alg},
             "cg": {"iterations": info["iterations"], "converged": info["converged"],
                    "rel_residual": info["rel_residual"], "rtol": args.cg_rtol, "ms": cg_ms,
                    "ms_per_iteration": cg_ms / max(1, info["iterations"]),
@@ -574,7 +577,7 @@ def run_ours(args, rank, world, local_rank):
         achieved = ab["step"] / (step_ms / K / 1e3) / 1e9
         kernel_name = "k_gather_rows" if (wl.dim, mesh.nb) in ((3, 10), (3, 8), (2, 10), (2, 4)) else "k_gather_nodes"
         kernel_file, alg_launch = "gather.cu", ab["step"]
-    traffic = traffic_record(kernel_file, kernel_name)
+    traffic = traffic_record(kernel_file, kernel_name, wl.name, args.elem_prec)
     value = job_rate(nnz, world, K, step_ms) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "GNNZ/s", "n_gpus": world, "steps": K,
