@@ -3,6 +3,7 @@ element by element, on every cell type and order (several tiles and ragged
 tails per kernel), both element precisions, and the edge cases."""
 import numpy as np
 import pytest
+import scipy.sparse as sp
 import torch
 
 import oracle
@@ -151,6 +152,55 @@ def test_lattice_out_of_range_moduli_take_fp64_route(P, cell, mk):
     vals = m.assemble_K(to_dev(rho)).cpu().numpy()
     rp, ci, v, va, _ = oracle_csr(cell, 1, c, cl, mat, rho)
     assert np.all(np.abs(vals - v) <= TOL64 * va + 1e-300)
+
+
+GENERAL_OOR = [c for c in CASES if c[0] in ("tet_p2_5x3x2_jitter", "tri_p3_17x9_jitter", "hex_q1_relabelled_uniform",
+                                           "quad_q1_9x6_distorted", "hex_q1_5x4x3_distorted", "tet_p1_5x3x2_jitter",
+                                           "quad_q2_7x5")]
+
+
+@pytest.mark.parametrize("name,cell,k,coords,cells", GENERAL_OOR, ids=[c[0] for c in GENERAL_OOR])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_general_out_of_range_moduli_take_fp64_route(P, name, cell, k, coords, cells, prec):
+    """The general gathers (every row layout, with and without the
+    sensitivity, and the generic node gather) with moduli below the
+    float-pair range: those nodes are gathered in plain FP64, the results match
+    the oracle, and the one-call step gives the bits of the separate calls."""
+    mat = (1.0, 0.0, 0.3, 3.0, 0)
+    m = P.Mesh(cell, k, coords, cells, *mat, elem_prec=prec)
+    assert m.path in ("cached", "uniform")
+    g = np.random.default_rng(12)
+    rho = g.uniform(0.001, 1.0, len(cells))
+    rho[::5] = 1e-9          # E = 1e-27
+    rho[1::7] = 0.0          # E = 0 exactly
+    rho[3::11] = 1e-30       # E = 1e-90
+    vals = m.assemble_K(to_dev(rho))
+    rp, ci, v, va, ndof = oracle_csr(cell, k, coords, cells, mat, rho)
+    tol = TOL64 if prec == "fp64" else TOL32
+    err = np.abs(vals.cpu().numpy() - v)
+    # entries that vanish in exact arithmetic carry rounding noise in both codes: an absolute floor
+    # relative to the largest entry and, for the entries whose node pair shares tiny cells only (the
+    # FP64 route this test is about), relative to the largest of those
+    assert np.all(err <= tol * va + (1e-15 if prec == "fp64" else 1e-7) * va.max() + 1e-300)
+    cn, nn = oracle.number(cell, k, len(coords), cells)
+    d = 2 if cell in ("tri", "quad") else 3
+    pairs = lambda sel: sp.coo_matrix((np.ones(sel.sum() * cn.shape[1] ** 2),
+                                       (np.repeat(cn[sel], cn.shape[1], axis=1).ravel(),
+                                        np.tile(cn[sel], (1, cn.shape[1])).ravel())), shape=(nn, nn)).tocsr()
+    normal, small = pairs(rho >= 1e-8), pairs((rho < 1e-8) & (rho > 0))
+    row = np.repeat(np.arange(len(rp) - 1), np.diff(rp)) // d
+    col = ci // d
+    tiny = (np.asarray(small[row, col]).ravel() > 0) & (np.asarray(normal[row, col]).ravel() == 0)
+    assert tiny.any()
+    fl = 1e-15 if prec == "fp64" else 1e-6
+    assert np.all(err[tiny] <= tol * va[tiny] + fl * va[tiny].max() + 1e-300)
+    u = g.standard_normal(ndof)
+    dc, c = m.sensitivity(to_dev(rho), to_dev(u))
+    dco, so, co, sabs = oracle.sensitivity(cell, k, coords, cells, mat, rho, u, with_abs=True)
+    dE = 3.0 * rho ** 2
+    assert np.all(np.abs(dc.cpu().numpy() - dco) <= tol * dE * sabs + 1e-300)
+    v2, dc2, c2 = m.step(to_dev(rho), to_dev(u))
+    assert torch.equal(v2, vals) and torch.equal(dc2, dc) and torch.equal(c2, c)
 
 
 def test_lattice_out_of_range_moduli_between_normal_calls(P):
