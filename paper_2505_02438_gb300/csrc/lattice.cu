@@ -120,9 +120,9 @@ __device__ __noinline__ void lattice_node_fp64(int nx, int ny, int nz, int ix, i
     lattice_node_fp64_body<D>(nx, ny, nz, ix, iy, iz, dl, valid, mi, rowlen, base, K0, rho, sp);
 }
 
-// Node chunks per warp: consecutive nodes, so the lattice index is decoded once
-// per chunk and then stepped; the next node's moduli are fetched before the
-// current node is processed.
+// Node chunks per warp: at most kChunk consecutive nodes, so the lattice index
+// is decoded once per chunk and then stepped; the next node's moduli are
+// fetched before the current node is processed.
 constexpr int kChunk = 16;
 // Sign classes (0 = i == j, 1 = {0,1}, 2 = {0,2}, 3 = {1,2}) whose entries are
 // formed by one FP64 multiply each; 2 puts 5 of the 9 entries on the FP64 pipe.
@@ -303,7 +303,7 @@ k_simp_df(int dim, int nx, int ny, int nz, int64_t nc, const double *__restrict_
 // buffers was 12% more instructions: 409 against 358 per node).
 template <int WPB>
 __global__ void __launch_bounds__(WPB * 32, SOPTX_LATTICE_MINBLOCKS)
-k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restrict__ node_off,
+k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, int chunk, const int64_t *__restrict__ node_off,
                           const float2 *__restrict__ Edf, const float2 *__restrict__ kappa_g,
                           const double *__restrict__ K0, const double *__restrict__ rho, SimpParams sp,
                           double *__restrict__ vals, const unsigned *__restrict__ flag, unsigned gen,
@@ -339,11 +339,11 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, const int64_t *__restric
     double *stage = stage_s[threadIdx.x >> 5];
     float2(*tab)[64] = tab_s[threadIdx.x >> 5];
 
-    const int64_t nchunks = (nn + kChunk - 1) / kChunk;
+    const int64_t nchunks = (nn + chunk - 1) / chunk;
     const int64_t warps = (int64_t)gridDim.x * WPB;
     for (int64_t ch = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5); ch < nchunks; ch += warps) {
-        const int64_t n_begin = ch * kChunk;
-        const int64_t n_end = min(n_begin + (int64_t)kChunk, nn);
+        const int64_t n_begin = ch * chunk;
+        const int64_t n_end = min(n_begin + (int64_t)chunk, nn);
         NodeIter ia;
         ia.decode((uint32_t)n_begin, nx, ny);
         NodeIter ib = ia;
@@ -775,16 +775,22 @@ static cudaError_t lattice_assemble_u(const soptx_mesh_s &m, const double *rho, 
     if (h.dim == 3) {
         const int64_t chunks = (h.nn + kChunk - 1) / kChunk;
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((chunks + WPB - 1) / WPB, 152 * 4));
+        // the chunk length (at most kChunk, even) that gives every warp the same
+        // number of chunks, give or take one: no warp runs a round alone at the end
+        const int64_t warps = (int64_t)grid * WPB;
+        const int64_t rounds = (h.nn + warps * kChunk - 1) / (warps * kChunk);
+        int chunk = (int)std::max<int64_t>(1, (h.nn + warps * rounds - 1) / (warps * rounds));
+        chunk += chunk & 1;
         if (u && m.d.udf) {
             // one-call step: scheduled while the moduli kernel runs (see grid_dep_wait)
             err = launch_dependent(k_lattice_assemble3<WPB>, grid, WPB * 32, st, h.lat_n[0], h.lat_n[1],
-                                   h.lat_n[2], h.nn, m.d.node_off, (const float2 *)m.d.Edf,
+                                   h.lat_n[2], h.nn, chunk, m.d.node_off, (const float2 *)m.d.Edf,
                                    (const float2 *)m.d.kappa, m.d.K0, rho, sp, vals, m.d.lat_bad, gen,
                                    0x38000000u + ((uint32_t)h.lat_kshift << 20), std::ldexp(1.0, h.lat_kshift));
             if (err != cudaSuccess) return err;
         } else {
             k_lattice_assemble3<WPB><<<grid, WPB * 32, 0, st>>>(
-                h.lat_n[0], h.lat_n[1], h.lat_n[2], h.nn, m.d.node_off, (const float2 *)m.d.Edf,
+                h.lat_n[0], h.lat_n[1], h.lat_n[2], h.nn, chunk, m.d.node_off, (const float2 *)m.d.Edf,
                 (const float2 *)m.d.kappa, m.d.K0, rho, sp, vals, m.d.lat_bad, gen,
                 0x38000000u + ((uint32_t)h.lat_kshift << 20), std::ldexp(1.0, h.lat_kshift));
         }
