@@ -685,7 +685,9 @@ static cudaError_t lattice_sens_t(const soptx_mesh_s &m, const double *rho, cons
     if ((int)h.sectors.size() != (h.dim << h.dim) * h.dim) return cudaErrorInvalidValue;
     if (after_assembly && h.dim == 3) {
         // in the one-call step, right after the 3D assembly, whose blocks let it start
-        // once the moduli kernel (the producer of u's pairs) has completed
+        // once the moduli kernel (the producer of u's pairs) has completed (as a
+        // dependent launch after the 2D assembly the sensitivity made some steps
+        // several times longer)
         return launch_dependent(k_lattice_sens<3, UT>, grid, kSensThreads, st, h.lat_n[0], h.lat_n[1], h.nc, rho,
                                 u, simp_params(m.mat), sector_table<3>(h.sectors), gscale, out, m.d.scratch,
                                 m.d.counter, c);
@@ -781,19 +783,12 @@ static cudaError_t lattice_assemble_u(const soptx_mesh_s &m, const double *rho, 
         const int64_t rounds = (h.nn + warps * kChunk - 1) / (warps * kChunk);
         int chunk = (int)std::max<int64_t>(1, (h.nn + warps * rounds - 1) / (warps * rounds));
         chunk += chunk & 1;
-        if (u && m.d.udf) {
-            // one-call step: scheduled while the moduli kernel runs (see grid_dep_wait)
-            err = launch_dependent(k_lattice_assemble3<WPB>, grid, WPB * 32, st, h.lat_n[0], h.lat_n[1],
-                                   h.lat_n[2], h.nn, chunk, m.d.node_off, (const float2 *)m.d.Edf,
-                                   (const float2 *)m.d.kappa, m.d.K0, rho, sp, vals, m.d.lat_bad, gen,
-                                   0x38000000u + ((uint32_t)h.lat_kshift << 20), std::ldexp(1.0, h.lat_kshift));
-            if (err != cudaSuccess) return err;
-        } else {
-            k_lattice_assemble3<WPB><<<grid, WPB * 32, 0, st>>>(
-                h.lat_n[0], h.lat_n[1], h.lat_n[2], h.nn, chunk, m.d.node_off, (const float2 *)m.d.Edf,
-                (const float2 *)m.d.kappa, m.d.K0, rho, sp, vals, m.d.lat_bad, gen,
-                0x38000000u + ((uint32_t)h.lat_kshift << 20), std::ldexp(1.0, h.lat_kshift));
-        }
+        // scheduled while the moduli kernel runs (see grid_dep_wait)
+        err = launch_dependent(k_lattice_assemble3<WPB>, grid, WPB * 32, st, h.lat_n[0], h.lat_n[1], h.lat_n[2],
+                               h.nn, chunk, m.d.node_off, (const float2 *)m.d.Edf, (const float2 *)m.d.kappa, m.d.K0,
+                               rho, sp, vals, m.d.lat_bad, gen, 0x38000000u + ((uint32_t)h.lat_kshift << 20),
+                               std::ldexp(1.0, h.lat_kshift));
+        if (err != cudaSuccess) return err;
     } else {
         // chunks of 3 .. 48 nodes: long enough to amortise a chunk's set-up, short
         // enough to give every warp slot of the GPU work on small meshes
@@ -801,11 +796,10 @@ static cudaError_t lattice_assemble_u(const soptx_mesh_s &m, const double *rho, 
         const int chunk = 3 * (int)std::max<int64_t>(1, std::min<int64_t>(16, groups / (152 * 4 * WPB)));
         const int64_t chunks = (h.nn + chunk - 1) / chunk;
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((chunks + WPB - 1) / WPB, 152 * 8));
-        k_lattice_assemble2<WPB><<<grid, WPB * 32, 0, st>>>(h.lat_n[0], h.lat_n[1], h.nn, chunk, m.d.node_off,
-                                                            (const float2 *)m.d.Edf, (const float2 *)m.d.kappa,
-                                                            vals, m.d.lat_bad, gen,
-                                                            0x38000000u + ((uint32_t)h.lat_kshift << 20),
-                                                            std::ldexp(1.0, h.lat_kshift));
+        err = launch_dependent(k_lattice_assemble2<WPB>, grid, WPB * 32, st, h.lat_n[0], h.lat_n[1], h.nn, chunk,
+                               m.d.node_off, (const float2 *)m.d.Edf, (const float2 *)m.d.kappa, vals, m.d.lat_bad,
+                               gen, 0x38000000u + ((uint32_t)h.lat_kshift << 20), std::ldexp(1.0, h.lat_kshift));
+        if (err != cudaSuccess) return err;
     }
     return cudaGetLastError();
 }
