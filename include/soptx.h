@@ -165,6 +165,28 @@ soptx_status soptx_assemble_and_sensitivity(soptx_mesh mesh, const double *d_rho
                                             double *d_dc, double *d_c, void *stream);
 
 /*
+ * The per-iteration step from host memory: the results of
+ * soptx_assemble_and_sensitivity (Sec. 2.2 and Appendix D) with rho and u
+ * read from, and dc and c written to, host buffers.
+ *   h_rho : host float64 [n_cells]; h_u : host float64 [ndof]
+ *   d_vals: device float64 [nnz], overwritten with the CSR values of K(rho)
+ *   h_dc  : host float64 [n_cells]; h_c : host float64 [1] or NULL.  When
+ *           h_c == h_dc + n_cells, dc and c come back in one copy.
+ * Asynchronous on `stream`: h_rho and h_u must stay unchanged, and h_dc and
+ * *h_c may be read, only once the stream has completed; page-locked host
+ * buffers (cudaHostAlloc, torch pin_memory) keep the copies asynchronous.
+ * On a box lattice the sensitivities, which need rho and u but not K, run on a
+ * second stream behind u's copy while the moduli and the assembly run on
+ * `stream`; everything is ordered on `stream` when the call returns.  The
+ * first call allocates the device staging (8 (2 n_cells + ndof + 1) bytes, in
+ * soptx_mesh_device_bytes), that stream and two events, kept with the mesh;
+ * calls on one mesh must therefore not overlap.  Results are bitwise those of
+ * the device-pointer calls.
+ */
+soptx_status soptx_step_host(soptx_mesh mesh, const double *h_rho, const double *h_u, double *d_vals,
+                             double *h_dc, double *h_c, void *stream);
+
+/*
  * Backward of f(rho, u) = u^T K(rho) u (the compliance written as a function
  * of an independent u) scaled by the incoming gradient g = *d_gout:
  *   d_grad_rho[e] = g p rho_e^(p-1) (E0 - Emin) u_e^T K_e^0 u_e   (= -g dc_e)

@@ -78,6 +78,7 @@ SIGNATURES = {
     "soptx_assemble_K": (i32, [P, P, P, P]),
     "soptx_sensitivity": (i32, [P, P, P, P, P, P]),
     "soptx_assemble_and_sensitivity": (i32, [P, P, P, P, P, P, P]),
+    "soptx_step_host": (i32, [P, P, P, P, P, P, P]),
     "soptx_compliance_vjp": (i32, [P, P, P, P, P, P, P]),
     "soptx_mesh_destroy": (i32, [P]),
     "soptx_host_plan": (i32, [i32, i32, i32, i64, P, i64, P, Pi64, Pi64, Pi32, Pi32, P, P, P]),

@@ -27,6 +27,16 @@ def _dptr(t, dtype, n, name):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _hptr(t, n, name):
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError("%s must be a host (CPU) tensor" % name)
+    if t.dtype != torch.float64:
+        raise TypeError("%s must have dtype torch.float64, got %s" % (name, t.dtype))
+    if not t.is_contiguous() or t.numel() != n:
+        raise ValueError("%s must be contiguous with %d elements (got %s)" % (name, n, tuple(t.shape)))
+    return ctypes.c_void_p(t.data_ptr())
+
+
 class Mesh:
     """A device-resident mesh: pattern, maps and element data (Sec. 3.2.2).
 
@@ -123,6 +133,24 @@ class Mesh:
             _dptr(vals, torch.float64, self.nnz, "vals"), _dptr(dc, torch.float64, self.n_cells, "dc"),
             _dptr(c, torch.float64, 1, "c"), _stream(stream)))
         return vals, dc, c
+
+    def step_host(self, rho, u, vals=None, dcc=None, stream=None):
+        """The step from host memory (soptx_step_host): rho [NC] and u [ndof]
+        are CPU float64 tensors (pinned for asynchronous copies); returns
+        (vals on the device, dc, c) with dc and c views of one host buffer
+        dcc [NC + 1] (pinned when made here), valid once the stream has
+        completed."""
+        if vals is None:
+            vals = torch.empty(self.nnz, dtype=torch.float64, device=self.device)
+        if dcc is None:
+            dcc = torch.empty(self.n_cells + 1, dtype=torch.float64, pin_memory=True)
+        _hptr(dcc, self.n_cells + 1, "dcc")
+        base = dcc.data_ptr()
+        N.check(N.lib().soptx_step_host(
+            self._h, _hptr(rho, self.n_cells, "rho"), _hptr(u, self.ndof, "u"),
+            _dptr(vals, torch.float64, self.nnz, "vals"), ctypes.c_void_p(base),
+            ctypes.c_void_p(base + 8 * self.n_cells), _stream(stream)))
+        return vals, dcc[:self.n_cells], dcc[self.n_cells:]
 
     def compliance_vjp(self, rho, u, gout, want_u=True, stream=None):
         grad_rho = torch.empty(self.n_cells, dtype=torch.float64, device=self.device)

@@ -34,11 +34,14 @@ static void free_device(DeviceMesh &d)
 {
     void *ptrs[] = {d.indptr, d.indices, d.cell_node, d.node_off, d.inc_ptr, d.inc,
                     d.pos, d.geo, d.M, d.K, d.scratch, d.Edf, d.kappa, d.K0, d.sectors, d.udf, d.part,
-                    d.inc_e, d.inc_a, d.counter, d.xcell, d.qw, d.qdphi, d.qdgeo, d.cg, d.lat_bad};
+                    d.inc_e, d.inc_a, d.counter, d.xcell, d.qw, d.qdphi, d.qdgeo, d.cg, d.lat_bad, d.stage};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (d.cg_exec) cudaGraphExecDestroy(d.cg_exec);
     if (d.cg_cap) cudaStreamDestroy(d.cg_cap);
+    for (cudaEvent_t e : d.ev)
+        if (e) cudaEventDestroy(e);
+    if (d.side) cudaStreamDestroy(d.side);
     d = DeviceMesh{};
 }
 
@@ -408,6 +411,78 @@ soptx_status soptx_assemble_and_sensitivity(soptx_mesh m, const double *d_rho, c
         SOPTX_FAIL(SOPTX_EINVAL, "d_rho / d_u / d_vals / d_dc is NULL");
     return cuda_status(launch_step(*m, d_rho, d_u, d_vals, d_dc, d_c, (cudaStream_t)stream),
                        "soptx_assemble_and_sensitivity");
+}
+
+soptx_status soptx_step_host(soptx_mesh m, const double *h_rho, const double *h_u, double *d_vals, double *h_dc,
+                             double *h_c, void *stream)
+{
+    if (!m) SOPTX_FAIL(SOPTX_EINVAL, "mesh is NULL");
+    const auto &h = m->h;
+    if ((!d_vals && h.nnz > 0) || (h.nc > 0 && !h_dc) || (h.nc > 0 && !h_rho) || (h.ndof > 0 && !h_u))
+        SOPTX_FAIL(SOPTX_EINVAL, "h_rho / h_u / d_vals / h_dc is NULL");
+    auto &d = m->d;
+    cudaError_t e = cudaSuccess;
+    if (!d.stage) {
+        const size_t bytes = (size_t)(2 * h.nc + h.ndof + 1) * sizeof(double);
+        void *p = nullptr;
+        e = dev_alloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return cuda_status(e, "soptx_step_host staging");
+        }
+        cudaStream_t side = nullptr;
+        cudaEvent_t ev[2] = {};
+        e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+        for (int i = 0; i < 2 && e == cudaSuccess; i++) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            for (cudaEvent_t x : ev)
+                if (x) cudaEventDestroy(x);
+            if (side) cudaStreamDestroy(side);
+            cudaFree(p);
+            return cuda_status(e, "soptx_step_host stream");
+        }
+        d.stage = (double *)p;
+        d.side = side;
+        for (int i = 0; i < 2; i++) d.ev[i] = ev[i];
+        m->device_bytes += (int64_t)bytes;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    double *rho_d = d.stage, *u_d = rho_d + h.nc, *dc_d = u_d + h.ndof, *c_d = dc_d + h.nc;
+    const size_t rb = (size_t)h.nc * sizeof(double), ub = (size_t)h.ndof * sizeof(double);
+    // dc and c back: one copy when the caller's c follows its dc
+    auto copy_back = [&](cudaStream_t s) -> cudaError_t {
+        if (h_dc && h_c && h_c == h_dc + h.nc)
+            return cudaMemcpyAsync(h_dc, dc_d, rb + sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaError_t r = rb ? cudaMemcpyAsync(h_dc, dc_d, rb, cudaMemcpyDeviceToHost, s) : cudaSuccess;
+        if (r == cudaSuccess && h_c) r = cudaMemcpyAsync(h_c, c_d, sizeof(double), cudaMemcpyDeviceToHost, s);
+        return r;
+    };
+#define SOPTX_TRY(x)                                                            \
+    do {                                                                        \
+        e = (x);                                                                \
+        if (e != cudaSuccess) return cuda_status(e, "soptx_step_host");         \
+    } while (0)
+    if (m->path == SOPTX_PATH_LATTICE && d.sectors && h.nc > 0) {
+        // the sensitivities need rho and u but not K: they run on the side stream
+        // while the moduli and the assembly run on `stream`.  rho goes first (the
+        // assembly waits for it); u's copy follows it and overlaps the assembly.
+        SOPTX_TRY(cudaMemcpyAsync(rho_d, h_rho, rb, cudaMemcpyHostToDevice, st));
+        SOPTX_TRY(cudaEventRecord(d.ev[0], st));
+        SOPTX_TRY(cudaStreamWaitEvent(d.side, d.ev[0], 0));
+        SOPTX_TRY(cudaMemcpyAsync(u_d, h_u, ub, cudaMemcpyHostToDevice, d.side));
+        SOPTX_TRY(launch_lattice_sensitivity(*m, rho_d, u_d, dc_d, c_d, nullptr, d.side));
+        SOPTX_TRY(copy_back(d.side));
+        SOPTX_TRY(cudaEventRecord(d.ev[1], d.side));
+        SOPTX_TRY(launch_lattice_assemble(*m, rho_d, d_vals, st));
+        SOPTX_TRY(cudaStreamWaitEvent(st, d.ev[1], 0));
+    } else {
+        if (rb) SOPTX_TRY(cudaMemcpyAsync(rho_d, h_rho, rb, cudaMemcpyHostToDevice, st));
+        if (ub) SOPTX_TRY(cudaMemcpyAsync(u_d, h_u, ub, cudaMemcpyHostToDevice, st));
+        SOPTX_TRY(launch_step(*m, rho_d, u_d, d_vals, dc_d, c_d, st));
+        SOPTX_TRY(copy_back(st));
+    }
+#undef SOPTX_TRY
+    return SOPTX_OK;
 }
 
 soptx_status soptx_compliance_vjp(soptx_mesh m, const double *d_rho, const double *d_u, const double *d_gout,

@@ -120,6 +120,10 @@ struct DeviceMesh {
     cudaGraphExec_t cg_exec = nullptr; // the CG iterations between two checks, as a graph
     cudaStream_t cg_cap = nullptr;     // its capture stream
     const void *cg_key[4] = {};        // vals, fixed, u and the iteration count it was made for
+    // the step from host buffers (made by the first soptx_step_host)
+    double *stage = nullptr;           // rho [nc], u [ndof], dc [nc], c [1] on the device
+    cudaStream_t side = nullptr;       // second stream: u's copy, the sensitivities, dc and c back
+    cudaEvent_t ev[2] = {};            // rho on the device (and all work before it), side stream done
 };
 
 struct Material {

@@ -266,3 +266,44 @@ def test_lattice_without_sectors_uses_general_sensitivity(P, cell, mk, prec):
     finally:
         N.lib().soptx_debug_lattice_no_sectors(0)
     assert m.path == "lattice"
+
+
+HOST_CASES = [c for c in CASES if c[0] in ("hex_q1_13x5x4_lattice", "q4_60x20_lattice", "tet_p2_5x3x2_jitter",
+                                           "hex_q1_relabelled_uniform")]
+
+
+@pytest.mark.parametrize("name,cell,k,coords,cells", HOST_CASES, ids=[c[0] for c in HOST_CASES])
+def test_step_host_matches_device_step(P, name, cell, k, coords, cells):
+    """soptx_step_host (host rho, u, dc, c; on a box lattice the sensitivities
+    on a second stream) gives the bits of the device-pointer step, call after
+    call with changing inputs, with dc and c in one buffer or two, c omitted,
+    and pageable host memory."""
+    import ctypes
+    from paper_2505_02438_gb300 import _native as N
+    m = P.Mesh(cell, k, coords, cells)
+    g = np.random.default_rng(21)
+    for it in range(3):
+        rho = g.uniform(0.001, 1.0, len(cells))
+        u = g.standard_normal(m.ndof)
+        v_ref, dc_ref, c_ref = m.step(to_dev(rho), to_dev(u))
+        torch.cuda.synchronize()
+        pin = it != 2
+        rho_h = torch.as_tensor(rho).pin_memory() if pin else torch.as_tensor(rho).clone()
+        u_h = torch.as_tensor(u).pin_memory() if pin else torch.as_tensor(u).clone()
+        vals, dc_h, c_h = m.step_host(rho_h, u_h)
+        torch.cuda.synchronize()
+        assert torch.equal(vals, v_ref)
+        assert torch.equal(dc_h, dc_ref.cpu()) and torch.equal(c_h, c_ref.cpu())
+    # dc and c in separate buffers, then without c
+    dc2 = torch.full((m.n_cells,), np.nan, dtype=torch.float64).pin_memory()
+    c2 = torch.full((1,), np.nan, dtype=torch.float64).pin_memory()
+    vals2 = torch.empty_like(v_ref)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for cptr in (ctypes.c_void_p(c2.data_ptr()), None):
+        N.check(N.lib().soptx_step_host(m._h, ctypes.c_void_p(rho_h.data_ptr()), ctypes.c_void_p(u_h.data_ptr()),
+                                        ctypes.c_void_p(vals2.data_ptr()), ctypes.c_void_p(dc2.data_ptr()), cptr, st))
+        torch.cuda.synchronize()
+        assert torch.equal(vals2, v_ref) and torch.equal(dc2, dc_ref.cpu()) and torch.equal(c2, c_ref.cpu())
+    with pytest.raises(N.SoptxError):
+        N.check(N.lib().soptx_step_host(m._h, None, ctypes.c_void_p(u_h.data_ptr()),
+                                        ctypes.c_void_p(vals2.data_ptr()), ctypes.c_void_p(dc2.data_ptr()), None, st))
