@@ -11,8 +11,8 @@ nonzeros), FP64, rho ~ U(0.001, 1), u ~ N(0, 1), seeded.
 Prints one JSON line.  N > 1 runs under torchrun, one rank per GPU, each rank
 solving its own copy of the design (independent problems: weak scaling, no
 collective on the data path).  --impl reference times the plain FP64 CPU
-oracle (the reference implementation of this build) on a bounded sample of the
-same workload.
+oracle (the reference implementation) on a bounded sample of the same
+workload.
 """
 import argparse
 import hashlib
@@ -540,6 +540,20 @@ def run_ours(args, rank, world, local_rank):
     sens_ms = sum(e[1].elapsed_time(e[2]) for e in sev)
     asm_ms, sens_ms = max_over_ranks([asm_ms, sens_ms], world, dev)
 
+    # the backward of f(rho, u) = u^T K(rho) u (soptx_compliance_vjp): grad_rho and grad_u = 2 g K(rho) u
+    gout = torch.ones(1, dtype=torch.float64, device=dev)
+    n_vjp = min(K, 200)
+    vev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(n_vjp)]
+    for _ in range(3):
+        mesh.compliance_vjp(rho, u, gout)
+    for k in range(n_vjp):
+        flush.zero_()
+        vev[k][0].record(stream)
+        mesh.compliance_vjp(rho, u, gout)
+        vev[k][1].record(stream)
+    torch.cuda.synchronize()
+    vjp_ms = max_over_ranks([sum(e[0].elapsed_time(e[1]) for e in vev)], world, dev)[0] / n_vjp
+
     # end to end through the host-buffer call (soptx_step_host): rho and u from pinned host
     # memory to the device, K(rho) on the device, dc and c back to one pinned host buffer
     n_e2e = min(K, 200)
@@ -590,6 +604,8 @@ def run_ours(args, rank, world, local_rank):
         "setup_s": setup_s,
         "separate_calls": {"assemble_ms": asm_ms / n_split, "sensitivity_ms": sens_ms / n_split,
                            "steps": n_split},
+        "backward": {"ms": vjp_ms, "calls": n_vjp,
+                     "what": "soptx_compliance_vjp: grad_rho = g E' u_e^T K_e u_e and grad_u = 2 g K(rho) u"},
         "step_alg_bytes": ab["step"], "step_hbm_frac": ab["step"] / (step_ms / K / 1e3) / 1e9 / peak,
         "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,

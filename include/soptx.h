@@ -192,6 +192,11 @@ soptx_status soptx_step_host(soptx_mesh mesh, const double *h_rho, const double 
  *   d_grad_rho[e] = g p rho_e^(p-1) (E0 - Emin) u_e^T K_e^0 u_e   (= -g dc_e)
  *   d_grad_u      = 2 g K(rho) u          (skipped when d_grad_u is NULL)
  * d_gout is a device float64 [1]; d_grad_rho [n_cells]; d_grad_u [ndof].
+ * The u-gradient is the product with K(rho) assembled into a mesh-owned
+ * scratch of 8 nnz bytes, made by the first call with d_grad_u (counted in
+ * soptx_mesh_device_bytes); if that memory cannot be allocated it is formed
+ * matrix-free from the element matrices instead (same result within the
+ * tolerance, about an order of magnitude slower).
  */
 soptx_status soptx_compliance_vjp(soptx_mesh mesh, const double *d_rho, const double *d_u,
                                   const double *d_gout, double *d_grad_rho, double *d_grad_u,

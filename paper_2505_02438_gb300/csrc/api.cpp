@@ -34,7 +34,8 @@ static void free_device(DeviceMesh &d)
 {
     void *ptrs[] = {d.indptr, d.indices, d.cell_node, d.node_off, d.inc_ptr, d.inc,
                     d.pos, d.geo, d.M, d.K, d.scratch, d.Edf, d.kappa, d.K0, d.sectors, d.udf, d.part,
-                    d.inc_e, d.inc_a, d.counter, d.xcell, d.qw, d.qdphi, d.qdgeo, d.cg, d.lat_bad, d.stage};
+                    d.inc_e, d.inc_a, d.counter, d.xcell, d.qw, d.qdphi, d.qdgeo, d.cg, d.lat_bad, d.stage,
+                    d.kvals};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (d.cg_exec) cudaGraphExecDestroy(d.cg_exec);
@@ -495,6 +496,21 @@ soptx_status soptx_compliance_vjp(soptx_mesh m, const double *d_rho, const doubl
     soptx_status s = cuda_status(launch_sensitivity(*m, d_rho, d_u, d_grad_rho, nullptr, 1.0, d_gout, st),
                                  "soptx_compliance_vjp");
     if (s != SOPTX_OK || !d_grad_u) return s;
+    // 2 g K(rho) u: through K(rho) assembled into the mesh's scratch and the product
+    // (the scratch, 8 nnz bytes, is made by the first such call); where that memory
+    // cannot be had, matrix-free from the element matrices (an order of magnitude slower)
+    auto &d = m->d;
+    if (!d.kvals && m->h.nnz > 0) {
+        void *p = nullptr;
+        if (dev_alloc(&p, (size_t)m->h.nnz * sizeof(double)) == cudaSuccess) {
+            d.kvals = (double *)p;
+            m->device_bytes += (int64_t)m->h.nnz * (int64_t)sizeof(double);
+        } else {
+            cudaGetLastError();
+        }
+    }
+    if (d.kvals)
+        return cuda_status(launch_Ku_assembled(*m, d_rho, d_u, d_gout, d_grad_u, d.kvals, st), "soptx_compliance_vjp");
     return cuda_status(launch_Ku(*m, d_rho, d_u, d_gout, d_grad_u, st), "soptx_compliance_vjp");
 }
 

@@ -120,6 +120,8 @@ struct DeviceMesh {
     cudaGraphExec_t cg_exec = nullptr; // the CG iterations between two checks, as a graph
     cudaStream_t cg_cap = nullptr;     // its capture stream
     const void *cg_key[4] = {};        // vals, fixed, u and the iteration count it was made for
+    // K(rho) for the backward's u-gradient (made by the first soptx_compliance_vjp with d_grad_u)
+    double *kvals = nullptr;
     // the step from host buffers (made by the first soptx_step_host)
     double *stage = nullptr;           // rho [nc], u [ndof], dc [nc], c [1] on the device
     cudaStream_t side = nullptr;       // second stream: u's copy, the sensitivities, dc and c back
@@ -154,6 +156,8 @@ cudaError_t launch_sensitivity(const soptx_mesh_s &m, const double *rho, const d
                                double *c, double scale, const double *gscale, cudaStream_t st);
 cudaError_t launch_Ku(const soptx_mesh_s &m, const double *rho, const double *u, const double *gout,
                       double *out, cudaStream_t st);
+cudaError_t launch_Ku_assembled(const soptx_mesh_s &m, const double *rho, const double *u, const double *gout,
+                                double *out, double *kvals, cudaStream_t st);
 int64_t sensitivity_scratch_len(const soptx_mesh_s &m);
 cudaError_t launch_lattice_assemble(const soptx_mesh_s &m, const double *rho, double *vals, cudaStream_t st);
 bool lattice_kappa_shift(int dim, const std::vector<double> &K0, int &shift);

@@ -66,3 +66,36 @@ def test_grad_only_rho(lib):
     dc, _ = m.sensitivity(rho.detach(), u)
     # rho-gradient of u^T K(rho) u is minus the compliance sensitivity, bit for bit on this path
     assert torch.allclose(rho.grad, -dc, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("mk", [lambda: W.cantilever_hex(6, 4, 3), lambda: W.jittered_tet(4, 3, 2, order=2)])
+def test_u_gradient_assembled_and_matrix_free(lib, mk):
+    """The u-gradient 2 g K(rho) u goes through K(rho) assembled into the mesh's
+    scratch; when that scratch cannot be allocated it is formed matrix-free.
+    Both match the oracle."""
+    import ctypes
+    from paper_2505_02438_gb300 import _native as N
+    wl = mk()
+    g = 1.75
+    gr_o, gu_o = oracle.compliance_vjp(wl.cell, wl.order, wl.coords, wl.cells, wl.mat, wl.rho,
+                                       wl.displacement(lib.Mesh.from_workload(wl).ndof), g)
+    rp, ci, va, _ = oracle.assemble(wl.cell, wl.order, wl.coords, wl.cells, wl.mat, wl.rho, absval=True)
+    for fail in (1, 0):
+        m = lib.Mesh.from_workload(wl)
+        u_np = wl.displacement(m.ndof)
+        scale = np.array([np.dot(va[rp[r]:rp[r + 1]], np.abs(u_np[ci[rp[r]:rp[r + 1]]])) for r in range(m.ndof)])
+        try:
+            N.lib().soptx_debug_fail_alloc_after(fail)
+            gr, gu = m.compliance_vjp(torch.as_tensor(wl.rho, device="cuda"), torch.as_tensor(u_np, device="cuda"),
+                                      torch.tensor([g], dtype=torch.float64, device="cuda"))
+        finally:
+            N.lib().soptx_debug_fail_alloc_after(0)
+        torch.cuda.synchronize()
+        nbytes = ctypes.c_int64(0)
+        N.check(N.lib().soptx_mesh_device_bytes(m._h, ctypes.byref(nbytes)))
+        assert nbytes.value == m.device_bytes + (0 if fail else 8 * m.nnz)   # the scratch only when it was had
+        assert np.all(np.abs(gu.cpu().numpy() - gu_o) <= TOL64 * 2 * g * scale)
+        dco, s, co, sabs = oracle.sensitivity(wl.cell, wl.order, wl.coords, wl.cells, wl.mat, wl.rho, u_np,
+                                              with_abs=True)
+        E0, Emin, nu, p, ps = wl.mat
+        assert np.all(np.abs(gr.cpu().numpy() - gr_o) <= TOL64 * g * p * wl.rho ** (p - 1) * (E0 - Emin) * sabs)
