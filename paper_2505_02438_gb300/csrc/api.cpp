@@ -492,15 +492,12 @@ soptx_status soptx_compliance_vjp(soptx_mesh m, const double *d_rho, const doubl
     if (!m) SOPTX_FAIL(SOPTX_EINVAL, "mesh is NULL");
     if (!d_gout) SOPTX_FAIL(SOPTX_EINVAL, "d_gout is NULL");
     if (m->h.nc > 0 && (!d_rho || !d_u || !d_grad_rho)) SOPTX_FAIL(SOPTX_EINVAL, "d_rho / d_u / d_grad_rho is NULL");
+    if (d_grad_u && m->h.ndof > 0 && !d_u) SOPTX_FAIL(SOPTX_EINVAL, "d_u is NULL");
     cudaStream_t st = (cudaStream_t)stream;
-    soptx_status s = cuda_status(launch_sensitivity(*m, d_rho, d_u, d_grad_rho, nullptr, 1.0, d_gout, st),
-                                 "soptx_compliance_vjp");
-    if (s != SOPTX_OK || !d_grad_u) return s;
-    // 2 g K(rho) u: through K(rho) assembled into the mesh's scratch and the product
-    // (the scratch, 8 nnz bytes, is made by the first such call); where that memory
-    // cannot be had, matrix-free from the element matrices (an order of magnitude slower)
     auto &d = m->d;
-    if (!d.kvals && m->h.nnz > 0) {
+    if (d_grad_u && !d.kvals && m->h.nnz > 0) {
+        // K(rho) for 2 g K(rho) u goes into a mesh-owned scratch of 8 nnz bytes, made once;
+        // where that memory cannot be had the product is formed matrix-free instead
         void *p = nullptr;
         if (dev_alloc(&p, (size_t)m->h.nnz * sizeof(double)) == cudaSuccess) {
             d.kvals = (double *)p;
@@ -509,8 +506,24 @@ soptx_status soptx_compliance_vjp(soptx_mesh m, const double *d_rho, const doubl
             cudaGetLastError();
         }
     }
-    if (d.kvals)
-        return cuda_status(launch_Ku_assembled(*m, d_rho, d_u, d_gout, d_grad_u, d.kvals, st), "soptx_compliance_vjp");
+    if (d_grad_u && m->h.nnz == 0) {
+        // no element couples any dof: K(rho) = 0
+        soptx_status s = cuda_status(launch_sensitivity(*m, d_rho, d_u, d_grad_rho, nullptr, 1.0, d_gout, st),
+                                     "soptx_compliance_vjp");
+        if (s != SOPTX_OK || m->h.ndof == 0) return s;
+        return cuda_status(cudaMemsetAsync(d_grad_u, 0, (size_t)m->h.ndof * sizeof(double), st),
+                           "soptx_compliance_vjp");
+    }
+    if (d_grad_u && d.kvals) {
+        // one step (K(rho) and the rho-gradient g E' s) then the product with u
+        soptx_status s = cuda_status(launch_step(*m, d_rho, d_u, d.kvals, d_grad_rho, nullptr, st, d_gout),
+                                     "soptx_compliance_vjp");
+        if (s != SOPTX_OK) return s;
+        return cuda_status(launch_scaled_product(*m, d.kvals, d_u, d_gout, d_grad_u, st), "soptx_compliance_vjp");
+    }
+    soptx_status s = cuda_status(launch_sensitivity(*m, d_rho, d_u, d_grad_rho, nullptr, 1.0, d_gout, st),
+                                 "soptx_compliance_vjp");
+    if (s != SOPTX_OK || !d_grad_u) return s;
     return cuda_status(launch_Ku(*m, d_rho, d_u, d_gout, d_grad_u, st), "soptx_compliance_vjp");
 }
 

@@ -156,8 +156,8 @@ cudaError_t launch_sensitivity(const soptx_mesh_s &m, const double *rho, const d
                                double *c, double scale, const double *gscale, cudaStream_t st);
 cudaError_t launch_Ku(const soptx_mesh_s &m, const double *rho, const double *u, const double *gout,
                       double *out, cudaStream_t st);
-cudaError_t launch_Ku_assembled(const soptx_mesh_s &m, const double *rho, const double *u, const double *gout,
-                                double *out, double *kvals, cudaStream_t st);
+cudaError_t launch_scaled_product(const soptx_mesh_s &m, const double *vals, const double *u, const double *gout,
+                                  double *out, cudaStream_t st);
 int64_t sensitivity_scratch_len(const soptx_mesh_s &m);
 cudaError_t launch_lattice_assemble(const soptx_mesh_s &m, const double *rho, double *vals, cudaStream_t st);
 bool lattice_kappa_shift(int dim, const std::vector<double> &K0, int &shift);
@@ -167,11 +167,11 @@ cudaError_t launch_lattice_sensitivity(const soptx_mesh_s &m, const double *rho,
                                        double *c, const double *gscale, cudaStream_t st);
 int lattice_sens_grid(int64_t nc);
 cudaError_t launch_lattice_step(const soptx_mesh_s &m, const double *rho, const double *u, double *vals, double *dc,
-                                double *c, cudaStream_t st);
+                                double *c, cudaStream_t st, const double *gscale = nullptr);
 cudaError_t launch_gather(const soptx_mesh_s &m, const double *rho, const double *u, double *vals, double *dc,
                           double *c, const double *gscale, cudaStream_t st);
 int gather_finalize_grid(int64_t nc);
 cudaError_t launch_step(const soptx_mesh_s &m, const double *rho, const double *u, double *vals, double *dc,
-                        double *c, cudaStream_t st);
+                        double *c, cudaStream_t st, const double *gscale = nullptr);
 __global__ void k_reduce_partials(int n, const double *__restrict__ partial, double *__restrict__ c);
 }  // namespace soptx

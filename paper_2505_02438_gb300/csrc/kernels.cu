@@ -280,16 +280,18 @@ cudaError_t launch_sensitivity(const soptx_mesh_s &m, const double *rho, const d
     return launch_gather(m, rho, u, nullptr, dc, c, gscale, st);
 }
 
+// gscale: dc = g E' s with g = *gscale (the backward), or the compliance sensitivity when NULL
 cudaError_t launch_step(const soptx_mesh_s &m, const double *rho, const double *u, double *vals, double *dc,
-                        double *c, cudaStream_t st)
+                        double *c, cudaStream_t st, const double *gscale)
 {
-    if (m.path == SOPTX_PATH_LATTICE && m.d.sectors && m.h.nc > 0) return launch_lattice_step(m, rho, u, vals, dc, c, st);
+    if (m.path == SOPTX_PATH_LATTICE && m.d.sectors && m.h.nc > 0)
+        return launch_lattice_step(m, rho, u, vals, dc, c, st, gscale);
     if (m.path == SOPTX_PATH_LATTICE || m.h.nc == 0) {
         cudaError_t err = launch_assemble(m, rho, vals, st);
         if (err != cudaSuccess) return err;
-        return launch_sensitivity(m, rho, u, dc, c, -1.0, nullptr, st);
+        return launch_sensitivity(m, rho, u, dc, c, -1.0, gscale, st);
     }
-    return launch_gather(m, rho, u, m.h.nnz > 0 ? vals : nullptr, dc, c, nullptr, st);
+    return launch_gather(m, rho, u, m.h.nnz > 0 ? vals : nullptr, dc, c, gscale, st);
 }
 
 int64_t sensitivity_scratch_len(const soptx_mesh_s &m) { return std::max(gather_finalize_grid(m.h.nc), 1); }

@@ -812,16 +812,16 @@ cudaError_t launch_lattice_assemble(const soptx_mesh_s &m, const double *rho, do
 // One call doing both passes: u is split into float pairs once, by the moduli
 // kernel, instead of at every corner of every cell.
 cudaError_t launch_lattice_step(const soptx_mesh_s &m, const double *rho, const double *u, double *vals, double *dc,
-                                double *c, cudaStream_t st)
+                                double *c, cudaStream_t st, const double *gscale)
 {
     if (!m.d.udf || !u) {
         cudaError_t err = lattice_assemble_u(m, rho, nullptr, vals, st);
         if (err != cudaSuccess) return err;
-        return launch_lattice_sensitivity(m, rho, u, dc, c, nullptr, st);
+        return launch_lattice_sensitivity(m, rho, u, dc, c, gscale, st);
     }
     cudaError_t err = lattice_assemble_u(m, rho, u, vals, st);
     if (err != cudaSuccess) return err;
-    return lattice_sens_t(m, rho, (const float2 *)m.d.udf, dc, c, nullptr, st, true);
+    return lattice_sens_t(m, rho, (const float2 *)m.d.udf, dc, c, gscale, st, true);
 }
 
 // kappa_delta[i][j] = K0[(a*, i), (b*, j)] for every offset delta (x fastest),

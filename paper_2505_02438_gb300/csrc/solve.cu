@@ -363,16 +363,13 @@ __global__ void k_scale_by_2g(int64_t n, const double *__restrict__ gout, double
 
 }  // namespace
 
-// The backward's u-gradient 2 g K(rho) u through the assembled values: K(rho)
-// into kvals (the mesh's scratch), the product, then the scale by 2 g.
-cudaError_t launch_Ku_assembled(const soptx_mesh_s &m, const double *rho, const double *u, const double *gout,
-                                double *out, double *kvals, cudaStream_t st)
+// out = 2 g K u from the assembled values (the backward's u-gradient)
+cudaError_t launch_scaled_product(const soptx_mesh_s &m, const double *vals, const double *u, const double *gout,
+                                  double *out, cudaStream_t st)
 {
     const auto &h = m.h;
     if (h.nn == 0) return cudaSuccess;
-    cudaError_t e = launch_assemble(m, rho, kvals, st);
-    if (e != cudaSuccess) return e;
-    e = launch_spmv(m, kvals, u, out, nullptr, nullptr, nullptr, nullptr, nullptr, st);
+    cudaError_t e = launch_spmv(m, vals, u, out, nullptr, nullptr, nullptr, nullptr, nullptr, st);
     if (e != cudaSuccess) return e;
     k_scale_by_2g<<<cg_grid_wide(h.ndof), kCgThreads, 0, st>>>(h.ndof, gout, out);
     return cudaGetLastError();

@@ -106,6 +106,9 @@ def test_empty_mesh(P):
     vals = m.assemble_K(rho)
     dc, c = m.sensitivity(rho, torch.zeros(6, dtype=torch.float64, device="cuda"))
     assert vals.numel() == 0 and dc.numel() == 0 and c.item() == 0.0
+    gr, gu = m.compliance_vjp(rho, torch.ones(6, dtype=torch.float64, device="cuda"),
+                              torch.ones(1, dtype=torch.float64, device="cuda"))
+    assert gr.numel() == 0 and torch.equal(gu.cpu(), torch.zeros(6, dtype=torch.float64))
 
 
 def test_invalid_arguments_raise(P):
