@@ -127,3 +127,39 @@ def test_wrong_dimension_and_order_rejected():
         host_plan("quad", 4, c, cl)
     with pytest.raises(N.SoptxError, match="dim"):
         host_plan("hex", 1, c, cl)
+
+
+def test_null_mesh_calls_return_einval(native):
+    """Every entry point that takes a mesh refuses NULL with SOPTX_EINVAL
+    before touching the device."""
+    L = native.lib()
+    EINVAL = 1
+    p = ctypes.c_void_p(0)
+    assert L.soptx_assemble_K(None, p, p, p) == EINVAL
+    assert L.soptx_sensitivity(None, p, p, p, p, p) == EINVAL
+    assert L.soptx_assemble_and_sensitivity(None, p, p, p, p, p, p) == EINVAL
+    assert L.soptx_step_host(None, p, p, p, p, p, p) == EINVAL
+    assert L.soptx_compliance_vjp(None, p, p, p, p, p, p) == EINVAL
+    assert b"NULL" in L.soptx_last_error()
+
+
+def test_traffic_records_are_keyed_on_kernel_workload_and_precision():
+    """bench.py reports ncu traffic only for the kernel, workload and element
+    precision it was captured on, and only while the kernel source is
+    unchanged."""
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    rec = os.path.join(ROOT, "profiles", "traffic.txt")
+    lines = [dict(x.split("=", 1) for x in ln.split() if "=" in x) for ln in open(rec) if ln.startswith("kernel=")]
+    assert lines
+    src = {"k_lattice_assemble3": "lattice.cu", "k_lattice_assemble2": "lattice.cu", "k_gather_rows": "gather.cu",
+           "k_spmv": "solve.cu"}
+    for kv in lines:
+        f = src[kv["kernel"]]
+        got = bench.traffic_record(f, kv["kernel"], kv["workload"], kv.get("prec", "fp64"))
+        if kv["source_sha"] == bench.kernel_source_sha(f):
+            assert got == float(kv["dram_bytes_per_launch"])
+        # never another workload's or precision's figure
+        assert bench.traffic_record(f, kv["kernel"], kv["workload"] + "_other", kv.get("prec", "fp64")) is None
+    assert bench.traffic_record("gather.cu", "k_gather_rows", "tet_p2_60x20x20", "fp16") is None
