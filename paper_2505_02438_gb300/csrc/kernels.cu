@@ -76,6 +76,8 @@ k_Ku(int64_t nn, int nb, const int32_t *__restrict__ inc_ptr, const int32_t *__r
     const int ldof = D * nb;
     const double f = 2.0 * (*gout);
     for (int64_t n = (int64_t)blockIdx.x * kWarps + warp; n < nn; n += (int64_t)gridDim.x * kWarps) {
+        // each lane sums E_e K_e[(a,i), c] u_c over its columns c of every incident
+        // cell (ascending), then one fixed-order warp sum per row
         double acc[D];
         for (int i = 0; i < D; i++) acc[i] = 0.0;
         for (int32_t q = inc_ptr[n]; q < inc_ptr[n + 1]; q++) {
@@ -83,16 +85,14 @@ k_Ku(int64_t nn, int nb, const int32_t *__restrict__ inc_ptr, const int32_t *__r
             const int64_t e = ea / nb;
             const int a = ea - (int)e * nb;
             const KT *Ke = K + e * kstride;
-            double part[D];
-            for (int i = 0; i < D; i++) part[i] = 0.0;
+            const double E = simp_E(sp, rho[e]);
             for (int c = lane; c < ldof; c += 32) {
                 const int b = c / D, j = c % D;
-                const double uc = u[(int64_t)D * cell_node[e * nb + b] + j];
-                for (int i = 0; i < D; i++) part[i] += KLoad<KT>::get64(Ke + (D * a + i) * ldof + c) * uc;
+                const double Eu = E * u[(int64_t)D * cell_node[e * nb + b] + j];
+                for (int i = 0; i < D; i++) acc[i] = fma(KLoad<KT>::get64(Ke + (D * a + i) * ldof + c), Eu, acc[i]);
             }
-            const double E = simp_E(sp, rho[e]);
-            for (int i = 0; i < D; i++) acc[i] += E * warp_sum(part[i]);
         }
+        for (int i = 0; i < D; i++) acc[i] = warp_sum(acc[i]);
         if (lane < D) {
             double v = acc[0];
             for (int i = 1; i < D; i++)
