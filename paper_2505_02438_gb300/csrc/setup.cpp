@@ -66,11 +66,17 @@ struct EntityTable {
     int64_t size() const { return (int64_t)rest.size(); }
 };
 
+// The vertex ids of an edge or face (n <= 4) in ascending order, padded with -1.
 std::array<int32_t, 4> sorted_key(const int32_t *v, int n)
 {
     std::array<int32_t, 4> k{-1, -1, -1, -1};
-    for (int i = 0; i < n; i++) k[i] = v[i];
-    std::sort(k.begin(), k.begin() + n);
+    n = std::min(n, 4);
+    for (int i = 0; i < n; i++) {
+        int32_t x = v[i];
+        int j = i;
+        for (; j > 0 && k[j - 1] > x; j--) k[j] = k[j - 1];
+        k[j] = x;
+    }
     return k;
 }
 
