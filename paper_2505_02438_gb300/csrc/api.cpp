@@ -46,6 +46,27 @@ static void free_device(DeviceMesh &d)
     d = DeviceMesh{};
 }
 
+// The mesh's second stream and its two events, made once (the host-buffer step and
+// the 2D lattice step use them).
+static cudaError_t ensure_side(soptx_mesh_s &m)
+{
+    auto &d = m.d;
+    if (d.side) return cudaSuccess;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev[2] = {};
+    cudaError_t e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; i++) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        for (cudaEvent_t x : ev)
+            if (x) cudaEventDestroy(x);
+        if (side) cudaStreamDestroy(side);
+        return e;
+    }
+    d.side = side;
+    for (int i = 0; i < 2; i++) d.ev[i] = ev[i];
+    return cudaSuccess;
+}
+
 static soptx_status cuda_status(cudaError_t e, const char *what)
 {
     if (e == cudaSuccess) return SOPTX_OK;
@@ -410,6 +431,10 @@ soptx_status soptx_assemble_and_sensitivity(soptx_mesh m, const double *d_rho, c
     if (!m) SOPTX_FAIL(SOPTX_EINVAL, "mesh is NULL");
     if ((!d_vals && m->h.nnz > 0) || (m->h.nc > 0 && (!d_rho || !d_u || !d_dc)))
         SOPTX_FAIL(SOPTX_EINVAL, "d_rho / d_u / d_vals / d_dc is NULL");
+    if (m->path == SOPTX_PATH_LATTICE && m->h.dim == 2 && m->d.sectors && m->h.nc > 0) {
+        cudaError_t e = ensure_side(*m);
+        if (e != cudaSuccess) return cuda_status(e, "soptx_assemble_and_sensitivity stream");
+    }
     return cuda_status(launch_step(*m, d_rho, d_u, d_vals, d_dc, d_c, (cudaStream_t)stream),
                        "soptx_assemble_and_sensitivity");
 }
@@ -431,22 +456,11 @@ soptx_status soptx_step_host(soptx_mesh m, const double *h_rho, const double *h_
             cudaGetLastError();
             return cuda_status(e, "soptx_step_host staging");
         }
-        cudaStream_t side = nullptr;
-        cudaEvent_t ev[2] = {};
-        e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
-        for (int i = 0; i < 2 && e == cudaSuccess; i++) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
-        if (e != cudaSuccess) {
-            for (cudaEvent_t x : ev)
-                if (x) cudaEventDestroy(x);
-            if (side) cudaStreamDestroy(side);
-            cudaFree(p);
-            return cuda_status(e, "soptx_step_host stream");
-        }
         d.stage = (double *)p;
-        d.side = side;
-        for (int i = 0; i < 2; i++) d.ev[i] = ev[i];
         m->device_bytes += (int64_t)bytes;
     }
+    e = ensure_side(*m);
+    if (e != cudaSuccess) return cuda_status(e, "soptx_step_host stream");
     cudaStream_t st = (cudaStream_t)stream;
     double *rho_d = d.stage, *u_d = rho_d + h.nc, *dc_d = u_d + h.ndof, *c_d = dc_d + h.nc;
     const size_t rb = (size_t)h.nc * sizeof(double), ub = (size_t)h.ndof * sizeof(double);

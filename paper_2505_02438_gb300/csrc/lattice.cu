@@ -757,7 +757,7 @@ bool build_lattice_sectors(int dim, const std::vector<double> &K0, double zero_t
 // The assembly; with u given (and m.d.udf), the moduli kernel also leaves u
 // as float pairs in m.d.udf for the sensitivity of the same step.
 static cudaError_t lattice_assemble_u(const soptx_mesh_s &m, const double *rho, const double *u, double *vals,
-                                      cudaStream_t st)
+                                      cudaStream_t st, cudaEvent_t moduli_done = nullptr)
 {
     const auto &h = m.h;
     const SimpParams sp = simp_params(m.mat);
@@ -773,6 +773,10 @@ static cudaError_t lattice_assemble_u(const soptx_mesh_s &m, const double *rho, 
                                                  m.d.udf ? u : nullptr, m.d.udf);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
+    if (moduli_done) {
+        err = cudaEventRecord(moduli_done, st);
+        if (err != cudaSuccess) return err;
+    }
     constexpr int WPB = 8;
     if (h.dim == 3) {
         const int64_t chunks = (h.nn + kChunk - 1) / kChunk;
@@ -818,6 +822,20 @@ cudaError_t launch_lattice_step(const soptx_mesh_s &m, const double *rho, const 
         cudaError_t err = lattice_assemble_u(m, rho, nullptr, vals, st);
         if (err != cudaSuccess) return err;
         return launch_lattice_sensitivity(m, rho, u, dc, c, gscale, st);
+    }
+    if (m.h.dim == 2 && m.d.side) {
+        // 2D: the sensitivity runs on the mesh's second stream beside the assembly
+        // (it needs the moduli kernel's u pairs, not K); the assembly's grid is
+        // not one full wave, so the two share the SMs
+        cudaError_t err = lattice_assemble_u(m, rho, u, vals, st, m.d.ev[0]);
+        if (err != cudaSuccess) return err;
+        err = cudaStreamWaitEvent(m.d.side, m.d.ev[0], 0);
+        if (err != cudaSuccess) return err;
+        err = lattice_sens_t(m, rho, (const float2 *)m.d.udf, dc, c, gscale, m.d.side);
+        if (err != cudaSuccess) return err;
+        err = cudaEventRecord(m.d.ev[1], m.d.side);
+        if (err != cudaSuccess) return err;
+        return cudaStreamWaitEvent(st, m.d.ev[1], 0);
     }
     cudaError_t err = lattice_assemble_u(m, rho, u, vals, st);
     if (err != cudaSuccess) return err;
