@@ -159,7 +159,10 @@ soptx_status soptx_sensitivity(soptx_mesh mesh, const double *d_rho, const doubl
                                double *d_dc, double *d_c, void *stream);
 
 /* One pass that produces both K(rho) and the sensitivities (the per-iteration
- * step); same arguments and results as the two calls above. */
+ * step); same arguments and results as the two calls above.  On a 2D box
+ * lattice the sensitivities run on a second, mesh-owned stream beside the
+ * assembly (made by the first such call, with two events); everything is
+ * ordered on `stream` when the call returns. */
 soptx_status soptx_assemble_and_sensitivity(soptx_mesh mesh, const double *d_rho,
                                             const double *d_u, double *d_vals,
                                             double *d_dc, double *d_c, void *stream);
