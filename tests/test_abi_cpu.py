@@ -163,3 +163,27 @@ def test_traffic_records_are_keyed_on_kernel_workload_and_precision():
         # never another workload's or precision's figure
         assert bench.traffic_record(f, kv["kernel"], kv["workload"] + "_other", kv.get("prec", "fp64")) is None
     assert bench.traffic_record("gather.cu", "k_gather_rows", "tet_p2_60x20x20", "fp16") is None
+
+
+@pytest.mark.parametrize("mk,cell,k,nc,ndof,nnz", [
+    (lambda: W.mbb_q4(60, 20), "quad", 1, 1200, 2562, 44164),
+    (lambda: W.cantilever_hex(120, 40, 40), "hex", 1, 192000, 610203, 47568609),
+    (lambda: W.jittered_tri(400, 200), "tri", 3, 160000, 1443602, 48996004),
+    (lambda: W.jittered_tet(60, 20, 20), "tet", 2, 144000, 610203, 50846409),
+    (lambda: W.mbb_q4(800, 400), "quad", 1, 320000, 642402, 11534404),
+    (lambda: W.cantilever_hex(30, 10, 10), "hex", 1, 3000, 11253, 787059),
+], ids=["q4_60x20", "hex_120x40x40", "tri_p3_400x200", "tet_p2_60x20x20", "q4_800x400", "hex_30x10x10"])
+def test_standard_workload_sizes(native, mk, cell, k, nc, ndof, nnz):
+    """The synthetic workloads have the cell, dof and nonzero counts of the
+    specified configurations (host-side plan, sizes only)."""
+    wl = mk()
+    assert wl.cell == cell and wl.order == k and len(wl.cells) == nc
+    coords = np.ascontiguousarray(wl.coords, np.float64)
+    cells = np.ascontiguousarray(wl.cells, np.int32)
+    nd, nz, nb, path = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+    native.check(native.lib().soptx_host_plan(coords.shape[1], native.CELL[cell], k, coords.shape[0],
+                                              coords.ctypes.data_as(ctypes.c_void_p), cells.shape[0],
+                                              cells.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nd),
+                                              ctypes.byref(nz), ctypes.byref(nb), ctypes.byref(path), None, None,
+                                              None))
+    assert (nd.value, nz.value) == (ndof, nnz)
