@@ -32,9 +32,12 @@
  *    Vertex order inside a cell: simplices list the vertex at the reference
  *    origin first, then the vertices at the unit vectors e_1..e_d (either
  *    orientation is accepted; |det J| is used); quads and hexes list their
- *    corners lexicographically on the unit square / cube, x fastest, and must
- *    be parallelograms / parallelepipeds (affine), so that reference integrals
- *    are exact.
+ *    corners lexicographically on the unit square / cube, x fastest.  Quads
+ *    and hexes may be general bilinear / trilinear cells: parallelograms and
+ *    parallelepipeds take the exact reference-integral contraction, any other
+ *    cell the (order+1)^d-point Gauss rule with the Jacobian of the geometry
+ *    map at every point (computed once, at mesh creation).  A cell whose
+ *    Jacobian changes sign or vanishes at a corner is rejected.
  *  - Lagrange order 1..3.  Higher-order nodes are numbered after the vertices:
  *    edge nodes (edges sorted by (min vertex id, max vertex id), the order-1
  *    nodes of an edge running from the min-id vertex to the max-id vertex),
@@ -103,8 +106,8 @@ typedef enum {
  *   stream           : stream for the setup copies and kernels
  *   out              : receives the mesh handle
  * Allocates device memory (reported by soptx_mesh_device_bytes) and
- * synchronises `stream`.  Errors: EINVAL (bad sizes, ids, degenerate or
- * non-affine cell, ndof >= 2^31), ENOMEM, ECUDA.  n_cells = 0 is allowed.
+ * synchronises `stream`.  Errors: EINVAL (bad sizes, ids, a degenerate or
+ * inverted cell, ndof >= 2^31), ENOMEM, ECUDA.  n_cells = 0 is allowed.
  */
 soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order,
                                int64_t n_vertices, const double *coords,
@@ -142,8 +145,14 @@ soptx_status soptx_mesh_device_bytes(soptx_mesh mesh, int64_t *bytes);
  *   d_rho  : device float64 [n_cells], element densities (any real values;
  *            the SIMP power is evaluated as given)
  *   d_vals : device float64 [nnz], overwritten with the CSR values
- * Each value is the sum of its element contributions in ascending element
- * order, without atomics: the result is bitwise reproducible run to run.
+ * No atomics: every value is formed in a fixed order, so the result is
+ * bitwise reproducible run to run, and it is within 1e-12 of the sum of the
+ * absolute element contributions of the exact value (FP64 element matrices).
+ * The order depends on the path: on a general mesh each value is the sum of
+ * its element contributions in ascending element order (float-pair
+ * accumulation); on a box lattice it is the reference block entry times a
+ * signed sum of the (at most 2^d) moduli of the cells the two nodes share,
+ * formed by per-axis sums and differences.
  */
 soptx_status soptx_assemble_K(soptx_mesh mesh, const double *d_rho, double *d_vals, void *stream);
 
@@ -226,8 +235,10 @@ soptx_status soptx_compliance_vjp(soptx_mesh mesh, const double *d_rho, const do
  * process exits; hence the limit: n_cells <= 8,388,608, larger lattices return
  * SOPTX_EINVAL.  The first call on a device looks up that array's device
  * address (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture.  All calls share the array, so calls that overlap
- * on the device race on it; every call overwrites the slots it uses.
+ * before any stream capture.  The address is kept for the life of the process:
+ * do not call this entry point on a device after a cudaDeviceReset of that
+ * device.  All calls share the array, so calls that overlap on the device race
+ * on it; every call overwrites the slots it uses.
  */
 soptx_status soptx_lattice_sensitivity_noalloc(int dim, const int32_t *cells_per_axis,
                                                const double *cell_size, const soptx_material *mat,

@@ -103,6 +103,16 @@ template <int D> struct SectorTable {
     float2 b[(1 << D) * D * D];
 };
 
+// Entries of the sector blocks that vanish on every box: a row or column
+// whose Walsh mode is the rigid translation (c xor e_i = 0), and the coupling
+// of components i != j whose axes lie on different sides of the sector
+// (bit i of c != bit j of c), which the box's reflection symmetry cancels.
+// The kernels skip them; the host stores them as exact zeros.
+__host__ __device__ constexpr bool sector_zero(int c, int i, int j)
+{
+    return (c ^ (1 << i)) == 0 || (c ^ (1 << j)) == 0 || (i != j && ((c >> i) & 1) != ((c >> j) & 1));
+}
+
 // Sum of `mine` over the grid into *c, deterministically: each block writes its
 // partial (a fixed-order butterfly per warp, then the warps in order), the last block to finish (an
 // atomic ticket on *counter) adds all partials in index order and resets the

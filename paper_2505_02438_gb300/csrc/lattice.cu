@@ -564,16 +564,6 @@ k_lattice_assemble2(int nx, int ny, int64_t nn, int chunk, const int64_t *__rest
     }
 }
 
-// Entries of the sector blocks that vanish on every box: a row or column
-// whose Walsh mode is the rigid translation (c xor e_i = 0), and the coupling
-// of components i != j whose axes lie on different sides of the sector
-// (bit i of c != bit j of c), which the box's reflection symmetry cancels.
-// The host checks them (build_lattice_sectors) before this path is taken.
-__host__ __device__ constexpr bool sector_zero(int c, int i, int j)
-{
-    return (c ^ (1 << i)) == 0 || (c ^ (1 << j)) == 0 || (i != j && ((c >> i) & 1) != ((c >> j) & 1));
-}
-
 // Sensitivity on the box lattice.  The reflections of a box across its
 // mid-planes commute with K^0, so in the Walsh basis of each displacement
 // component, f_t(a) = (-1)^(t.a) over the 2^d corners a, K^0 splits into 2^d

@@ -13,6 +13,9 @@
 // In host code the array's name is only a host-side handle: its device address
 // is looked up with cudaGetSymbolAddress once per device (on the first call
 // made on that device, with that device current) and passed to the kernel.
+// The address is kept for the life of the process, so this entry point must
+// not be called on a device after a cudaDeviceReset of that device (the reset
+// unloads the module and the kept address no longer points at the array).
 // Because all calls share the one array, calls that overlap on the device
 // race on it; each block overwrites its own slot, so nothing needs clearing.
 #include <cmath>
@@ -87,6 +90,7 @@ k_lattice_sens_noalloc(int nx, int ny, int nz, int64_t nc, const double *__restr
             for (int i = 0; i < D; i++)
 #pragma unroll
                 for (int j = i; j < D; j++) {
+                    if (sector_zero(c, i, j)) continue;
                     const float2 bb = B.b[(c * D + i) * D + j];
                     const df t = df_mul_raw(df_mul_raw(x[i], x[j]), df{bb.x, bb.y});
                     float err;
@@ -148,7 +152,9 @@ void box_element_matrix(const double *h, double lam, double mu, double *K)
         }
 }
 
-// Sector blocks B_c[i][j] = f_{c^e_i}^T K_ij f_{c^e_j} / 4^d (off-diagonal doubled).
+// Sector blocks B_c[i][j] = f_{c^e_i}^T K_ij f_{c^e_j} / 4^d (off-diagonal
+// doubled); the entries that vanish on every box (sector_zero) are stored as
+// exact zeros, as for a mesh on the lattice path.
 template <int D>
 void box_sectors(const double *K, SectorTable<D> &B)
 {
@@ -161,7 +167,7 @@ void box_sectors(const double *K, SectorTable<D> &B)
                 double s = 0.0;
                 for (int a = 0; a < NCR; a++)
                     for (int b = 0; b < NCR; b++) s += f(t, a) * K[(D * a + i) * LD + D * b + j] * f(t2, b);
-                const double x = (i == j ? 1.0 : 2.0) * s / ((double)NCR * NCR);
+                const double x = sector_zero(c, i, j) ? 0.0 : (i == j ? 1.0 : 2.0) * s / ((double)NCR * NCR);
                 const float hh = (float)x;
                 B.b[(c * D + i) * D + j] = make_float2(hh, (float)(x - (double)hh));
             }
@@ -203,11 +209,16 @@ soptx_status run_noalloc(const int32_t *n, const double *h, const soptx_material
     box_element_matrix<D>(h, lam, mu, K);
     SectorTable<D> B;
     box_sectors<D>(K, B);
-    SimpParams sp;
-    sp.Emin = mat->Emin;
-    sp.dE = mat->E0 - mat->Emin;
-    sp.p = mat->p;
-    sp.p_int = (mat->p == std::floor(mat->p) && mat->p <= 16.0) ? (int)mat->p : 0;
+    Material m{};
+    m.E0 = mat->E0;
+    m.Emin = mat->Emin;
+    m.nu = mat->nu;
+    m.p = mat->p;
+    m.dE = mat->E0 - mat->Emin;
+    m.lam = lam;
+    m.mu = mu;
+    m.p_int = (mat->p == std::floor(mat->p) && mat->p <= 16.0) ? (int)mat->p : 0;
+    const SimpParams sp = simp_params(m);
     const int grid = (int)((nc + kNaCellsPerBlock - 1) / kNaCellsPerBlock);
     k_lattice_sens_noalloc<D><<<grid, kNaThreads, 0, st>>>(n[0], n[1], D == 3 ? n[2] : 1, nc, rho, u, sp, B, dc,
                                                            partials);
