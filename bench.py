@@ -86,7 +86,14 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.QUERY,
                                           "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
-            time.sleep(0.3)
+            # the timed region starts only once nvidia-smi has initialised and
+            # written its first sample (its start-up would otherwise overlap it)
+            t0 = time.time()
+            while time.time() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.05)
+                if os.path.getsize(self.path) > 0:
+                    break
+            time.sleep(0.15)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self

@@ -39,6 +39,13 @@ __device__ __forceinline__ df shfl_df(df v, int src)
     return df{__shfl_sync(kFull, v.h, src), __shfl_sync(kFull, v.l, src)};
 }
 
+// x with its sign bit flipped when bit 31 of `mask` is set (an integer XOR on
+// the high word, no FP64 instruction).
+__device__ __forceinline__ double flip_sign(double x, uint32_t mask)
+{
+    return __hiloint2double(__double2hiint(x) ^ (int)mask, __double2loint(x));
+}
+
 // Bulk shared -> global copies by the copy engine (cp.async.bulk, no tensor
 // map): both addresses 16-byte aligned, size a multiple of 16.  A warp
 // stages a node's rows in shared memory and one lane hands them to the copy
@@ -124,12 +131,17 @@ __device__ __noinline__ void lattice_node_fp64(int nx, int ny, int nz, int ix, i
 // is decoded once per chunk and then stepped; the next node's moduli are
 // fetched before the current node is processed.
 constexpr int kChunk = 16;
-// Sign classes (0 = i == j, 1 = {0,1}, 2 = {0,2}, 3 = {1,2}) whose entries are
-// formed by one FP64 multiply each; 2 puts 5 of the 9 entries on the FP64 pipe.
-#ifndef SOPTX_LATTICE_FP64_CLASSES
-#define SOPTX_LATTICE_FP64_CLASSES 2
-#endif
-constexpr int kFp64Classes = SOPTX_LATTICE_FP64_CLASSES < 1 ? 1 : SOPTX_LATTICE_FP64_CLASSES;
+// Sign classes of a lane's 3 x 3 block: 0 = i == j, 1 = {0,1}, 2 = {0,2},
+// 3 = {1,2}.  On a box the two entries of an off-diagonal class are equal or
+// opposite: with the Q1 gradients of an axis-aligned box,
+//     K[(a,i),(b,j)] = (lam s_ai s_bj + mu s_aj s_bi) f,
+//     K[(a,j),(b,i)] = (lam s_aj s_bi + mu s_ai s_bj) f
+// (s the signs of the corners along each axis, f the common integral), so
+// kappa_delta[j][i] = +-kappa_delta[i][j] and both entries of a class share
+// one product (the host checks this before the lattice path is taken).  The
+// diagonal class and class {0,1} take one FP64 multiply per product on the
+// otherwise idle FP64 pipe (4 of a lane's 6 products), classes {0,2} and
+// {1,2} multiply in float pairs and convert each product.
 
 // Row layout of node idx in the CSR values: whether the lane's offset delta is
 // a neighbour (valid), its position mi among the node's neighbours and the
@@ -294,9 +306,11 @@ k_simp_df(int dim, int nx, int ny, int nz, int64_t nc, const double *__restrict_
 // 3D assembly, two nodes at a time (n, n+1 of a chunk): one corner load, one X
 // stage and one hand-off to the copy engine serve both (their rows are
 // contiguous in the CSR values); the Y and Z stages and the entries run once
-// per node.  Each lane forms its 9 entries: the classes below kFp64Classes
-// convert T once and take one FP64 multiply per entry on the otherwise idle
-// FP64 pipe, the others multiply in float pairs and convert each entry.  One
+// per node.  Each lane forms its 9 entries from 6 products (see the sign
+// classes above): the diagonal class and class {0,1} convert T once and take
+// one FP64 multiply per product, the other two multiply in float pairs and
+// convert; the second entry of each off-diagonal class is the first with its
+// sign bit flipped when the pair is opposite.  One
 // staging buffer per warp holds both nodes' rows, each value at the 16-byte
 // phase of its destination; before it is refilled the warp waits until the
 // copy engine has read the previous pair (one node at a time with two
@@ -326,6 +340,17 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, int chunk, const int64_t
         kapd_s[t] = ((double)kappa_g[t].x + (double)kappa_g[t].y) * kscale;
     }
     __syncthreads();
+    // the sign of entry (j, i) relative to (i, j) for the classes {0,1}, {0,2}, {1,2}
+    // (bit 31 of the high word of the FP64 value)
+    uint32_t sflip[3];
+    {
+        const int ij[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            const float a = kap_s[dl * 9 + ij[q][0] * 3 + ij[q][1]].x, b = kap_s[dl * 9 + ij[q][1] * 3 + ij[q][0]].x;
+            sflip[q] = (__float_as_uint(a) ^ __float_as_uint(b)) & 0x80000000u;
+        }
+    }
     grid_dep_wait();
     grid_dep_launch();
     const int ox = lane & 3, oy = (lane >> 2) & 3;
@@ -407,24 +432,24 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, int chunk, const int64_t
                         const float2 t = tab[k][tq[q]];
                         T[q] = df{t.x, t.y};
                     }
-                    double Td[kFp64Classes];
-#pragma unroll
-                    for (int q = 0; q < kFp64Classes; q++) Td[q] = df_to_double_biased(T[q].h, T[q].l, 0x38000000u);
-#pragma unroll
-                    for (int i = 0; i < 3; i++) {
-                        double *row = st + i * rowlen + 3 * mi;
-#pragma unroll
-                        for (int j = 0; j < 3; j++) {
-                            const int q = (i == j) ? 0 : (i + j == 1 ? 1 : (i + j == 2 ? 2 : 3));
-                            if (q < kFp64Classes) {
-                                row[j] = kapd_s[dl * 9 + i * 3 + j] * Td[q < kFp64Classes ? q : 0];
-                            } else {
-                                const float2 kv = kap_s[dl * 9 + i * 3 + j];
-                                const df v = df_mul_raw(df{kv.x, kv.y}, T[q]);
-                                row[j] = df_to_double_biased(v.h, v.l, pbias);
-                            }
-                        }
-                    }
+                    const double T0 = df_to_double_biased(T[0].h, T[0].l, 0x38000000u);
+                    const double T1 = df_to_double_biased(T[1].h, T[1].l, 0x38000000u);
+                    double *r0 = st + 3 * mi, *r1 = r0 + rowlen, *r2 = r1 + rowlen;
+                    const double *kd = kapd_s + dl * 9;
+                    r0[0] = kd[0] * T0;
+                    r1[1] = kd[4] * T0;
+                    r2[2] = kd[8] * T0;
+                    const double v01 = kd[1] * T1;
+                    r0[1] = v01;
+                    r1[0] = flip_sign(v01, sflip[0]);
+                    const float2 k02 = kap_s[dl * 9 + 2], k12 = kap_s[dl * 9 + 5];
+                    const df p02 = df_mul_raw(df{k02.x, k02.y}, T[2]), p12 = df_mul_raw(df{k12.x, k12.y}, T[3]);
+                    const double v02 = df_to_double_biased(p02.h, p02.l, pbias);
+                    const double v12 = df_to_double_biased(p12.h, p12.l, pbias);
+                    r0[2] = v02;
+                    r2[0] = flip_sign(v02, sflip[1]);
+                    r1[2] = v12;
+                    r2[1] = flip_sign(v12, sflip[2]);
                 }
             }
             fence_proxy_async_smem();
@@ -486,8 +511,11 @@ k_lattice_assemble2(int nx, int ny, int64_t nn, int chunk, const int64_t *__rest
     const int cl = lane < 27 ? lane - 9 * g : 8;
     const int dl = cl;
     const int dx = dl % 3 - 1, dy = dl / 3 - 1;
-    // the lane's kappa: diagonal entries in FP64, the others as (scaled) float pairs
-    const float2 k01 = kappa_g[dl * 4 + 1], k10 = kappa_g[dl * 4 + 2];
+    // the lane's kappa: diagonal entries in FP64, the off-diagonal pair as one
+    // (scaled) float pair: kappa[1][0] = +-kappa[0][1] on a box (see the sign
+    // classes of the 3D kernel), so one product serves both entries
+    const float2 k01 = kappa_g[dl * 4 + 1];
+    const uint32_t sflip = (__float_as_uint(k01.x) ^ __float_as_uint(kappa_g[dl * 4 + 2].x)) & 0x80000000u;
     const double k00 = ((double)kappa_g[dl * 4].x + (double)kappa_g[dl * 4].y) * kscale;
     const double k11 = ((double)kappa_g[dl * 4 + 3].x + (double)kappa_g[dl * 4 + 3].y) * kscale;
     // axis options: the low cell (L), the high one (H), or both: H + L on the
@@ -544,9 +572,10 @@ k_lattice_assemble2(int nx, int ny, int64_t nn, int chunk, const int64_t *__rest
                 double *r0 = stage + sbase + 2 * mi, *r1 = r0 + rowlen;
                 r0[0] = k00 * tdd;
                 r1[1] = k11 * tdd;
-                const df v01 = df_mul_raw(df{k01.x, k01.y}, Tp), v10 = df_mul_raw(df{k10.x, k10.y}, Tp);
-                r0[1] = df_to_double_biased(v01.h, v01.l, pbias);
-                r1[0] = df_to_double_biased(v10.h, v10.l, pbias);
+                const df v01 = df_mul_raw(df{k01.x, k01.y}, Tp);
+                const double o01 = df_to_double_biased(v01.h, v01.l, pbias);
+                r0[1] = o01;
+                r1[0] = flip_sign(o01, sflip);
             }
             __syncwarp();
             if (!badm) {
@@ -869,6 +898,20 @@ bool lattice_kappa_shift(int dim, const std::vector<double> &K0, int &shift)
     for (double x : kap)
         if (std::fabs(x) > std::ldexp(kmax, -40)) kmin = std::min(kmin, std::fabs(x));
     if (!(kmax > 0.0) || !std::isfinite(kmax) || !(kmin >= std::ldexp(kmax, -24))) return false;
+    // the kernels form entry (j, i) of each block as +-entry (i, j): the pairs
+    // must agree to the rounding of K^0 (a few ulps), with the sign the kernels
+    // read off the two stored entries
+    const int nd = dim == 3 ? 27 : 9;
+    for (int dl = 0; dl < nd; dl++)
+        for (int i = 0; i < dim; i++)
+            for (int j = i + 1; j < dim; j++) {
+                const double a = kap[(size_t)dl * dim * dim + i * dim + j], b = kap[(size_t)dl * dim * dim + j * dim + i];
+                // (entries that vanish in exact arithmetic may carry rounding noise of
+                // either sign: the absolute term covers them)
+                const double tol = 1e-14 * std::max(std::fabs(a), std::fabs(b)) + 1e-15 * kmax;
+                const bool same = std::signbit(a) == std::signbit(b);
+                if (!(std::fabs(same ? a - b : a + b) <= tol)) return false;
+            }
     shift = std::ilogb(kmax);
     return shift > -900 && shift < 900;
 }
