@@ -417,10 +417,14 @@ static int elem_matrix(const elem_ctx *c, const double *xv, double *Ke)
     memset(Ke, 0, sizeof(double) * ldof * ldof);
     double B[6][OR_MAXLDOF], DB[6][OR_MAXLDOF];
     for (int q = 0; q < c->nq; q++) {
+        /* J = sum_v x_v (grad N_v)^T, formed from the edge vectors x_v - x_0:
+         * the vertex basis sums to one, so its gradients sum to zero and J is
+         * the same; with vertex 0 as origin its rounding is relative to the
+         * cell's size instead of the cell's distance from the origin. */
         double J[3][3] = { { 0 } }, G[3][3];
-        for (int v = 0; v < c->nv; v++)
+        for (int v = 1; v < c->nv; v++)
             for (int i = 0; i < d; i++)
-                for (int m = 0; m < d; m++) J[i][m] += xv[v * d + i] * c->dgeo[q][v][m];
+                for (int m = 0; m < d; m++) J[i][m] += (xv[v * d + i] - xv[i]) * c->dgeo[q][v][m];
         double det = inv_det(d, J, G);
         if (!(fabs(det) > 0.0) || !isfinite(det)) return -1;
         /* physical gradients: dphi/dx_i = sum_m G[m][i] dphi/dxi_m */

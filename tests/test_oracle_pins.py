@@ -268,6 +268,25 @@ def test_element_matrix_scaling_and_rotation(cell, k):
     np.testing.assert_allclose(Kr, Rb @ K @ Rb.T, atol=1e-12 * np.abs(K).max())
 
 
+@pytest.mark.parametrize("cell,k", [("quad", 1), ("hex", 1), ("tri", 3), ("tet", 2), ("quad", 2), ("hex", 2)])
+def test_element_matrix_translation_invariance(cell, k):
+    """K_e^0 depends on a cell's shape, not on where it sits: a cell moved far
+    from the origin (here by about 1e3 to 2e4 edge lengths, as on the largest
+    meshes) has the matrix of the same cell at the origin, to a few rounding
+    errors of its entries, including entries that cancel (the Q4 coupling
+    (nu - (1 - nu) / 2) / (4 (1 - nu^2)))."""
+    rng = np.random.default_rng(9)
+    d = W.DIM[cell]
+    # vertices on a dyadic grid and integer shifts: the moved cell is exactly the same shape
+    xv = np.round(affine_cell(cell, rng) * 2.0 ** 20) / 2.0 ** 20
+    K = oracle.element_matrix(cell, k, xv, 0.3)
+    for shift in (1e3, 2e4):
+        t = np.round(shift * (1.0 + rng.uniform(size=d))) * np.where(rng.uniform(size=d) < 0.5, -1.0, 1.0)
+        assert np.array_equal((xv + t) - t, xv)
+        Kt = oracle.element_matrix(cell, k, xv + t, 0.3)
+        assert np.all(np.abs(Kt - K) <= 2e-15 * np.abs(K).max() + 8e-16 * np.abs(K)), (shift, np.abs(Kt - K).max())
+
+
 # ---------------------------------------------------------------- numbering
 
 def small_mesh(cell, jitter=0.0, seed=0):
