@@ -138,6 +138,19 @@ soptx_status soptx_mesh_copy_cell_nodes(soptx_mesh mesh, int32_t *d_cell_nodes, 
 
 /* Device path chosen for the mesh and the device bytes the mesh holds. */
 soptx_status soptx_mesh_path(soptx_mesh mesh, soptx_path *path);
+
+/*
+ * The kernels that serve the mesh's per-call work.
+ *   *assembly    : 0 box lattice (k_lattice_assemble2/3), 1 row gather of
+ *                  element matrices (cached, or one shared matrix), 2
+ *                  per-call contraction of the reference integrals in FP32
+ *                  (k_contract_rows: FP32 element matrices of affine cells)
+ *   *sensitivity : 0 box lattice (Walsh sectors), 1 fused into the row
+ *                  gather, 2 strain energy at quadrature points
+ *                  (k_strain_energy: affine cells)
+ * Either pointer may be NULL.
+ */
+soptx_status soptx_mesh_routes(soptx_mesh mesh, int32_t *assembly, int32_t *sensitivity);
 soptx_status soptx_mesh_device_bytes(soptx_mesh mesh, int64_t *bytes);
 
 /*
@@ -268,6 +281,20 @@ const char *soptx_last_error(void);
 
 /* Library version string. */
 const char *soptx_version(void);
+
+/*
+ * Diagnostic (no counterpart in the paper): the current device's throughput of
+ * FP32 and FP64 fused multiply-adds and of f32 -> f64 conversions, from
+ * all-SM microkernels timed with CUDA events (best of five launches).  The
+ * ratio ffma / dfma is why this library forms FP64-accurate element
+ * arithmetic in float pairs on the FP32 pipes.  Synchronises the device;
+ * allocates and frees a small buffer.  Errors: EINVAL (NULL), ENOMEM, ECUDA.
+ */
+typedef struct {
+    double ffma_per_s, dfma_per_s, f2f64_per_s;
+    int32_t sms;
+} soptx_pipe_rates;
+soptx_status soptx_measure_pipe_rates(soptx_pipe_rates *out);
 
 /* Test hook for failure handling: the n-th device allocation from now on
  * (n >= 1) fails as if the device were out of memory; n <= 0 disables. */

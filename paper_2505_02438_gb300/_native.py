@@ -56,7 +56,8 @@ class Request(ctypes.Structure):
 
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("queue_us", ctypes.c_double), ("latency_us", ctypes.c_double),
-                ("gpu_us", ctypes.c_double), ("nnz", ctypes.c_int64), ("mesh_was_resident", ctypes.c_int32)]
+                ("gpu_us", ctypes.c_double), ("nnz", ctypes.c_int64), ("mesh_was_resident", ctypes.c_int32),
+                ("gpu_start_us", ctypes.c_double), ("gpu_end_us", ctypes.c_double)]
 
 
 class ServerStats(ctypes.Structure):
@@ -64,6 +65,11 @@ class ServerStats(ctypes.Structure):
                 ("evictions", ctypes.c_int64), ("mesh_setups", ctypes.c_int64), ("resident_bytes", ctypes.c_int64),
                 ("peak_resident_bytes", ctypes.c_int64), ("resident_meshes", ctypes.c_int32),
                 ("in_flight", ctypes.c_int32), ("queued", ctypes.c_int32)]
+
+
+class PipeRates(ctypes.Structure):
+    _fields_ = [("ffma_per_s", ctypes.c_double), ("dfma_per_s", ctypes.c_double), ("f2f64_per_s", ctypes.c_double),
+                ("sms", ctypes.c_int32)]
 
 
 SIGNATURES = {
@@ -75,6 +81,7 @@ SIGNATURES = {
     "soptx_mesh_copy_cell_nodes": (i32, [P, P, P]),
     "soptx_mesh_path": (i32, [P, Pi32]),
     "soptx_mesh_device_bytes": (i32, [P, Pi64]),
+    "soptx_mesh_routes": (i32, [P, Pi32, Pi32]),
     "soptx_assemble_K": (i32, [P, P, P, P]),
     "soptx_sensitivity": (i32, [P, P, P, P, P, P]),
     "soptx_assemble_and_sensitivity": (i32, [P, P, P, P, P, P, P]),
@@ -101,6 +108,7 @@ SIGNATURES = {
     "soptx_server_destroy": (i32, [P]),
     "soptx_last_error": (ctypes.c_char_p, []),
     "soptx_version": (ctypes.c_char_p, []),
+    "soptx_measure_pipe_rates": (i32, [ctypes.POINTER(PipeRates)]),
     "soptx_debug_fail_alloc_after": (None, [i64]),
     "soptx_debug_lattice_no_sectors": (None, [i32]),
 }

@@ -70,6 +70,11 @@ class Mesh:
         N.check(L.soptx_mesh_device_bytes(h, ctypes.byref(nbytes)))
         self.path = N.PATH[path.value]
         self.device_bytes = nbytes.value
+        ra, rs = ctypes.c_int32(), ctypes.c_int32()
+        N.check(L.soptx_mesh_routes(h, ctypes.byref(ra), ctypes.byref(rs)))
+        # the kernels serving the per-call work (soptx_mesh_routes)
+        self.routes = {"assembly": ("lattice", "gather", "contract")[ra.value],
+                       "sensitivity": ("lattice", "gather", "strain")[rs.value]}
 
     @classmethod
     def from_workload(cls, wl, elem_prec=None, stream=None):

@@ -35,7 +35,7 @@ static void free_device(DeviceMesh &d)
     void *ptrs[] = {d.indptr, d.indices, d.cell_node, d.node_off, d.inc_ptr, d.inc,
                     d.pos, d.geo, d.M, d.K, d.scratch, d.Edf, d.kappa, d.K0, d.sectors, d.udf, d.part,
                     d.inc_e, d.inc_a, d.counter, d.xcell, d.qw, d.qdphi, d.qdgeo, d.cg, d.lat_bad, d.stage,
-                    d.kvals};
+                    d.kvals, d.sgeo, d.sq, d.cgeo, d.Mf, d.corder};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (d.cg_exec) cudaGraphExecDestroy(d.cg_exec);
@@ -89,6 +89,70 @@ static soptx_status upload(T **dst, const std::vector<T> &src, cudaStream_t st, 
         if (e != cudaSuccess) return cuda_status(e, what);
     }
     return SOPTX_OK;
+}
+
+static float2 split_pair(double x)
+{
+    const float hh = (float)x;
+    return make_float2(hh, (float)(x - (double)hh));
+}
+
+// Tables of the strain-energy sensitivities (k_strain_energy).
+static soptx_status setup_strain(soptx_mesh_s &m, const RefElement &ref, cudaStream_t st)
+{
+    const HostMesh &h = m.h;
+    RefQuad q;
+    if (is_simplex(h.cell)) build_simplex_quadrature(ref, q);
+    else build_tensor_quadrature(ref, q);
+    std::vector<float2> tab((size_t)q.nq * (1 + h.nb * h.dim));
+    for (int p = 0; p < q.nq; p++) tab[p] = split_pair(q.w[p]);
+    for (size_t t = 0; t < q.dphi.size(); t++) tab[q.nq + t] = split_pair(q.dphi[t]);
+    const int ng = h.dim * h.dim + 1;
+    const int64_t ncg = m.path == SOPTX_PATH_UNIFORM ? 1 : h.nc;
+    std::vector<float2> sg((size_t)ncg * ng);
+    for (size_t t = 0; t < sg.size(); t++) sg[t] = split_pair(h.geo[t]);
+    soptx_status s = upload(&m.d.sq, tab, st, m.device_bytes, "quadrature table");
+    if (s == SOPTX_OK) s = upload(&m.d.sgeo, sg, st, m.device_bytes, "cell geometry pairs");
+    if (s == SOPTX_OK) {
+        m.d.snq = q.nq;
+        m.d.strain = true;
+    }
+    return s;
+}
+
+// Tables of the per-call contraction (k_contract_rows): G and |det J| per cell
+// in FP32 (whole float4s), the reference integrals [a][b][k][l] in FP32.
+static soptx_status setup_contract(soptx_mesh_s &m, const RefElement &ref, cudaStream_t st)
+{
+    const HostMesh &h = m.h;
+    const int d = h.dim, nb = h.nb, ng = d * d + 1, n4 = d == 3 ? 3 : 2, mp = d == 3 ? 12 : 4;
+    std::vector<float4> cg((size_t)h.nc * n4, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int64_t e = 0; e < h.nc; e++) {
+        float *dst = reinterpret_cast<float *>(&cg[(size_t)e * n4]);
+        for (int t = 0; t < ng; t++) dst[t] = (float)h.geo[(size_t)e * ng + t];
+    }
+    std::vector<float> mf((size_t)nb * nb * mp, 0.f);
+    for (int a = 0; a < nb; a++)
+        for (int b = 0; b < nb; b++)
+            for (int k = 0; k < d; k++)
+                for (int l = 0; l < d; l++)
+                    mf[((size_t)a * nb + b) * mp + k * d + l] = (float)ref.M[(((size_t)k * d + l) * nb + a) * nb + b];
+    // processing order: nodes by incident-cell count, largest first, ascending ids
+    // within a count (a counting sort), so a warp's node groups walk as many cells
+    std::vector<int32_t> order((size_t)h.nn);
+    {
+        int32_t cmax = 0;
+        for (int64_t n = 0; n < h.nn; n++) cmax = std::max(cmax, h.inc_ptr[n + 1] - h.inc_ptr[n]);
+        std::vector<int64_t> start((size_t)cmax + 2, 0);
+        for (int64_t n = 0; n < h.nn; n++) start[(size_t)(cmax - (h.inc_ptr[n + 1] - h.inc_ptr[n])) + 1]++;
+        for (size_t c = 1; c < start.size(); c++) start[c] += start[c - 1];
+        for (int64_t n = 0; n < h.nn; n++) order[(size_t)start[(size_t)(cmax - (h.inc_ptr[n + 1] - h.inc_ptr[n]))]++] = (int32_t)n;
+    }
+    soptx_status s = upload(&m.d.cgeo, cg, st, m.device_bytes, "cell geometry");
+    if (s == SOPTX_OK) s = upload(&m.d.Mf, mf, st, m.device_bytes, "reference integrals (FP32)");
+    if (s == SOPTX_OK) s = upload(&m.d.corder, order, st, m.device_bytes, "node order");
+    if (s == SOPTX_OK) m.d.contract = true;
+    return s;
 }
 
 static bool material_ok(const soptx_material *m, int dim, Material &out, std::string &err)
@@ -276,6 +340,17 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
         }
         if (s == SOPTX_OK) s = cuda_status(cudaStreamSynchronize(st), "mesh setup");
     }
+    if (s == SOPTX_OK && m->path != SOPTX_PATH_LATTICE && !h.nonaffine && h.nc > 0) {
+        // affine cells off the lattice: the sensitivities from the strain energy at
+        // the points of a rule exact for it (G and |det J| per cell as float pairs,
+        // the weights and reference gradients of the rule)
+        s = setup_strain(*m, ref, st);
+        // FP32 element matrices: the assembly contracts the reference integrals with
+        // each cell's Jacobian per call (FP32 tables), the cache is not read
+        if (s == SOPTX_OK && prec == SOPTX_ELEM_FP32 && m->path == SOPTX_PATH_CACHED &&
+            contract_fits(h.dim, h.nb, h.max_deg))
+            s = setup_contract(*m, ref, st);
+    }
     if (s == SOPTX_OK && (m->path != SOPTX_PATH_LATTICE || !d.sectors)) {
         // per-call float-pair moduli and displacements, per-(cell, node) partials
         // of the general path (also the sensitivity of a lattice whose element
@@ -402,6 +477,14 @@ soptx_status soptx_mesh_path(soptx_mesh m, soptx_path *path)
     return SOPTX_OK;
 }
 
+soptx_status soptx_mesh_routes(soptx_mesh m, int32_t *assembly, int32_t *sensitivity)
+{
+    if (!m) SOPTX_FAIL(SOPTX_EINVAL, "mesh is NULL");
+    if (assembly) *assembly = m->path == SOPTX_PATH_LATTICE ? 0 : (m->d.contract ? 2 : 1);
+    if (sensitivity) *sensitivity = (m->path == SOPTX_PATH_LATTICE && m->d.sectors) ? 0 : (m->d.strain ? 2 : 1);
+    return SOPTX_OK;
+}
+
 soptx_status soptx_mesh_device_bytes(soptx_mesh m, int64_t *bytes)
 {
     if (!m || !bytes) SOPTX_FAIL(SOPTX_EINVAL, "mesh or bytes is NULL");
@@ -431,7 +514,7 @@ soptx_status soptx_assemble_and_sensitivity(soptx_mesh m, const double *d_rho, c
     if (!m) SOPTX_FAIL(SOPTX_EINVAL, "mesh is NULL");
     if ((!d_vals && m->h.nnz > 0) || (m->h.nc > 0 && (!d_rho || !d_u || !d_dc)))
         SOPTX_FAIL(SOPTX_EINVAL, "d_rho / d_u / d_vals / d_dc is NULL");
-    if (m->path == SOPTX_PATH_LATTICE && m->h.dim == 2 && m->d.sectors && m->h.nc > 0) {
+    if (((m->path == SOPTX_PATH_LATTICE && m->h.dim == 2 && m->d.sectors) || m->d.strain) && m->h.nc > 0) {
         cudaError_t e = ensure_side(*m);
         if (e != cudaSuccess) return cuda_status(e, "soptx_assemble_and_sensitivity stream");
     }

@@ -613,6 +613,15 @@ cudaError_t gather_t(const soptx_mesh_s &m, const double *rho, double *vals, boo
 
 int gather_finalize_grid(int64_t nc) { return ggrid(nc, 256); }
 
+// E(rho_e) per cell (and, with u, u per dof) as float pairs into the mesh's buffers.
+cudaError_t launch_prep(const soptx_mesh_s &m, const double *rho, const double *u, cudaStream_t st)
+{
+    const auto &h = m.h;
+    k_prep<<<ggrid(std::max(h.nc, u ? h.ndof : 0), 256), 256, 0, st>>>(h.nc, rho, simp_params(m.mat), m.d.Edf,
+                                                                       h.ndof, u, m.d.udf);
+    return cudaGetLastError();
+}
+
 // vals may be nullptr (sensitivity only); u may be nullptr (assembly only).
 cudaError_t launch_gather(const soptx_mesh_s &m, const double *rho, const double *u, double *vals, double *dc,
                           double *c, const double *gscale, cudaStream_t st)

@@ -56,6 +56,9 @@ struct RefQuad {
     std::vector<double> dgeo;   // [nq][nvc][dim]
 };
 void build_tensor_quadrature(const RefElement &ref, RefQuad &q);
+// Quadrature of the reference simplex exact for degree 2 (order - 1), with the
+// reference gradients of the basis at its points (dgeo left empty).
+void build_simplex_quadrature(const RefElement &ref, RefQuad &q);
 
 // ---------------------------------------------------------------- host mesh setup
 struct HostMesh {
@@ -115,6 +118,16 @@ struct DeviceMesh {
     // general path
     float2 *udf = nullptr;         // [ndof] u as float pairs (general path; lattice: one-call step)
     double *part = nullptr;        // [nc][nb] per-(cell, node) partials of u_e^T K_e^0 u_e
+    // meshes of affine cells: strain-energy sensitivities (contract.cu)
+    bool strain = false;           // the sensitivities take k_strain_energy
+    float2 *sgeo = nullptr;        //   [nc, or 1 when uniform][d*d + 1] G and |det J| as float pairs
+    float2 *sq = nullptr;          //   quadrature: weights [snq], reference gradients [snq][nb][d]
+    int snq = 0;
+    // FP32 element matrices of affine cells: assembled by contraction per call
+    bool contract = false;         // the assembly takes k_contract_rows
+    float4 *cgeo = nullptr;        //   [nc][2 or 3] G and |det J| in FP32
+    float *Mf = nullptr;           //   [nb][nb][4 or 12] reference integrals in FP32
+    int32_t *corder = nullptr;     //   [nn] nodes by incident-cell count, largest first
     // equilibrium solve (allocated by the first soptx_solve_cg)
     double *cg = nullptr;          // r z p q diag [ndof], scalars, partials, counters
     cudaGraphExec_t cg_exec = nullptr; // the CG iterations between two checks, as a graph
@@ -171,6 +184,12 @@ cudaError_t launch_lattice_step(const soptx_mesh_s &m, const double *rho, const 
 cudaError_t launch_gather(const soptx_mesh_s &m, const double *rho, const double *u, double *vals, double *dc,
                           double *c, const double *gscale, cudaStream_t st);
 int gather_finalize_grid(int64_t nc);
+cudaError_t launch_prep(const soptx_mesh_s &m, const double *rho, const double *u, cudaStream_t st);
+// contract.cu
+bool contract_fits(int dim, int nb, int max_deg);
+cudaError_t launch_contract_assemble(const soptx_mesh_s &m, const double *rho, double *vals, cudaStream_t st);
+cudaError_t launch_strain_sensitivity(const soptx_mesh_s &m, const double *rho, const double *u, double *out,
+                                      double *c, const double *gscale, cudaStream_t st);
 cudaError_t launch_step(const soptx_mesh_s &m, const double *rho, const double *u, double *vals, double *dc,
                         double *c, cudaStream_t st, const double *gscale = nullptr);
 __global__ void k_reduce_partials(int n, const double *__restrict__ partial, double *__restrict__ c);

@@ -266,6 +266,7 @@ cudaError_t launch_assemble(const soptx_mesh_s &m, const double *rho, double *va
 {
     if (m.h.nn == 0 || m.h.nnz == 0) return cudaSuccess;
     if (m.path == SOPTX_PATH_LATTICE) return launch_lattice_assemble(m, rho, vals, st);
+    if (m.d.contract) return launch_contract_assemble(m, rho, vals, st);
     return launch_gather(m, rho, nullptr, vals, nullptr, nullptr, nullptr, st);
 }
 
@@ -277,6 +278,7 @@ cudaError_t launch_sensitivity(const soptx_mesh_s &m, const double *rho, const d
         return cudaSuccess;
     }
     if (m.path == SOPTX_PATH_LATTICE && m.d.sectors) return launch_lattice_sensitivity(m, rho, u, dc, c, gscale, st);
+    if (m.d.strain) return launch_strain_sensitivity(m, rho, u, dc, c, gscale, st);
     return launch_gather(m, rho, u, nullptr, dc, c, gscale, st);
 }
 
@@ -286,7 +288,18 @@ cudaError_t launch_step(const soptx_mesh_s &m, const double *rho, const double *
 {
     if (m.path == SOPTX_PATH_LATTICE && m.d.sectors && m.h.nc > 0)
         return launch_lattice_step(m, rho, u, vals, dc, c, st, gscale);
-    if (m.path == SOPTX_PATH_LATTICE || m.h.nc == 0) {
+    if (m.d.strain && m.d.side && m.h.nc > 0 && m.h.nnz > 0) {
+        // affine cells: the sensitivities need rho and u but not K, so they run on
+        // the mesh's second stream beside the assembly
+        cudaError_t err = cudaEventRecord(m.d.ev[0], st);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(m.d.side, m.d.ev[0], 0);
+        if (err == cudaSuccess) err = launch_strain_sensitivity(m, rho, u, dc, c, gscale, m.d.side);
+        if (err == cudaSuccess) err = cudaEventRecord(m.d.ev[1], m.d.side);
+        if (err == cudaSuccess) err = launch_assemble(m, rho, vals, st);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(st, m.d.ev[1], 0);
+        return err;
+    }
+    if (m.path == SOPTX_PATH_LATTICE || m.h.nc == 0 || m.d.strain) {
         cudaError_t err = launch_assemble(m, rho, vals, st);
         if (err != cudaSuccess) return err;
         return launch_sensitivity(m, rho, u, dc, c, -1.0, gscale, st);

@@ -328,4 +328,94 @@ void build_tensor_quadrature(const RefElement &ref, RefQuad &q)
     }
 }
 
+// Reference gradients of the simplex basis at xi: with the barycentric
+// coordinates lam_0 = 1 - sum xi, lam_m = xi_m, the basis function of node a
+// is prod_v f_v(lam_v), f_v(t) = prod_{s < alpha_v} (k t - s) / (s + 1), and
+// d/dxi_m = d/dlam_m - d/dlam_0.
+static void simplex_basis_grad(const RefElement &ref, const double *xi, double *dphi)
+{
+    const int dim = ref.dim, k = ref.order, nb = ref.nb;
+    double lam[4] = {1.0, 0.0, 0.0, 0.0};
+    for (int m = 0; m < dim; m++) {
+        lam[m + 1] = xi[m];
+        lam[0] -= xi[m];
+    }
+    for (int a = 0; a < nb; a++) {
+        const int alpha[4] = {ref.lat[a][3], ref.lat[a][0], ref.lat[a][1], ref.lat[a][2]};
+        double f[4], df[4];
+        for (int v = 0; v <= dim; v++) {
+            double val = 1.0, der = 0.0;
+            for (int s = 0; s < alpha[v]; s++) {
+                const double c = (k * lam[v] - s) / (s + 1.0), dc = k / (s + 1.0);
+                der = der * c + val * dc;
+                val *= c;
+            }
+            f[v] = val;
+            df[v] = der;
+        }
+        double dl[4];
+        for (int v = 0; v <= dim; v++) {
+            double g = df[v];
+            for (int w = 0; w <= dim; w++)
+                if (w != v) g *= f[w];
+            dl[v] = g;
+        }
+        for (int m = 0; m < dim; m++) dphi[(size_t)a * dim + m] = dl[m + 1] - dl[0];
+    }
+}
+
+// Quadrature of the reference simplex exact for polynomials of degree
+// 2 (k - 1), the degree of the strain energy density of a P_k field:
+//   k = 1: the centroid;
+//   k = 2: triangle, the three edge midpoints (weights 1/6); tetrahedron, the
+//          symmetric four-point rule with barycentric coordinates
+//          (alpha, beta, beta, beta), alpha = (5 + 3 sqrt 5) / 20,
+//          beta = (5 - sqrt 5) / 20, weights 1/24;
+//   k = 3: the conical product of Gauss-Legendre rules (the collapsed square /
+//          cube: xi_1 = u, xi_2 = v (1 - u), xi_3 = w (1 - u)(1 - v), Jacobian
+//          (1 - u)^(d-1) (1 - v)^(d-2)), 3 x 3 points on the triangle and
+//          4 x 3 x 3 on the tetrahedron: the substituted integrand has degree
+//          p + d - 1 in u, p + d - 2 in v and p in w, p = 4.
+void build_simplex_quadrature(const RefElement &ref, RefQuad &q)
+{
+    const int dim = ref.dim, k = ref.order, nb = ref.nb;
+    std::vector<std::array<double, 3>> pts;
+    std::vector<double> wts;
+    if (k == 1) {
+        pts.push_back({1.0 / (dim + 1), 1.0 / (dim + 1), dim == 3 ? 0.25 : 0.0});
+        wts.push_back(dim == 3 ? 1.0 / 6 : 0.5);
+    } else if (k == 2 && dim == 2) {
+        pts = {{0.5, 0.0, 0.0}, {0.5, 0.5, 0.0}, {0.0, 0.5, 0.0}};
+        wts.assign(3, 1.0 / 6);
+    } else if (k == 2) {
+        const double al = (5.0 + 3.0 * std::sqrt(5.0)) / 20.0, be = (5.0 - std::sqrt(5.0)) / 20.0;
+        // lam_0 = alpha (the origin vertex), then alpha on each unit vertex
+        pts = {{be, be, be}, {al, be, be}, {be, al, be}, {be, be, al}};
+        wts.assign(4, 1.0 / 24);
+    } else {
+        std::vector<double> tu, wu, tv, wv;
+        gauss_legendre01(dim == 3 ? 4 : 3, tu, wu);
+        gauss_legendre01(3, tv, wv);
+        for (size_t iu = 0; iu < tu.size(); iu++)
+            for (size_t iv = 0; iv < tv.size(); iv++)
+                for (size_t iw = 0; iw < (dim == 3 ? tv.size() : 1); iw++) {
+                    const double u = tu[iu], v = tv[iv];
+                    if (dim == 2) {
+                        pts.push_back({u, v * (1.0 - u), 0.0});
+                        wts.push_back(wu[iu] * wv[iv] * (1.0 - u));
+                    } else {
+                        const double w = tv[iw];
+                        pts.push_back({u, v * (1.0 - u), w * (1.0 - u) * (1.0 - v)});
+                        wts.push_back(wu[iu] * wv[iv] * wv[iw] * (1.0 - u) * (1.0 - u) * (1.0 - v));
+                    }
+                }
+    }
+    q.nq = (int)pts.size();
+    q.nvc = 0;
+    q.w = wts;
+    q.dphi.assign((size_t)q.nq * nb * dim, 0.0);
+    q.dgeo.clear();
+    for (int p = 0; p < q.nq; p++) simplex_basis_grad(ref, pts[p].data(), &q.dphi[(size_t)p * nb * dim]);
+}
+
 }  // namespace soptx
