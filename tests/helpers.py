@@ -58,3 +58,56 @@ def oracle_csr(cell, k, coords, cells, mat, rho, rows=None):
     rp, ci, v, ndof = oracle.assemble(cell, k, coords, cells, mat, rho, rows=rows)
     _, _, va, _ = oracle.assemble(cell, k, coords, cells, mat, rho, rows=rows, absval=True)
     return rp, ci, v, va, ndof
+
+
+def _oracle_rows_job(job):
+    """One worker of oracle_full_parallel: the oracle's rows [r0, r1), their
+    values and the per-entry scale (sum of |contributions|)."""
+    cell, k, coords, cells, mat, rho, r0, r1 = job
+    rows = np.arange(r0, r1, dtype=np.int64)
+    rp, ci, v, ndof = oracle.assemble(cell, k, coords, cells, mat, rho, rows=rows)
+    _, _, va, _ = oracle.assemble(cell, k, coords, cells, mat, rho, rows=rows, absval=True)
+    return rp, ci, v, va, ndof
+
+
+def _oracle_sens_job(job):
+    cell, k, coords, cells, mat, rho, u, e0, e1 = job
+    sel = np.arange(e0, e1, dtype=np.int64)
+    dc, s, _, sa = oracle.sensitivity(cell, k, coords, cells, mat, rho, u, sel=sel, with_abs=True)
+    return dc, s, sa
+
+
+def _pool_size():
+    import os
+    n = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    return max(1, min(16, n))
+
+
+def oracle_full_parallel(cell, k, coords, cells, mat, rho, u, ndof):
+    """The oracle's whole CSR matrix (rowptr, cols, vals, |contribution| sums)
+    and every cell's (dc, s, sum_ab |u_a K_ab u_b|), computed by the oracle
+    unchanged over contiguous row and cell ranges in a spawned process pool
+    (spawn: safe in a process that has used the GPU)."""
+    import multiprocessing as mp
+    n = _pool_size()
+    rb = np.linspace(0, ndof, 4 * n + 1).astype(np.int64)
+    cb = np.linspace(0, len(cells), 2 * n + 1).astype(np.int64)
+    rjobs = [(cell, k, coords, cells, mat, rho, int(a), int(b)) for a, b in zip(rb[:-1], rb[1:]) if b > a]
+    cjobs = [(cell, k, coords, cells, mat, rho, u, int(a), int(b)) for a, b in zip(cb[:-1], cb[1:]) if b > a]
+    with mp.get_context("spawn").Pool(n) as pool:
+        rparts = pool.map(_oracle_rows_job, rjobs)
+        cparts = pool.map(_oracle_sens_job, cjobs)
+    assert all(p[4] == ndof for p in rparts)
+    rowptr = [np.zeros(1, np.int64)]
+    base = 0
+    for rp, _, _, _, _ in rparts:
+        rowptr.append(rp[1:] + base)
+        base += rp[-1]
+    rowptr = np.concatenate(rowptr)
+    cols = np.concatenate([p[1] for p in rparts])
+    vals = np.concatenate([p[2] for p in rparts])
+    va = np.concatenate([p[3] for p in rparts])
+    dc = np.concatenate([p[0] for p in cparts])
+    s = np.concatenate([p[1] for p in cparts])
+    sa = np.concatenate([p[2] for p in cparts])
+    return rowptr, cols, vals, va, dc, s, sa
