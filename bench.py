@@ -54,6 +54,14 @@ def workload(name):
         return W.mbb_q4(800, 400)
     if name == "hexj":
         return W.jittered_hex(120, 40, 40)
+    if name == "hexq2":
+        return W.cantilever_hex(40, 14, 14, order=2)
+    if name == "hexq2j":
+        return W.jittered_hex(40, 14, 14, order=2)
+    if name == "hexq3":
+        return W.cantilever_hex(26, 9, 9, order=3)
+    if name == "hexq3j":
+        return W.jittered_hex(26, 9, 9, order=3)
     raise ValueError(name)
 
 
@@ -262,26 +270,20 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_serve(args, rank, world, local_rank):
-    """Serving stream: 64 design jobs x 8 iterations = 512 assemble + sensitivity
-    requests through the continuous-batching server.  Every job's mesh is made
-    resident first (its setup timed apart); then a closed loop (all 512
-    submitted at once) gives the saturated rate R, and open loops with Poisson
-    arrivals at 0.5 R, 0.7 R and 0.9 R give the latency percentiles."""
+def serve_stream(n_jobs, iters, fracs, local_rank):
+    """n_jobs design jobs x iters assemble + sensitivity requests through the
+    continuous-batching server.  Every job's mesh is made resident first (its
+    setup timed apart); then a closed loop (all requests submitted at once)
+    gives the saturated rate R, and open loops with Poisson arrivals at
+    frac * R give the latency percentiles."""
     import threading
 
     import torch
-    from paper_2505_02438_gb300 import build as B
     from paper_2505_02438_gb300 import workloads as W
     from paper_2505_02438_gb300.api import host_plan
-    from paper_2505_02438_gb300.serve import Server
+    from paper_2505_02438_gb300.serve import Server, overlap
 
-    if rank != 0:
-        return
-    torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    B.build_library()
-    n_jobs, iters = 64, 8
     jobs = W.serving_stream(n_jobs=n_jobs, iters=iters)
     srv = Server(hbm_cap_bytes=120 << 30, max_slots=16, n_streams=8, max_queue=4096, device=local_rank)
     inputs, outs = {}, {}
@@ -316,10 +318,11 @@ def run_serve(args, rank, world, local_rank):
     res = [srv.wait(t) for t in tick]
     closed_s = time.perf_counter() - t0
     assert all(r["status"] == 0 for r in res)
+    closed_overlap = overlap(res)
     total_nnz = sum(nnz[job] for job, _ in order)
     R = len(order) / closed_s
     loads = {}
-    for frac in (0.5, 0.7, 0.9):
+    for frac in fracs:
         arr = W.poisson_arrivals(len(order), frac * R)
         tick = [None] * len(order)
         start = time.perf_counter()
@@ -342,26 +345,69 @@ def run_serve(args, rank, world, local_rank):
         loads[str(frac)] = {"rate_rps": frac * R, "p50_ms": float(np.percentile(lat, 50)),
                             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
                             "gpu_p50_ms": float(np.percentile(gpu, 50)),
-                            "gnnz_per_s": total_nnz / (end - start) / 1e9, "wall_s": end - start}
+                            "gnnz_per_s": total_nnz / (end - start) / 1e9, "wall_s": end - start,
+                            "overlap": overlap(res)}
     st = srv.stats()
     srv.close()
-    head = loads["0.7"]
     fam = {"quad": 0, "hex": 0, "tet": 0}
     for j in jobs:
         fam[j["workload"].cell] += 1
-    line = {"metric": METRIC, "value": total_nnz / closed_s / 1e9, "unit": "GNNZ/s", "n_gpus": 1,
-            "steps": len(order), "warmup": n_jobs, "higher_is_better": True, "scaling": "weak",
+    return {"jobs": n_jobs, "iterations": iters, "requests": len(order), "families": fam,
+            "fp32_jobs": sum(j["elem_prec"] == "fp32" for j in jobs),
+            "closed_loop": {"requests_per_s": R, "gnnz_per_s": total_nnz / closed_s / 1e9, "wall_s": closed_s,
+                            "overlap": closed_overlap},
+            "open_loop": loads, "mesh_setup_s": setup_s, "peak_resident_gb": st["peak_resident_bytes"] / 1e9,
+            "evictions": st["evictions"], "total_nnz": total_nnz}
+
+
+def run_serve(args, rank, world, local_rank):
+    """Serving stream: 64 design jobs x 8 iterations = 512 requests, open loops
+    at 0.5, 0.7 and 0.9 of the saturated rate."""
+    import torch
+    from paper_2505_02438_gb300 import build as B
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local_rank)
+    B.build_library()
+    sv = serve_stream(64, 8, (0.5, 0.7, 0.9), local_rank)
+    head = sv["open_loop"]["0.7"]
+    sv["p50_ms"], sv["p99_ms"] = head["p50_ms"], head["p99_ms"]
+    line = {"metric": METRIC, "value": sv["closed_loop"]["gnnz_per_s"], "unit": "GNNZ/s", "n_gpus": 1,
+            "steps": sv["requests"], "warmup": sv["jobs"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 and f32-elem/f64-acc (per job)", "data": "synthetic",
             "config": {"workload": "serving stream: 64 design jobs x 8 iterations = 512 requests, "
                                    "Q4 60x20..800x400, hex Q1 30x10x10..120x40x40, P2 tet up to 144k cells, "
                                    "FP64 or FP32 element matrices per job, Poisson arrivals",
-                       "families": fam, "hbm_cap_gb": 120, "max_slots": 16, "n_streams": 8,
-                       "fp32_jobs": sum(j["elem_prec"] == "fp32" for j in jobs)},
-            "serving": {"closed_loop": {"requests_per_s": R, "gnnz_per_s": total_nnz / closed_s / 1e9,
-                                        "wall_s": closed_s},
-                        "open_loop": loads, "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"],
-                        "mesh_setup_s": setup_s, "peak_resident_gb": st["peak_resident_bytes"] / 1e9,
-                        "evictions": st["evictions"], "total_nnz": total_nnz}}
+                       "families": sv["families"], "hbm_cap_gb": 120, "max_slots": 16, "n_streams": 8,
+                       "fp32_jobs": sv["fp32_jobs"]},
+            "serving": sv}
+    print(json.dumps(line), flush=True)
+
+
+def run_rates(args, rank, world, local_rank):
+    """The device's FP32 / FP64 fused multiply-add and f32 -> f64 conversion
+    rates (soptx_measure_pipe_rates), with the clocks they ran at."""
+    import ctypes
+
+    import torch
+    from paper_2505_02438_gb300 import _native as N
+    from paper_2505_02438_gb300 import build as B
+    if rank != 0:
+        return
+    torch.cuda.set_device(local_rank)
+    B.build_library()
+    r = N.PipeRates()
+    sampler = ClockSampler(local_rank)
+    with sampler:
+        N.check(N.lib().soptx_measure_pipe_rates(ctypes.byref(r)))
+    line = {"metric": "FP32 / FP64 fused multiply-add rate", "value": r.dfma_per_s / 1e12, "unit": "T DFMA/s",
+            "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "all-SM microkernels, 8 independent chains per thread, best of 5"},
+            "rates": {"ffma_T_per_s": r.ffma_per_s / 1e12, "dfma_T_per_s": r.dfma_per_s / 1e12,
+                      "f2f64_T_per_s": r.f2f64_per_s / 1e12, "ffma_over_dfma": r.ffma_per_s / r.dfma_per_s,
+                      "sms": r.sms},
+            "clocks": sampler.summary()}
     print(json.dumps(line), flush=True)
 
 
@@ -488,7 +534,153 @@ WORKLOAD_DESC = {
     "q4max": "Q4 plane stress 800x400 (320,000 cells, the largest serving mesh), FP64 K(rho) CSR + dc + c",
     "hexj": "3D cantilever box 120x40x40 trilinear hex Q1, interior vertices jittered (192,000 general hexahedra), "
             "FP64 K(rho) CSR + dc + c",
+    "hexq2": "box 40x14x14 of Q2 hexahedra (7,840 cells, 27 nodes each, 204,363 dofs, 36,889,641 nnz), "
+             "FP64 K(rho) CSR + dc + c",
+    "hexq2j": "40x14x14 Q2 hexahedra, interior vertices jittered (general trilinear cells), FP64 K(rho) CSR + dc + c",
+    "hexq3": "box 26x9x9 of Q3 hexahedra (2,106 cells, 64 nodes each, 185,808 dofs, 65,087,424 nnz), "
+             "FP64 K(rho) CSR + dc + c",
+    "hexq3j": "26x9x9 Q3 hexahedra, interior vertices jittered (general trilinear cells), FP64 K(rho) CSR + dc + c",
 }
+
+
+# The other configurations, each a compact record in the default line.
+EXTRA_CONFIGS = [
+    # (key, workload, element precision, time the backward)
+    ("q4_60x20", "q4", "fp64", False),
+    ("q4_800x400", "q4max", "fp64", False),
+    ("tri_p3_fp64", "tri", "fp64", False),
+    ("tri_p3_fp32", "tri", "fp32", False),
+    ("tet_p2_fp64", "tet", "fp64", True),
+    ("tet_p2_fp32", "tet", "fp32", False),
+]
+
+
+def assembly_kernel(mesh, wl, prec):
+    """(kernel name, kernel file) of the mesh's assembly launch."""
+    if mesh.routes["assembly"] == "lattice":
+        return ("k_lattice_assemble3" if wl.dim == 3 else "k_lattice_assemble2"), "lattice.cu"
+    if mesh.routes["assembly"] == "contract":
+        return "k_contract_rows", "contract.cu"
+    if (wl.dim, mesh.nb) in ((3, 10), (3, 8), (2, 10), (2, 4)):
+        return "k_gather_rows", "gather.cu"
+    return "k_gather_nodes", "gather.cu"
+
+
+def time_config(P, key, wl_name, prec, backward, steps, warmup, flush, dev, peak, ref=None, sample_seed=5):
+    """One configuration, timed like the headline (per-step CUDA events, L2
+    flushed between steps): the one-call step, the assembly call alone (its
+    roofline), optionally the backward; with ref (the FP64 form's outputs on
+    the device) the FP32 form's error against it.  Returns (record, outputs,
+    sample) where sample holds the values of seeded rows and cells for the
+    oracle comparison of the CPU leg."""
+    import torch
+    wl = workload(wl_name)
+    t0 = time.perf_counter()
+    mesh = P.Mesh.from_workload(wl, elem_prec=prec)
+    setup_s = time.perf_counter() - t0
+    nnz, ndof, nc = mesh.nnz, mesh.ndof, mesh.n_cells
+    rho = torch.as_tensor(wl.rho, device=dev)
+    u = torch.as_tensor(wl.displacement(ndof), device=dev)
+    vals = torch.empty(nnz, dtype=torch.float64, device=dev)
+    dc = torch.empty(nc, dtype=torch.float64, device=dev)
+    c = torch.empty(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        mesh.step(rho, u, vals, dc, c)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        mesh.step(rho, u, vals, dc, c)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    per = np.array([a.elapsed_time(b) for a, b in ev])
+    aev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        aev[k][0].record(stream)
+        mesh.assemble_K(rho, vals)
+        aev[k][1].record(stream)
+    torch.cuda.synchronize()
+    asm = float(np.mean([a.elapsed_time(b) for a, b in aev]))
+    mesh.step(rho, u, vals, dc, c)
+    ab = algorithmic_bytes(wl, nnz, ndof)
+    kname, kfile = assembly_kernel(mesh, wl, prec)
+    achieved = ab["assemble"] / (asm / 1e3) / 1e9
+    ms = float(per.mean())
+    rec = {"workload": WORKLOAD_DESC[wl_name], "path": mesh.path, "routes": dict(mesh.routes), "elem_prec": prec,
+           "nnz": nnz, "n_cells": nc,
+           "setup_s": setup_s, "ms_per_step": ms, "gnnz_per_s": nnz / (ms / 1e3) / 1e9,
+           "step_us_p10_p50_p90": [float(np.percentile(per, q)) * 1e3 for q in (10, 50, 90)],
+           "step_hbm_frac": ab["step"] / (ms / 1e3) / 1e9 / peak, "assemble_ms": asm,
+           "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "unit": "GB/s",
+                        "frac": achieved / peak, "alg_bytes_per_launch": ab["assemble"],
+                        "traffic": traffic_record(kfile, kname, wl.name, prec)},
+           "steps": steps}
+    if backward:
+        gout = torch.ones(1, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            mesh.compliance_vjp(rho, u, gout)
+        bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            bev[k][0].record(stream)
+            mesh.compliance_vjp(rho, u, gout)
+            bev[k][1].record(stream)
+        torch.cuda.synchronize()
+        rec["backward_ms"] = float(np.mean([a.elapsed_time(b) for a, b in bev]))
+    torch.cuda.synchronize()
+    if ref is not None:
+        v64, dc64, c64 = ref
+        kscale = v64.abs().max()
+        ek = (vals - v64).abs()
+        rec["error_vs_fp64_form"] = {
+            "K_max_err_over_max": float(ek.max() / kscale),
+            "K_max_rel_err": float((ek / (v64.abs() + 1e-7 * kscale)).max()),
+            "dc_max_err_over_max": float((dc - dc64).abs().max() / dc64.abs().max()),
+            "c_rel_err": float(abs(c.item() - c64.item()) / abs(c64.item()))}
+    # seeded rows and cells of this result, for the oracle comparison of the CPU leg
+    g = np.random.default_rng(sample_seed)
+    rows = np.unique(g.choice(ndof, min(ndof, 200), replace=False)).astype(np.int64)
+    cells = np.unique(g.choice(nc, min(nc, 200), replace=False)).astype(np.int64)
+    indptr, _ = mesh.pattern()
+    ip = indptr.cpu().numpy()
+    vh = vals.cpu().numpy()
+    sample = {"wl": wl, "prec": prec, "rows": rows, "vals": [vh[ip[r]:ip[r + 1]] for r in rows],
+              "cells": cells, "dc": dc.cpu().numpy()[cells], "u": u.cpu().numpy()}
+    del vh
+    mesh.close()
+    return rec, (vals, dc, c), sample
+
+
+def oracle_error(sample):
+    """The oracle on a result's sampled rows and cells (the CPU leg): the GPU
+    values' error relative to each entry's scale, sum_e |E_e K_e[a,b]|, and dc's
+    relative to E'_e sum_ab |u_a K_ab u_b|; and the oracle's own rate there."""
+    import oracle
+    wl = sample["wl"]
+    t0 = time.perf_counter()
+    rp, ci, v, _ = oracle.assemble(wl.cell, wl.order, wl.coords, wl.cells, wl.mat, wl.rho, rows=sample["rows"])
+    _, _, va, _ = oracle.assemble(wl.cell, wl.order, wl.coords, wl.cells, wl.mat, wl.rho, rows=sample["rows"],
+                                  absval=True)
+    dco, _, _, sa = oracle.sensitivity(wl.cell, wl.order, wl.coords, wl.cells, wl.mat, wl.rho, sample["u"],
+                                       sel=sample["cells"], with_abs=True)
+    dt = time.perf_counter() - t0
+    got = np.concatenate(sample["vals"])
+    # the parity tests' criterion |err| <= tol * sum|contributions| + floor, floor =
+    # (1e-15 | 1e-7) * max (entries that vanish exactly carry rounding noise in the
+    # oracle), written as err / (sum|contributions| + floor / tol) <= tol
+    tol = 1e-12 if sample["prec"] == "fp64" else 2e-6
+    scale = va + (1e-15 if sample["prec"] == "fp64" else 1e-7) / tol * va.max()
+    ok_pattern = len(got) == len(v)
+    kerr = np.abs(got - v) / scale if ok_pattern else np.array([np.inf])
+    E0, Emin, nu, p, ps = wl.mat
+    r = wl.rho[sample["cells"]]
+    derr = np.abs(sample["dc"] - dco) / (p * r ** (p - 1) * (E0 - Emin) * sa)
+    return {"rows": len(sample["rows"]), "cells": len(sample["cells"]), "K_max_err_over_scale": float(kerr.max()),
+            "K_rms_err_over_scale": float(np.sqrt(np.mean(kerr ** 2))), "dc_max_err_over_scale": float(derr.max()),
+            "tolerance": tol, "oracle_s": dt,
+            "oracle_gnnz_per_s": len(v) / dt / 1e9}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -533,14 +725,16 @@ def run_ours(args, rank, world, local_rank):
         evs[2].record(stream)
 
     warm_ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    for _ in range(args.warmup):
-        step_calls(warm_ev)
-    torch.cuda.synchronize()
-
     K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
-    sampler = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else local_rank)
+    sampler = ClockSampler(local_rank)
     with sampler:
+        # the warm-up steps run once the clock sampler is up, right before the timed
+        # steps, so the GPU does not idle (and clock down) between the two
+        for _ in range(args.warmup):
+            flush.zero_()
+            step_calls(warm_ev)
+        torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
@@ -602,22 +796,46 @@ def run_ours(args, rank, world, local_rank):
         e1.synchronize()
         e2e_ms += e0.elapsed_time(e1)
     e2e_ms = max_over_ranks([e2e_ms], world, dev)[0]
+    routes = dict(mesh.routes)
+
+    # every other configuration, one compact record each (rank 0 alone, N = 1)
+    extra, samples = {}, {}
+    if world == 1 and args.workload == "hex" and not args.no_extra:
+        peak_gbs, _ = peaks()
+        ref64 = None
+        for key, wname, prec, bwd in EXTRA_CONFIGS:
+            ref = ref64 if (prec == "fp32" and ref64 is not None and ref64[0] == wname) else None
+            rec, outs, sample = time_config(P, key, wname, prec, bwd, args.extra_steps, 3, flush, dev, peak_gbs,
+                                            ref=ref[1] if ref else None)
+            extra[key] = rec
+            samples[key] = sample
+            ref64 = (wname, outs) if prec == "fp64" else None
+            del outs
+        torch.cuda.empty_cache()
+        sv = serve_stream(16, 4, (0.7,), local_rank)
+        head = sv["open_loop"]["0.7"]
+        extra["serving"] = {"requests": sv["requests"], "jobs": sv["jobs"], "iterations": sv["iterations"],
+                            "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"], "load": "0.7 of the saturated rate",
+                            "gnnz_per_s_open_loop": head["gnnz_per_s"],
+                            "gnnz_per_s_closed_loop": sv["closed_loop"]["gnnz_per_s"],
+                            "families": sv["families"], "fp32_jobs": sv["fp32_jobs"],
+                            "peak_resident_gb": sv["peak_resident_gb"],
+                            "overlap_open_loop": head["overlap"], "overlap_closed_loop": sv["closed_loop"]["overlap"]}
 
     if rank != 0:
         return
     ab = algorithmic_bytes(wl, nnz, ndof)
     peak, peak_kind = peaks()
-    if lattice:
+    kernel_name, kernel_file = assembly_kernel(mesh, wl, args.elem_prec)
+    if routes["sensitivity"] != "gather":
         # the assembly kernel's launches, timed through soptx_assemble_K (which also holds
         # the short element-moduli kernel, so the figure is a lower bound)
         achieved = ab["assemble"] / (asm_ms / n_split / 1e3) / 1e9
-        kernel_name = "k_lattice_assemble3" if wl.dim == 3 else "k_lattice_assemble2"
-        kernel_file, alg_launch = "lattice.cu", ab["assemble"]
+        alg_launch = ab["assemble"]
     else:
         # one fused gather does both passes: its algorithmic bytes are the whole step's
         achieved = ab["step"] / (step_ms / K / 1e3) / 1e9
-        kernel_name = "k_gather_rows" if (wl.dim, mesh.nb) in ((3, 10), (3, 8), (2, 10), (2, 4)) else "k_gather_nodes"
-        kernel_file, alg_launch = "gather.cu", ab["step"]
+        alg_launch = ab["step"]
     traffic = traffic_record(kernel_file, kernel_name, wl.name, args.elem_prec)
     value = job_rate(nnz, world, K, step_ms) / 1e9
     line = {
@@ -625,10 +843,12 @@ def run_ours(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": step_ms / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.elem_prec == "fp64" else "f32-elem/f64-acc",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC[args.workload], "path": mesh.path, "nnz": nnz, "ndof": ndof,
+        "config": {"workload": WORKLOAD_DESC[args.workload], "path": mesh.path, "routes": routes, "nnz": nnz,
+                   "ndof": ndof,
                    "n_cells": nc, "elem_prec": args.elem_prec, "l2": "flushed (256 MiB write) between steps",
                    "parallelism": "replicas" if world > 1 else "single"},
         "step_us_p10_p50_p90": [float(np.percentile(per_step, q)) * 1e3 for q in (10, 50, 90)],
+        "step_us_max": float(per_step.max()) * 1e3,
         "sens_elems_per_s": job_rate(nc, world, K, step_ms),
         "setup_s": setup_s,
         "separate_calls": {"assemble_ms": asm_ms / n_split, "sensitivity_ms": sens_ms / n_split,
@@ -649,12 +869,17 @@ def run_ours(args, rank, world, local_rank):
         "wall_s_timed_region": wall,
     }
     if args.elem_prec == "fp32":
-        line["accuracy_vs_fp64"] = fp32_accuracy(P, wl, mesh, rho, u)
+        line["accuracy_vs_fp64"] = fp32_accuracy(P, wl, P.Mesh.from_workload(wl, elem_prec="fp32"), rho, u)
+    if extra:
+        line["configs"] = extra
     if world == 1 and not args.no_cpu_baseline:
         r, desc = cpu_oracle_sample(args.workload, args.cpu_seconds)
         line["cpu_baseline"] = {"value": r, "unit": "GNNZ/s", "cores": 1, "kind": "oracle", "sample": desc}
         ra, na, desca = cpu_oracle_all_cores(args.workload, args.cpu_seconds / 3)
         line["cpu_baseline"]["all_cores"] = {"value": ra, "unit": "GNNZ/s", "cores": na, "sample": desca}
+        # the oracle on seeded rows and cells of every other configuration's GPU result
+        for key, sample in samples.items():
+            line["configs"][key]["error_vs_oracle"] = oracle_error(sample)
     print(json.dumps(line), flush=True)
 
 
@@ -664,9 +889,11 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="hex", choices=sorted(WORKLOAD_DESC) + ["serve", "solve", "to"])
+    ap.add_argument("--workload", default="hex", choices=sorted(WORKLOAD_DESC) + ["serve", "solve", "to", "rates"])
     ap.add_argument("--elem-prec", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the records of the other configurations")
+    ap.add_argument("--extra-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--cg-rtol", type=float, default=1e-6)
     ap.add_argument("--cg-max-iter", type=int, default=3000)
@@ -685,6 +912,9 @@ def main():
         return
     if args.workload == "solve":
         run_solve(args, rank, world, local_rank)
+        return
+    if args.workload == "rates":
+        run_rates(args, rank, world, local_rank)
         return
     if args.workload == "to":
         run_to(args, rank, world, local_rank)

@@ -70,6 +70,12 @@ typedef struct {
     double gpu_us;           /* device time of the request's kernels          */
     int64_t nnz;             /* CSR nonzeros of the job's mesh                */
     int32_t mesh_was_resident; /* 1 if no mesh setup was needed              */
+    /* device timeline of the request, in microseconds from an event the server
+     * records at creation: when its stream reached the request's first
+     * operation and when its last operation completed (gpu_end_us -
+     * gpu_start_us = gpu_us).  Intervals of different requests that intersect
+     * were in flight on the device at the same time. */
+    double gpu_start_us, gpu_end_us;
 } soptx_result;
 
 typedef struct {

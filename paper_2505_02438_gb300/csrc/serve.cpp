@@ -73,6 +73,7 @@ int64_t mesh_bytes_bound(const soptx_request &r)
 struct soptx_server_s {
     soptx_server_opts opts{};
     std::vector<cudaStream_t> streams;
+    cudaEvent_t t0 = nullptr;   // origin of the requests' device timeline
     std::mutex mu;
     std::condition_variable cv_sched, cv_done;
     std::deque<Req *> queue;
@@ -106,10 +107,20 @@ struct soptx_server_s {
                 k++;
                 continue;
             }
-            float ms = 0.f;
-            if (e == cudaSuccess) cudaEventElapsedTime(&ms, q->ev0, q->ev1);
-            else cudaGetLastError();
+            float ms = 0.f, ms0 = 0.f, ms1 = 0.f;
+            if (e == cudaSuccess) {
+                cudaEventElapsedTime(&ms, q->ev0, q->ev1);
+                if (cudaEventElapsedTime(&ms0, t0, q->ev0) != cudaSuccess ||
+                    cudaEventElapsedTime(&ms1, t0, q->ev1) != cudaSuccess) {
+                    cudaGetLastError();
+                    ms0 = ms1 = 0.f;
+                }
+            } else {
+                cudaGetLastError();
+            }
             q->res.gpu_us = 1e3 * ms;
+            q->res.gpu_start_us = 1e3 * ms0;
+            q->res.gpu_end_us = 1e3 * ms1;
             q->job->in_flight--;
             finish(q, e == cudaSuccess ? SOPTX_OK : SOPTX_ECUDA);
             inflight.erase(inflight.begin() + k);
@@ -293,6 +304,14 @@ soptx_status soptx_server_create(const soptx_server_opts *opts, soptx_server *ou
         }
         s->streams.push_back(st);
     }
+    if (cudaEventCreate(&s->t0) != cudaSuccess || cudaEventRecord(s->t0, s->streams[0]) != cudaSuccess ||
+        cudaEventSynchronize(s->t0) != cudaSuccess) {
+        cudaGetLastError();
+        if (s->t0) cudaEventDestroy(s->t0);
+        for (auto x : s->streams) cudaStreamDestroy(x);
+        delete s;
+        SOPTX_FAIL(SOPTX_ECUDA, "timeline event");
+    }
     s->th = std::thread([s] { s->run(); });
     *out = s;
     return SOPTX_OK;
@@ -393,6 +412,7 @@ soptx_status soptx_server_destroy(soptx_server s)
         delete kv.second;
     }
     for (auto st : s->streams) cudaStreamDestroy(st);
+    if (s->t0) cudaEventDestroy(s->t0);
     delete s;
     return SOPTX_OK;
 }

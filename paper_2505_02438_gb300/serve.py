@@ -60,7 +60,8 @@ class Server:
         res = N.Result()
         N.check(N.lib().soptx_serve_wait(self._h, ctypes.c_uint64(ticket), int(timeout_us), ctypes.byref(res)))
         out = dict(status=res.status, queue_us=res.queue_us, latency_us=res.latency_us, gpu_us=res.gpu_us,
-                   nnz=res.nnz, mesh_was_resident=bool(res.mesh_was_resident))
+                   nnz=res.nnz, mesh_was_resident=bool(res.mesh_was_resident), gpu_start_us=res.gpu_start_us,
+                   gpu_end_us=res.gpu_end_us)
         vals, dc, c = self.outputs(ticket)
         out.update(vals=vals, dc=dc, c=c)
         del self._keep[ticket]
@@ -87,3 +88,24 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def overlap(results):
+    """How much the requests' device intervals [gpu_start_us, gpu_end_us]
+    overlapped: the largest number in flight at one instant, and the share of
+    requests whose interval intersects another's."""
+    iv = sorted((r["gpu_start_us"], r["gpu_end_us"]) for r in results if r["gpu_end_us"] > r["gpu_start_us"])
+    ev = sorted([(a, 1) for a, _ in iv] + [(b, -1) for _, b in iv], key=lambda t: (t[0], t[1]))
+    cur = peak = 0
+    for _, d in ev:
+        cur += d
+        peak = max(peak, cur)
+    shared = 0
+    end_max = -np.inf
+    for k, (a, b) in enumerate(iv):
+        # intersects an earlier interval, or the next one starts before this ends
+        if a < end_max or (k + 1 < len(iv) and iv[k + 1][0] < b):
+            shared += 1
+        end_max = max(end_max, b)
+    return {"max_in_flight": peak, "overlapped_share": shared / max(1, len(iv))}
+

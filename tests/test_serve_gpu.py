@@ -95,3 +95,41 @@ def test_error_paths(lib):
         assert srv.wait(x)["status"] == 0
     assert busy >= 1
     srv.close()
+
+
+def test_requests_of_different_jobs_are_in_flight_together(lib):
+    """Requests of different jobs run on different streams: with their meshes
+    resident and submitted together, their device intervals overlap (the
+    record that shows it: gpu_start_us / gpu_end_us on one timeline), while
+    the requests of one job run one after the other.  The meshes are as large
+    as the serving mix's largest hexahedral ones (about 80 us of device work
+    per request, several times the host's time to launch one): requests much
+    shorter than a launch finish before the next one reaches the device."""
+    from paper_2505_02438_gb300.serve import Server, overlap
+    jobs = [dict(job=j, workload=W.cantilever_hex(100, 40, 40, wl=300 + j)) for j in range(3)]
+    meshes = {j["job"]: lib.Mesh.from_workload(j["workload"]) for j in jobs}
+    srv = Server(max_slots=8, n_streams=4)
+    # first request per job makes its mesh resident
+    warm = [srv.submit(j["job"], j["workload"], *inputs(meshes[j["job"]], j["job"], 0)) for j in jobs]
+    assert all(srv.wait(t)["status"] == 0 for t in warm)
+    # every input and output allocated first: a fresh device allocation synchronises
+    # the device, which would serialise the requests
+    reqs = []
+    for it in range(3):
+        for j in jobs:
+            m = meshes[j["job"]]
+            reqs.append((j, inputs(m, j["job"], it + 1), torch.empty(m.nnz, dtype=torch.float64, device="cuda")))
+    torch.cuda.synchronize()
+    tickets = [(j["job"], srv.submit(j["job"], j["workload"], *x, vals=vals)) for j, x, vals in reqs]
+    res = [(job, srv.wait(t)) for job, t in tickets]
+    srv.close()
+    assert all(r["status"] == 0 for _, r in res)
+    for _, r in res:
+        assert r["gpu_end_us"] > r["gpu_start_us"] >= 0.0
+        assert abs((r["gpu_end_us"] - r["gpu_start_us"]) - r["gpu_us"]) <= 1.0 + 1e-3 * r["gpu_us"]
+    ov = overlap([r for _, r in res])
+    assert ov["max_in_flight"] >= 2, ov
+    # one job's requests share its stream: they never overlap each other
+    for j in jobs:
+        iv = sorted((r["gpu_start_us"], r["gpu_end_us"]) for job, r in res if job == j["job"])
+        assert all(b[0] >= a[1] - 1.0 for a, b in zip(iv, iv[1:])), iv
