@@ -348,6 +348,11 @@ template <> struct SArith<true> {
         return r;
     }
     static __device__ __forceinline__ V add(V x, V y) { return df_add_lazy(x, y); }
+    static __device__ __forceinline__ V sum(V x, V y) { return df_add(x, y); }
+    static __device__ __forceinline__ V shfl_xor(V x, int o)
+    {
+        return df{__shfl_xor_sync(kFull, x.h, o), __shfl_xor_sync(kFull, x.l, o)};
+    }
     static __device__ __forceinline__ V mul(V x, V y) { return df_mul(x, y); }
     static __device__ __forceinline__ V from_u(double x) { return df_split_z(x); }
     static __device__ __forceinline__ V from_pair(float2 v) { return df{v.x, v.y}; }
@@ -366,6 +371,8 @@ template <> struct SArith<false> {
     static __device__ __forceinline__ void fma(Acc &a, V x, V y) { a.s = fmaf(x, y, a.s); }
     static __device__ __forceinline__ V val(const Acc &a) { return a.s; }
     static __device__ __forceinline__ V add(V x, V y) { return x + y; }
+    static __device__ __forceinline__ V sum(V x, V y) { return x + y; }
+    static __device__ __forceinline__ V shfl_xor(V x, int o) { return __shfl_xor_sync(kFull, x, o); }
     static __device__ __forceinline__ V mul(V x, V y) { return x * y; }
     // rounded to FP32 with integer operations (no FP64 conversion)
     static __device__ __forceinline__ V from_u(double x)
@@ -497,6 +504,102 @@ __global__ void __launch_bounds__(128) k_strain_energy(const StrainArgs A)
     if (A.c) grid_sum_last_block(mine, A.partial, A.counter, A.c);
 }
 
+// The strain energy density at quadrature point q of a cell whose
+// displacements are staged at us[(b d + i) * ustride] (reference gradients at
+// the point dq[b][m], G row-major), times the point's weight.
+template <int D, bool PAIR>
+__device__ __forceinline__ typename SArith<PAIR>::V
+point_energy(const StrainArgs &A, const typename SArith<PAIR>::V *us, int ustride, int q,
+             const typename SArith<PAIR>::V *G, typename SArith<PAIR>::V lam, typename SArith<PAIR>::V mu)
+{
+    using S = SArith<PAIR>;
+    using V = typename S::V;
+    typename S::Acc U[D][D];
+    const float2 *dq = A.qd + (size_t)q * A.nb * D;
+    for (int bb = 0; bb < A.nb; bb++) {
+        V ub[D], dp[D];
+#pragma unroll
+        for (int i = 0; i < D; i++) ub[i] = us[(bb * D + i) * ustride];
+#pragma unroll
+        for (int m = 0; m < D; m++) dp[m] = S::from_pair(__ldg(dq + bb * D + m));
+#pragma unroll
+        for (int i = 0; i < D; i++)
+#pragma unroll
+            for (int m = 0; m < D; m++) S::fma(U[i][m], ub[i], dp[m]);
+    }
+    V Uv[D][D];
+#pragma unroll
+    for (int i = 0; i < D; i++)
+#pragma unroll
+        for (int m = 0; m < D; m++) Uv[i][m] = S::val(U[i][m]);
+    V gu[D][D];
+#pragma unroll
+    for (int i = 0; i < D; i++)
+#pragma unroll
+        for (int j = 0; j < D; j++) {
+            typename S::Acc a;
+#pragma unroll
+            for (int m = 0; m < D; m++) S::fma(a, Uv[i][m], G[m * D + j]);
+            gu[i][j] = S::val(a);
+        }
+    V tr = gu[0][0];
+#pragma unroll
+    for (int m = 1; m < D; m++) tr = S::add(tr, gu[m][m]);
+    typename S::Acc sh;
+#pragma unroll
+    for (int i = 0; i < D; i++)
+#pragma unroll
+        for (int j = 0; j < D; j++) S::fma(sh, gu[i][j], S::add(gu[i][j], gu[j][i]));
+    typename S::Acc dens;
+    S::fma(dens, lam, S::mul(tr, tr));
+    S::fma(dens, mu, S::val(sh));
+    return S::mul(S::from_pair(__ldg(A.qw + q)), S::val(dens));
+}
+
+// The same sensitivities with a warp per cell, for cells with many nodes and
+// points (nb nq >= 256: Q3 quadrilaterals, Q2/Q3 hexahedra, P3 tetrahedra),
+// where one thread per cell leaves most of the GPU idle: the warp stages the
+// cell's displacements in shared memory, each lane takes the points q = lane,
+// lane + 32, ..., and a fixed-order butterfly sums the lanes' energies (the
+// same bits on every lane).
+template <int D, bool PAIR>
+__global__ void __launch_bounds__(128) k_strain_energy_warp(const StrainArgs A)
+{
+    using S = SArith<PAIR>;
+    using V = typename S::V;
+    extern __shared__ float2 ush2[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const int nb = A.nb, nv = nb * D;
+    V *us = reinterpret_cast<V *>(ush2) + (size_t)warp * nv;
+    const double g = A.gscale ? *A.gscale : -1.0;
+    const V lam = S::from_pair(A.lam), mu = S::from_pair(A.mu);
+    double mine = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * wpb + warp; e < A.nc; e += (int64_t)gridDim.x * wpb) {
+        __syncwarp();
+        for (int t = lane; t < nv; t += 32) {
+            const int bb = t / D, i = t - D * bb;
+            us[t] = S::from_u(A.u[(int64_t)D * A.cell_node[e * nb + bb] + i]);
+        }
+        __syncwarp();
+        V G[D * D];
+        const float2 *gp = A.geo + e * A.geo_stride;
+#pragma unroll
+        for (int t = 0; t < D * D; t++) G[t] = S::from_pair(gp[t]);
+        const V det = S::from_pair(gp[D * D]);
+        V sv = S::from_pair(make_float2(0.f, 0.f));
+        for (int q = lane; q < A.nq; q += 32) sv = S::sum(sv, point_energy<D, PAIR>(A, us, 1, q, G, lam, mu));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sv = S::sum(sv, S::shfl_xor(sv, o));
+        if (lane == 0) {
+            const double sd = S::to_double(S::mul(sv, det));
+            const double r = A.rho[e];
+            A.out[e] = g * simp_dE(A.sp, r) * sd;
+            mine += simp_E(A.sp, r) * sd;
+        }
+    }
+    if (A.c) grid_sum_last_block(mine, A.partial, A.counter, A.c);
+}
+
 template <int D, int NB, int MINB>
 cudaError_t contract_launch(const soptx_mesh_s &m, const double *rho, double *vals, cudaStream_t st)
 {
@@ -605,6 +708,17 @@ cudaError_t launch_strain_sensitivity(const soptx_mesh_s &m, const double *rho, 
     A.c = c;
     const bool f32 = m.prec == SOPTX_ELEM_FP32;
     const size_t vb = f32 ? sizeof(float) : sizeof(float2);
+    if ((int64_t)h.nb * A.nq >= 256) {
+        // a warp per cell: 4 warps per block, each staging one cell's displacements
+        const size_t smem = (size_t)4 * h.nb * h.dim * vb;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((h.nc + 3) / 4, m.d.scratch_len));
+        auto k = h.dim == 3 ? (f32 ? k_strain_energy_warp<3, false> : k_strain_energy_warp<3, true>)
+                            : (f32 ? k_strain_energy_warp<2, false> : k_strain_energy_warp<2, true>);
+        cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        k<<<grid, 128, smem, st>>>(A);
+        return cudaGetLastError();
+    }
     // threads per block: a power of two whose staging fits in 96 KiB
     int T = 128;
     while (T > 32 && (size_t)T * h.nb * h.dim * vb > 96 * 1024) T >>= 1;

@@ -307,7 +307,13 @@ cudaError_t launch_step(const soptx_mesh_s &m, const double *rho, const double *
     return launch_gather(m, rho, u, m.h.nnz > 0 ? vals : nullptr, dc, c, gscale, st);
 }
 
-int64_t sensitivity_scratch_len(const soptx_mesh_s &m) { return std::max(gather_finalize_grid(m.h.nc), 1); }
+// Block partials of c: enough for every sensitivity grid, the widest being the
+// strain-energy kernel with a warp per cell (4 cells per block, at most 152 x 16 blocks).
+int64_t sensitivity_scratch_len(const soptx_mesh_s &m)
+{
+    const int64_t warp_grid = std::min<int64_t>((m.h.nc + 3) / 4, 152 * 16);
+    return std::max<int64_t>(std::max<int64_t>(gather_finalize_grid(m.h.nc), warp_grid), 1);
+}
 
 template <int D, typename KT>
 static cudaError_t ku_t(const soptx_mesh_s &m, const double *rho, const double *u, const double *gout, double *out,
