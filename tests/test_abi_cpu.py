@@ -153,8 +153,9 @@ def test_traffic_records_are_keyed_on_kernel_workload_and_precision():
     rec = os.path.join(ROOT, "profiles", "traffic.txt")
     lines = [dict(x.split("=", 1) for x in ln.split() if "=" in x) for ln in open(rec) if ln.startswith("kernel=")]
     assert lines
-    src = {"k_lattice_assemble3": "lattice.cu", "k_lattice_assemble2": "lattice.cu", "k_gather_rows": "gather.cu",
-           "k_spmv": "solve.cu"}
+    src = {"k_lattice_assemble3": "lattice.cu", "k_lattice_assemble2": "lattice.cu", "k_lattice_sens": "lattice.cu",
+           "k_gather_rows": "gather.cu", "k_gather_nodes": "gather.cu", "k_contract_rows": "contract.cu",
+           "k_strain_energy": "contract.cu", "k_spmv": "solve.cu"}
     for kv in lines:
         f = src[kv["kernel"]]
         got = bench.traffic_record(f, kv["kernel"], kv["workload"], kv.get("prec", "fp64"))
