@@ -35,7 +35,7 @@ static void free_device(DeviceMesh &d)
     void *ptrs[] = {d.indptr, d.indices, d.cell_node, d.node_off, d.inc_ptr, d.inc,
                     d.pos, d.geo, d.M, d.K, d.scratch, d.Edf, d.kappa, d.K0, d.sectors, d.udf, d.part,
                     d.inc_e, d.inc_a, d.counter, d.xcell, d.qw, d.qdphi, d.qdgeo, d.cg, d.lat_bad, d.stage,
-                    d.kvals, d.sgeo, d.sq, d.cgeo, d.Mf, d.corder};
+                    d.kvals, d.sgeo, d.sq, d.cgeo, d.Mf, d.corder, d.cinc_e, d.cinc_a, d.crec};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (d.cg_exec) cudaGraphExecDestroy(d.cg_exec);
@@ -148,9 +148,78 @@ static soptx_status setup_contract(soptx_mesh_s &m, const RefElement &ref, cudaS
         for (size_t c = 1; c < start.size(); c++) start[c] += start[c - 1];
         for (int64_t n = 0; n < h.nn; n++) order[(size_t)start[(size_t)(cmax - (h.inc_ptr[n + 1] - h.inc_ptr[n]))]++] = (int32_t)n;
     }
+    // Each node's cells as a chain: the next cell is the unvisited one that holds
+    // the most of the nodes the group's lanes hold now (ties: the lowest cell id);
+    // a lane keeps its node when the next cell has it, and the cell's other nodes
+    // go to the free lanes in local order.  A lane whose column block continues
+    // into the next cell keeps its row sums in registers instead of a round trip
+    // through shared memory.  Per (incidence, lane): local node b << 11 | block p.
+    const int64_t ninc = h.inc_ptr[(size_t)h.nn];
+    std::vector<int32_t> ce((size_t)ninc);
+    std::vector<uint8_t> ca((size_t)ninc);
+    std::vector<uint16_t> rec((size_t)ninc * nb);
+    {
+        std::vector<int64_t> lane_mark((size_t)h.nn, -1), cell_mark((size_t)h.nn, -1);
+        std::vector<int32_t> cell_loc((size_t)h.nn, 0);
+        std::vector<int32_t> lanes(nb), next(nb);
+        std::vector<char> used, taken(nb);
+        int64_t stamp = 0;
+        for (int64_t n = 0; n < h.nn; n++) {
+            const int32_t q0 = h.inc_ptr[(size_t)n], cnt = h.inc_ptr[(size_t)n + 1] - q0;
+            used.assign((size_t)cnt, 0);
+            int32_t t = 0;
+            for (int32_t k = 0; k < cnt; k++) {
+                if (k > 0) {
+                    // the unvisited cell sharing the most nodes with the lanes
+                    ++stamp;
+                    for (int L = 0; L < nb; L++) lane_mark[(size_t)lanes[L]] = stamp;
+                    int best = -1, bshare = -1;
+                    for (int32_t c = 0; c < cnt; c++) {
+                        if (used[(size_t)c]) continue;
+                        const int32_t *cn = &h.cell_node[(size_t)h.inc_e[(size_t)(q0 + c)] * nb];
+                        int share = 0;
+                        for (int b = 0; b < nb; b++) share += lane_mark[(size_t)cn[b]] == stamp;
+                        if (share > bshare) { bshare = share; best = c; }
+                    }
+                    t = best;
+                }
+                used[(size_t)t] = 1;
+                const int32_t qo = q0 + t, e = h.inc_e[(size_t)qo];
+                const int32_t *cn = &h.cell_node[(size_t)e * nb];
+                if (k == 0) {
+                    for (int L = 0; L < nb; L++) next[L] = L;
+                } else {
+                    ++stamp;
+                    for (int b = 0; b < nb; b++) { cell_mark[(size_t)cn[b]] = stamp; cell_loc[(size_t)cn[b]] = b; }
+                    std::fill(taken.begin(), taken.end(), 0);
+                    for (int L = 0; L < nb; L++) {
+                        next[L] = cell_mark[(size_t)lanes[L]] == stamp ? cell_loc[(size_t)lanes[L]] : -1;
+                        if (next[L] >= 0) taken[next[L]] = 1;
+                    }
+                    int b = 0;
+                    for (int L = 0; L < nb; L++) {
+                        if (next[L] >= 0) continue;
+                        while (taken[b]) b++;
+                        next[L] = b;
+                        taken[b] = 1;
+                    }
+                }
+                const int64_t qn = q0 + k;
+                ce[(size_t)qn] = e;
+                ca[(size_t)qn] = h.inc_a[(size_t)qo];
+                for (int L = 0; L < nb; L++) {
+                    lanes[L] = cn[next[L]];
+                    rec[(size_t)qn * nb + L] = (uint16_t)((next[L] << 11) | h.pos[(size_t)qo * nb + next[L]]);
+                }
+            }
+        }
+    }
     soptx_status s = upload(&m.d.cgeo, cg, st, m.device_bytes, "cell geometry");
     if (s == SOPTX_OK) s = upload(&m.d.Mf, mf, st, m.device_bytes, "reference integrals (FP32)");
     if (s == SOPTX_OK) s = upload(&m.d.corder, order, st, m.device_bytes, "node order");
+    if (s == SOPTX_OK) s = upload(&m.d.cinc_e, ce, st, m.device_bytes, "contraction cell chains");
+    if (s == SOPTX_OK) s = upload(&m.d.cinc_a, ca, st, m.device_bytes, "contraction local indices");
+    if (s == SOPTX_OK) s = upload(&m.d.crec, rec, st, m.device_bytes, "contraction lane records");
     if (s == SOPTX_OK) m.d.contract = true;
     return s;
 }

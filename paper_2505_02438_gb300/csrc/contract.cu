@@ -4,17 +4,22 @@
 //
 //  k_contract_rows : FP32 element matrices, never stored.  A group of NB lanes
 //                    (NB = basis functions per cell) owns the d rows of one
-//                    node and walks the node's incident cells in ascending
-//                    order; for each cell, lane b forms the d x d block
-//                    K_e^0[(a,.),(b,.)] of the node's local index a by the
+//                    node and walks the node's incident cells as a chain
+//                    fixed at mesh creation (each next cell shares as many
+//                    of the lanes' current column nodes as possible); for
+//                    each cell, a lane takes one local node b and forms the
+//                    d x d block K_e^0[(a,.),(b,.)] of the node's local
+//                    index a by the
 //                    fast assembly of Sec. 3.2.2: the reference integrals
 //                    M^{kl}_{ab} = int d_k phi_a d_l phi_b (shared memory,
 //                    FP32) contracted with the cell's G = J^-1 and |det J|,
 //                        P_ij = |det J| sum_kl G_ki G_lj M^{kl}_{ab},
 //                        K_ij = lam P_ij + mu P_ji + mu delta_ij tr P,
 //                    and adds E_e K_ij into the rows' float-pair accumulators
-//                    in shared memory (FP64-accurate sums in ascending cell
-//                    order, no atomics).  The rows leave as FP64 values.
+//                    in shared memory (FP64-accurate sums in the chain's
+//                    fixed order, no atomics); a lane whose column block
+//                    continues into the next cell keeps its sums in
+//                    registers meanwhile.  The rows leave as FP64 values.
 //  k_strain_energy : s_e = u_e^T K_e^0 u_e = int_e lam (div u)^2 + 2 mu eps:eps
 //                    by a quadrature rule exact for the energy density of the
 //                    cell's order, one thread per cell: the reference
@@ -52,9 +57,9 @@ struct ContractArgs {
     int max_deg;
     const int64_t *__restrict__ node_off;
     const int32_t *__restrict__ inc_ptr;
-    const int32_t *__restrict__ inc_e;
-    const uint8_t *__restrict__ inc_a;
-    const uint16_t *__restrict__ pos;
+    const int32_t *__restrict__ inc_e;   // each node's cells in chain order
+    const uint8_t *__restrict__ inc_a;   // the node's local index in each
+    const uint16_t *__restrict__ rec;    // per (incidence, lane): local node b << 11 | column block p
     const float4 *__restrict__ cgeo;
     const float *__restrict__ Mf;
     const float2 *__restrict__ Edf;
@@ -155,10 +160,11 @@ __device__ __noinline__ void contract_node_fp64(const ContractArgs &A, const flo
         const int32_t q = q0 + t;
         const int64_t e = A.inc_e[q];
         const int a = A.inc_a[q];
-        const int p = A.pos[(int64_t)q * NB + b];
+        const uint32_t r = A.rec[(int64_t)q * NB + b];
+        const int p = (int)(r & 2047u), lb = (int)(r >> 11);
         float G[D * D], det, M[D * D], K[D][D];
         load_cgeo<D>(A.cgeo, e, G, det);
-        load_mpair<D>(Ms, a * NB + b, M);
+        load_mpair<D>(Ms, a * NB + lb, M);
         contract_block<D>(M, G, det, A.lam, A.mu, K);
         const double E = simp_E(A.sp, A.rho[e]);
 #pragma unroll
@@ -232,7 +238,7 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
             const int32_t q = min(q0 + it, qlast);
             e = __ldg(A.inc_e + q);
             a = __ldg(A.inc_a + q);
-            p = __ldg(A.pos + (int64_t)q * NB + b);
+            p = __ldg(A.rec + (int64_t)q * NB + b);
         };
         auto fetch_data = [&](int32_t e, int a, int p, Cell &c) {
             const float4 *gp = A.cgeo + (int64_t)G4 * e;
@@ -244,6 +250,10 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
         };
         const int ro1 = rowlen, ro2 = 2 * rowlen;
         bool bad = false;
+        // the lane's row sums of its current column block: read from shared memory
+        // when the block starts, written back when the next cell has another one
+        float2 v[D][D];
+        bool held = false;
         auto body = [&](const Cell &cur, Cell &nxt, int it) {
             fetch_data(e2, a2, p2, nxt);
             fetch_idx(it + 2, e2, a2, p2);
@@ -259,17 +269,21 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
                     G[0] = cur.g[0].x; G[1] = cur.g[0].y; G[2] = cur.g[0].z; G[3] = cur.g[0].w;
                     det = cur.g[1].x;
                 }
+                const int slot = cur.p & 2047, lb = cur.p >> 11;
                 float M[D * D], K[D][D];
-                load_mpair<D>(Ms, cur.a * NB + b, M);
+                load_mpair<D>(Ms, cur.a * NB + lb, M);
                 contract_block<D>(M, G, det, A.lam, A.mu, K);
-                // the lane's slots are distinct within a cell: read all, then write back
-                const int base = gacc + D * cur.p;
+                // the lane's slots are distinct within a cell, and a block held in
+                // registers is no other lane's in the next cell
+                const int base = gacc + D * slot;
                 const int rbase[3] = {base, base + ro1, base + ro2};
-                float2 v[D][D];
+                const bool keep = it + 1 < cnt && (nxt.p & 2047) == slot;
+                if (!held) {
 #pragma unroll
-                for (int i = 0; i < D; i++)
+                    for (int i = 0; i < D; i++)
 #pragma unroll
-                    for (int j = 0; j < D; j++) v[i][j] = accs[rbase[i] + j];
+                        for (int j = 0; j < D; j++) v[i][j] = accs[rbase[i] + j];
+                }
 #pragma unroll
                 for (int i = 0; i < D; i++)
 #pragma unroll
@@ -280,10 +294,13 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
                         const float pl = __fmaf_rn(cur.E.y, k, __fmaf_rn(cur.E.x, k, -ph));
                         acc_add(v[i][j].x, v[i][j].y, df{ph, pl});
                     }
+                if (!keep) {
 #pragma unroll
-                for (int i = 0; i < D; i++)
+                    for (int i = 0; i < D; i++)
 #pragma unroll
-                    for (int j = 0; j < D; j++) accs[rbase[i] + j] = v[i][j];
+                        for (int j = 0; j < D; j++) accs[rbase[i] + j] = v[i][j];
+                }
+                held = keep;
             }
             __syncwarp();
         };
@@ -308,20 +325,14 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
             const int head = (int)((reinterpret_cast<uintptr_t>(out) >> 3) & 1u);
             if (head && b == 0) {
                 const float2 v = accs[gacc];
-                float h, l;
-                two_sum(v.x, v.y, h, l);
-                __stcs(out, df_to_double(h, l));
+                __stcs(out, pair_to_double(v.x, v.y));
             }
             for (int t = head + 2 * b; t < blk; t += 2 * NB) {
                 const float2 v0 = accs[gacc + t];
-                float h0, l0;
-                two_sum(v0.x, v0.y, h0, l0);
-                const double d0 = df_to_double(h0, l0);
+                const double d0 = pair_to_double(v0.x, v0.y);
                 if (t + 1 < blk) {
                     const float2 v1 = accs[gacc + t + 1];
-                    float h1, l1;
-                    two_sum(v1.x, v1.y, h1, l1);
-                    __stcs(reinterpret_cast<double2 *>(out + t), make_double2(d0, df_to_double(h1, l1)));
+                    __stcs(reinterpret_cast<double2 *>(out + t), make_double2(d0, pair_to_double(v1.x, v1.y)));
                 } else {
                     __stcs(out + t, d0);
                 }
@@ -609,9 +620,9 @@ cudaError_t contract_launch(const soptx_mesh_s &m, const double *rho, double *va
     A.max_deg = h.max_deg;
     A.node_off = m.d.node_off;
     A.inc_ptr = m.d.inc_ptr;
-    A.inc_e = m.d.inc_e;
-    A.inc_a = m.d.inc_a;
-    A.pos = m.d.pos;
+    A.inc_e = m.d.cinc_e;
+    A.inc_a = m.d.cinc_a;
+    A.rec = m.d.crec;
     A.cgeo = m.d.cgeo;
     A.Mf = m.d.Mf;
     A.Edf = m.d.Edf;
@@ -654,7 +665,8 @@ static bool contract_layout(int dim, int nb)
 // degree) fit in a CTA's share of shared memory.
 bool contract_fits(int dim, int nb, int max_deg)
 {
-    if (!contract_layout(dim, nb)) return false;
+    // a lane record holds the local node in 5 bits and the column block in 11
+    if (!contract_layout(dim, nb) || nb > 32 || max_deg > 2048) return false;
     const size_t mbytes = (size_t)nb * nb * (dim == 3 ? 12 : 4) * sizeof(float);
     const size_t per_warp = (size_t)(32 / nb) * dim * dim * max_deg * sizeof(float2);
     const int minb = contract_minb(dim, nb);

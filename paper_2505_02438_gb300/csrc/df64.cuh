@@ -153,6 +153,28 @@ __device__ __forceinline__ double df_to_double_biased(float p, float e, uint32_t
     return __longlong_as_double((long long)bits);
 }
 
+// The exact FP64 value of a float built from its bit pattern with integer
+// operations (exponent rebias, mantissa shift): no FP64-pipe conversion.
+// Zero and denormal floats give a signed zero (an absolute error below
+// 2^-126); x must be finite.
+__device__ __forceinline__ double f32_to_f64_bits(float x)
+{
+    const uint32_t u = __float_as_uint(x), a = u & 0x7fffffffu, sign = u & 0x80000000u;
+    const bool normal = a >= 0x00800000u;
+    const uint32_t hi = normal ? (((a >> 3) + 0x38000000u) | sign) : sign;
+    const uint32_t lo = normal ? (u << 29) : 0u;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// FP64 value of an unnormalised pair s + c (finite): both halves widened
+// exactly, then one FP64 addition, so the result is s + c correctly rounded
+// (up to the flush of denormal halves).  Costs one FP64-pipe instruction and
+// about a dozen integer ones.
+__device__ __forceinline__ double pair_to_double(float s, float c)
+{
+    return __dadd_rn(f32_to_f64_bits(s), f32_to_f64_bits(c));
+}
+
 // Sum without the final renormalisation (s, e): enough when the result only
 // feeds further pair arithmetic.
 __device__ __forceinline__ df df_add_lazy(df a, df b)

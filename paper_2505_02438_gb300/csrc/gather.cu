@@ -313,9 +313,7 @@ __global__ void __launch_bounds__(kGW * 32, kGatherMinB) k_gather_nodes(const Ga
             double *out = A.vals + (int64_t)D * D * off;
             for (int t = ll; t < blk; t += GL) {
                 const float2 v = acc[t];
-                float h, l;
-                two_sum(v.x, v.y, h, l);
-                __stcs(out + t, df_to_double(h, l));
+                __stcs(out + t, pair_to_double(v.x, v.y));
             }
         }
         __syncwarp();
@@ -501,9 +499,7 @@ __global__ void __launch_bounds__(kGW * 32, MINB) k_gather_rows(const GatherArgs
             double *out = A.vals + (int64_t)D * D * off;
             for (int t = ll; t < blk; t += GL) {
                 const float2 v = acc[t];
-                float h, l;
-                two_sum(v.x, v.y, h, l);
-                __stcs(out + t, df_to_double(h, l));
+                __stcs(out + t, pair_to_double(v.x, v.y));
             }
         }
         __syncwarp();

@@ -128,6 +128,9 @@ struct DeviceMesh {
     float4 *cgeo = nullptr;        //   [nc][2 or 3] G and |det J| in FP32
     float *Mf = nullptr;           //   [nb][nb][4 or 12] reference integrals in FP32
     int32_t *corder = nullptr;     //   [nn] nodes by incident-cell count, largest first
+    int32_t *cinc_e = nullptr;     //   [ninc] each node's cells in the contraction's chain order
+    uint8_t *cinc_a = nullptr;     //   [ninc] the node's local index in those cells
+    uint16_t *crec = nullptr;      //   [ninc][nb] per lane: local node b << 11 | column block p
     // equilibrium solve (allocated by the first soptx_solve_cg)
     double *cg = nullptr;          // r z p q diag [ndof], scalars, partials, counters
     cudaGraphExec_t cg_exec = nullptr; // the CG iterations between two checks, as a graph
