@@ -35,7 +35,7 @@ static void free_device(DeviceMesh &d)
     void *ptrs[] = {d.indptr, d.indices, d.cell_node, d.node_off, d.inc_ptr, d.inc,
                     d.pos, d.geo, d.M, d.K, d.scratch, d.Edf, d.kappa, d.K0, d.sectors, d.udf, d.part,
                     d.inc_e, d.inc_a, d.counter, d.xcell, d.qw, d.qdphi, d.qdgeo, d.cg, d.lat_bad, d.stage,
-                    d.kvals, d.sgeo, d.sq, d.cgeo, d.Mf, d.corder, d.cinc_e, d.cinc_a, d.crec};
+                    d.kvals, d.sgeo, d.sq, d.cgeo, d.Mf, d.cnrec, d.cinc_e, d.cinc_a, d.crec};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (d.cg_exec) cudaGraphExecDestroy(d.cg_exec);
@@ -126,6 +126,9 @@ static soptx_status setup_contract(soptx_mesh_s &m, const RefElement &ref, cudaS
 {
     const HostMesh &h = m.h;
     const int d = h.dim, nb = h.nb, ng = d * d + 1, n4 = d == 3 ? 3 : 2, mp = d == 3 ? 12 : 4;
+    // a node record holds the incident-cell count in 16 bits: larger fans keep the cached gather
+    for (int64_t n = 0; n < h.nn; n++)
+        if (h.inc_ptr[(size_t)n + 1] - h.inc_ptr[(size_t)n] >= 65536) return SOPTX_OK;
     std::vector<float4> cg((size_t)h.nc * n4, make_float4(0.f, 0.f, 0.f, 0.f));
     for (int64_t e = 0; e < h.nc; e++) {
         float *dst = reinterpret_cast<float *>(&cg[(size_t)e * n4]);
@@ -216,7 +219,14 @@ static soptx_status setup_contract(soptx_mesh_s &m, const RefElement &ref, cudaS
     }
     soptx_status s = upload(&m.d.cgeo, cg, st, m.device_bytes, "cell geometry");
     if (s == SOPTX_OK) s = upload(&m.d.Mf, mf, st, m.device_bytes, "reference integrals (FP32)");
-    if (s == SOPTX_OK) s = upload(&m.d.corder, order, st, m.device_bytes, "node order");
+    std::vector<int4> nrec((size_t)h.nn);
+    for (int64_t i = 0; i < h.nn; i++) {
+        const int64_t n = order[(size_t)i], off = h.node_off[(size_t)n];
+        const int32_t deg = (int32_t)(h.node_off[(size_t)n + 1] - off), q0 = h.inc_ptr[(size_t)n],
+                      cnt = h.inc_ptr[(size_t)n + 1] - q0;
+        nrec[(size_t)i] = make_int4((int)(uint32_t)off, (int)(off >> 32), q0, (int)(((uint32_t)cnt << 16) | (uint32_t)deg));
+    }
+    if (s == SOPTX_OK) s = upload(&m.d.cnrec, nrec, st, m.device_bytes, "node records");
     if (s == SOPTX_OK) s = upload(&m.d.cinc_e, ce, st, m.device_bytes, "contraction cell chains");
     if (s == SOPTX_OK) s = upload(&m.d.cinc_a, ca, st, m.device_bytes, "contraction local indices");
     if (s == SOPTX_OK) s = upload(&m.d.crec, rec, st, m.device_bytes, "contraction lane records");

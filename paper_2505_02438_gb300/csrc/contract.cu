@@ -55,15 +55,13 @@ template <int D> struct MPad {
 struct ContractArgs {
     int64_t nn;
     int max_deg;
-    const int64_t *__restrict__ node_off;
-    const int32_t *__restrict__ inc_ptr;
+    const int4 *__restrict__ nrec;       // per processing position: row block offset, q0, cnt << 16 | deg
     const int32_t *__restrict__ inc_e;   // each node's cells in chain order
     const uint8_t *__restrict__ inc_a;   // the node's local index in each
     const uint16_t *__restrict__ rec;    // per (incidence, lane): local node b << 11 | column block p
     const float4 *__restrict__ cgeo;
     const float *__restrict__ Mf;
     const float2 *__restrict__ Edf;
-    const int32_t *__restrict__ order;   // nodes by incident-cell count, largest first
     const double *__restrict__ rho;
     SimpParams sp;
     float lam, mu;
@@ -197,57 +195,100 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
     const unsigned gmask = (NB == 32 ? kFull : ((1u << NB) - 1u)) << (gg * NB);
     const int acc_len = D * D * A.max_deg;
     const int gacc = (warp * NPW + gg) * acc_len;   // the group's accumulators: accs[gacc ...]
+    // Round r of the warp takes positions first + r step .. + NPW - 1 of the
+    // processing order (nodes by incident-cell count, largest first), so its
+    // groups walk about as many cells each.  A node's record is one 16-byte load.
     const int64_t step = (int64_t)gridDim.x * wpb * NPW;
-    for (int64_t n0 = ((int64_t)blockIdx.x * wpb + warp) * NPW; n0 < A.nn; n0 += step) {
-        // the warp's nodes come from the order sorted by incident-cell count, so
-        // its groups walk about as many cells each
-        const bool has = act && n0 + g < A.nn;
-        const int64_t n = has ? A.order[n0 + g] : 0;
-        int64_t off = 0;
-        int deg = 0;
-        int32_t q0 = 0, cnt = 0;
-        if (has) {
-            off = A.node_off[n];
-            deg = (int)(A.node_off[n + 1] - off);
-            q0 = A.inc_ptr[n];
-            cnt = A.inc_ptr[n + 1] - q0;
+    const int64_t first = ((int64_t)blockIdx.x * wpb + warp) * NPW;
+    struct Node {
+        int64_t off;
+        int32_t q0, cnt, deg;
+    };
+    auto load_node = [&](int64_t n0, Node &N) {
+        N = Node{0, 0, 0, 0};
+        if (act && n0 + g < A.nn) {
+            const int4 r = __ldg(A.nrec + n0 + g);
+            N.off = (int64_t)(uint32_t)r.x | ((int64_t)r.y << 32);
+            N.q0 = r.z;
+            N.cnt = (int32_t)((uint32_t)r.w >> 16);
+            N.deg = r.w & 0xffff;
         }
+    };
+    auto warp_max = [](int x) {
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) x = max(x, __shfl_xor_sync(kFull, x, o));
+        return x;
+    };
+    struct Cell {
+        float4 g[G4];
+        float2 E;
+        int a, p;
+    };
+    // The rounds' incidences form one stream: cell, a and the lane record are
+    // loaded two items ahead, geometry and modulus one ahead, across the end of
+    // a round into the next one (or the one after, when the next has a single
+    // item), so a node's first cells are in flight while the previous node's
+    // rows are written.  Position s counts from the current round's first item;
+    // a group's index past its node's last incidence is clamped to it (the item
+    // is not used), so the loads need no predicates.
+    // the round after next: only its first incidence and cell count
+    auto load_head = [&](int64_t n0, int32_t &q, int32_t &c) {
+        q = 0;
+        c = 0;
+        if (act && n0 + g < A.nn) {
+            const int2 r = __ldg(reinterpret_cast<const int2 *>(A.nrec + n0 + g) + 1);
+            q = r.x;
+            c = (int32_t)((uint32_t)r.y >> 16);
+        }
+    };
+    Node N0, N1;
+    int32_t q02, cnt2;
+    load_node(first, N0);
+    load_node(first + step, N1);
+    load_head(first + 2 * step, q02, cnt2);
+    int imax0 = warp_max(N0.cnt), imax1 = warp_max(N1.cnt);
+    auto fetch_idx = [&](int s, int32_t &e, int &a, int &p) {
+        int32_t qs = N0.q0, cs = N0.cnt;
+        int k = s;
+        if (s >= imax0) {
+            k = s - imax0;
+            if (k < imax1) {
+                qs = N1.q0;
+                cs = N1.cnt;
+            } else {
+                k -= imax1;
+                qs = q02;
+                cs = cnt2;
+            }
+        }
+        const int32_t q = qs + min(k, max(cs - 1, 0));
+        e = __ldg(A.inc_e + q);
+        a = __ldg(A.inc_a + q);
+        p = __ldg(A.rec + (int64_t)q * NB + b);
+    };
+    auto fetch_data = [&](int32_t e, int a, int p, Cell &c) {
+        const float4 *gp = A.cgeo + (int64_t)G4 * e;
+#pragma unroll
+        for (int w = 0; w < G4; w++) c.g[w] = __ldg(gp + w);
+        c.E = __ldg(A.Edf + e);
+        c.a = a;
+        c.p = p;
+    };
+    int32_t e1, e2;
+    int a1, p1, a2, p2;
+    fetch_idx(0, e1, a1, p1);
+    fetch_idx(1, e2, a2, p2);
+    Cell c0, c1;
+    fetch_data(e1, a1, p1, c0);
+    for (int64_t n0 = first; n0 < A.nn; n0 += step) {
+        const bool has = act && n0 + g < A.nn;
+        const int64_t off = N0.off;
+        const int deg = N0.deg;
+        const int32_t q0 = N0.q0, cnt = N0.cnt;
         const int rowlen = D * deg, blk = D * rowlen;
         for (int t = b; t < blk; t += NB) accs[gacc + t] = make_float2(0.f, 0.f);
-        int imax = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) imax = max(imax, __shfl_xor_sync(kFull, imax, o));
         __syncwarp();
 
-        // incidence it of the group's node: the cell's geometry and modulus, the
-        // node's local index a in it and the column block p of the lane's node b.
-        // Cell, a and p are loaded two incidences ahead, geometry and modulus one
-        // ahead, so each dependent load has a whole cell's work to arrive in.
-        // Indices past the node's last incidence are clamped to it (a group with
-        // fewer cells than the warp's longest repeats its last one unused), so the
-        // loads need no predicates.
-        const int32_t qlast = q0 + max(cnt - 1, 0);
-        struct Cell {
-            float4 g[G4];
-            float2 E;
-            int a, p;
-        };
-        int32_t e2;
-        int a2, p2;
-        auto fetch_idx = [&](int it, int32_t &e, int &a, int &p) {
-            const int32_t q = min(q0 + it, qlast);
-            e = __ldg(A.inc_e + q);
-            a = __ldg(A.inc_a + q);
-            p = __ldg(A.rec + (int64_t)q * NB + b);
-        };
-        auto fetch_data = [&](int32_t e, int a, int p, Cell &c) {
-            const float4 *gp = A.cgeo + (int64_t)G4 * e;
-#pragma unroll
-            for (int w = 0; w < G4; w++) c.g[w] = __ldg(gp + w);
-            c.E = __ldg(A.Edf + e);
-            c.a = a;
-            c.p = p;
-        };
         const int ro1 = rowlen, ro2 = 2 * rowlen;
         bool bad = false;
         // the lane's row sums of its current column block: read from shared memory
@@ -304,15 +345,15 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
             }
             __syncwarp();
         };
-        int32_t e1;
-        int a1, p1;
-        fetch_idx(0, e1, a1, p1);
-        fetch_idx(1, e2, a2, p2);
-        Cell c0, c1;
-        fetch_data(e1, a1, p1, c0);
-        for (int it = 0; it < imax; it += 2) {
+        for (int it = 0; it < imax0; it += 2) {
             body(c0, c1, it);
-            if (it + 1 < imax) body(c1, c0, it + 1);
+            if (it + 1 < imax0) body(c1, c0, it + 1);
+        }
+        if (imax0 & 1) {
+            // after an odd count the next round's first cell arrived in c1
+            const Cell t = c0;
+            c0 = c1;
+            c1 = t;
         }
         // a group whose node met an out-of-range modulus redoes it in FP64
         const unsigned badm = __ballot_sync(kFull, bad);
@@ -339,6 +380,11 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
             }
         }
         __syncwarp();
+        N0 = N1;
+        load_node(n0 + 2 * step, N1);
+        load_head(n0 + 3 * step, q02, cnt2);
+        imax0 = imax1;
+        imax1 = warp_max(N1.cnt);
     }
 }
 
@@ -618,15 +664,13 @@ cudaError_t contract_launch(const soptx_mesh_s &m, const double *rho, double *va
     ContractArgs A;
     A.nn = h.nn;
     A.max_deg = h.max_deg;
-    A.node_off = m.d.node_off;
-    A.inc_ptr = m.d.inc_ptr;
+    A.nrec = m.d.cnrec;
     A.inc_e = m.d.cinc_e;
     A.inc_a = m.d.cinc_a;
     A.rec = m.d.crec;
     A.cgeo = m.d.cgeo;
     A.Mf = m.d.Mf;
     A.Edf = m.d.Edf;
-    A.order = m.d.corder;
     A.rho = rho;
     A.sp = simp_params(m.mat);
     A.lam = (float)m.mat.lam;
@@ -643,8 +687,14 @@ cudaError_t contract_launch(const soptx_mesh_s &m, const double *rho, double *va
     auto kern = k_contract_rows<D, NB, MINB>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
+    // persistent: the CTAs that fit at once, each warp taking many rounds
+    int dev = 0, sms = 0, per_sm = 0;
+    err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpb * 32, smem);
+    if (err != cudaSuccess) return err;
     const int64_t groups = (h.nn + NPW - 1) / NPW;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((groups + wpb - 1) / wpb, 152 * 16));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((groups + wpb - 1) / wpb, (int64_t)sms * std::max(per_sm, 1)));
     kern<<<grid, wpb * 32, smem, st>>>(A);
     return cudaGetLastError();
 }

@@ -127,7 +127,8 @@ struct DeviceMesh {
     bool contract = false;         // the assembly takes k_contract_rows
     float4 *cgeo = nullptr;        //   [nc][2 or 3] G and |det J| in FP32
     float *Mf = nullptr;           //   [nb][nb][4 or 12] reference integrals in FP32
-    int32_t *corder = nullptr;     //   [nn] nodes by incident-cell count, largest first
+    int4 *cnrec = nullptr;         //   [nn] nodes by incident-cell count, largest first: row block
+                                   //   offset (2 ints), first incidence, cells << 16 | degree
     int32_t *cinc_e = nullptr;     //   [ninc] each node's cells in the contraction's chain order
     uint8_t *cinc_a = nullptr;     //   [ninc] the node's local index in those cells
     uint16_t *crec = nullptr;      //   [ninc][nb] per lane: local node b << 11 | column block p
