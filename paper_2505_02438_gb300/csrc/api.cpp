@@ -35,7 +35,7 @@ static void free_device(DeviceMesh &d)
     void *ptrs[] = {d.indptr, d.indices, d.cell_node, d.node_off, d.inc_ptr, d.inc,
                     d.pos, d.geo, d.M, d.K, d.scratch, d.Edf, d.kappa, d.K0, d.sectors, d.udf, d.part,
                     d.inc_e, d.inc_a, d.counter, d.xcell, d.qw, d.qdphi, d.qdgeo, d.cg, d.lat_bad, d.stage,
-                    d.kvals, d.sgeo, d.sq, d.cgeo, d.Mf, d.cnrec, d.cinc_e, d.cinc_a, d.crec};
+                    d.kvals, d.sgeo, d.sq, d.cgeo, d.Mf, d.cnrec, d.cinc_e, d.cinc_a, d.crec, d.cticket};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (d.cg_exec) cudaGraphExecDestroy(d.cg_exec);
@@ -230,6 +230,7 @@ static soptx_status setup_contract(soptx_mesh_s &m, const RefElement &ref, cudaS
     if (s == SOPTX_OK) s = upload(&m.d.cinc_e, ce, st, m.device_bytes, "contraction cell chains");
     if (s == SOPTX_OK) s = upload(&m.d.cinc_a, ca, st, m.device_bytes, "contraction local indices");
     if (s == SOPTX_OK) s = upload(&m.d.crec, rec, st, m.device_bytes, "contraction lane records");
+    if (s == SOPTX_OK) s = upload(&m.d.cticket, std::vector<unsigned>(2, 0u), st, m.device_bytes, "round counter");
     if (s == SOPTX_OK) m.d.contract = true;
     return s;
 }

@@ -56,6 +56,7 @@ struct ContractArgs {
     int64_t nn;
     int max_deg;
     const int4 *__restrict__ nrec;       // per processing position: row block offset, q0, cnt << 16 | deg
+    unsigned *__restrict__ ticket;       // [0] rounds handed out, [1] warps done (both zero between calls)
     const int32_t *__restrict__ inc_e;   // each node's cells in chain order
     const uint8_t *__restrict__ inc_a;   // the node's local index in each
     const uint16_t *__restrict__ rec;    // per (incidence, lane): local node b << 11 | column block p
@@ -195,11 +196,18 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
     const unsigned gmask = (NB == 32 ? kFull : ((1u << NB) - 1u)) << (gg * NB);
     const int acc_len = D * D * A.max_deg;
     const int gacc = (warp * NPW + gg) * acc_len;   // the group's accumulators: accs[gacc ...]
-    // Round r of the warp takes positions first + r step .. + NPW - 1 of the
-    // processing order (nodes by incident-cell count, largest first), so its
-    // groups walk about as many cells each.  A node's record is one 16-byte load.
-    const int64_t step = (int64_t)gridDim.x * wpb * NPW;
-    const int64_t first = ((int64_t)blockIdx.x * wpb + warp) * NPW;
+    // Round r takes positions r NPW .. r NPW + NPW - 1 of the processing order
+    // (nodes by incident-cell count, largest first), so a warp's groups walk
+    // about as many cells each.  Warps take rounds from a counter, three ahead
+    // (the prefetch below reaches two rounds past the current one), so a CTA
+    // that starts late, beside another kernel, simply takes fewer.  The last warp
+    // to finish sets the counter back to zero.  A node's record is one 16-byte load.
+    const int64_t rounds = (A.nn + NPW - 1) / NPW;
+    auto grab = [&]() -> int64_t {
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(A.ticket, 1u);
+        return (int64_t)__shfl_sync(kFull, t, 0);
+    };
     struct Node {
         int64_t off;
         int32_t q0, cnt, deg;
@@ -243,9 +251,10 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
     };
     Node N0, N1;
     int32_t q02, cnt2;
-    load_node(first, N0);
-    load_node(first + step, N1);
-    load_head(first + 2 * step, q02, cnt2);
+    int64_t r0 = grab(), r1 = grab(), r2 = grab();
+    load_node(r0 * NPW, N0);
+    load_node(r1 * NPW, N1);
+    load_head(r2 * NPW, q02, cnt2);
     int imax0 = warp_max(N0.cnt), imax1 = warp_max(N1.cnt);
     auto fetch_idx = [&](int s, int32_t &e, int &a, int &p) {
         int32_t qs = N0.q0, cs = N0.cnt;
@@ -280,7 +289,8 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
     fetch_idx(1, e2, a2, p2);
     Cell c0, c1;
     fetch_data(e1, a1, p1, c0);
-    for (int64_t n0 = first; n0 < A.nn; n0 += step) {
+    while (r0 < rounds) {
+        const int64_t n0 = r0 * NPW;
         const bool has = act && n0 + g < A.nn;
         const int64_t off = N0.off;
         const int deg = N0.deg;
@@ -380,11 +390,21 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
             }
         }
         __syncwarp();
+        r0 = r1;
+        r1 = r2;
+        r2 = grab();
         N0 = N1;
-        load_node(n0 + 2 * step, N1);
-        load_head(n0 + 3 * step, q02, cnt2);
+        load_node(r1 * NPW, N1);
+        load_head(r2 * NPW, q02, cnt2);
         imax0 = imax1;
         imax1 = warp_max(N1.cnt);
+    }
+    if (lane == 0) {
+        __threadfence();
+        if (atomicAdd(A.ticket + 1, 1u) == gridDim.x * (unsigned)wpb - 1u) {
+            A.ticket[0] = 0u;
+            A.ticket[1] = 0u;
+        }
     }
 }
 
@@ -665,6 +685,7 @@ cudaError_t contract_launch(const soptx_mesh_s &m, const double *rho, double *va
     A.nn = h.nn;
     A.max_deg = h.max_deg;
     A.nrec = m.d.cnrec;
+    A.ticket = m.d.cticket;
     A.inc_e = m.d.cinc_e;
     A.inc_a = m.d.cinc_a;
     A.rec = m.d.crec;
