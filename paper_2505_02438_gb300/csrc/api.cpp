@@ -156,7 +156,9 @@ static soptx_status setup_contract(soptx_mesh_s &m, const RefElement &ref, cudaS
     // a lane keeps its node when the next cell has it, and the cell's other nodes
     // go to the free lanes in local order.  A lane whose column block continues
     // into the next cell keeps its row sums in registers instead of a round trip
-    // through shared memory.  Per (incidence, lane): local node b << 11 | block p.
+    // through shared memory.  Per (incidence, lane): column block p (bits 0-8),
+    // local node b (bits 9-13), and whether this is the first (bit 14) or the last
+    // (bit 15) time the node's chain meets that block.
     const int64_t ninc = h.inc_ptr[(size_t)h.nn];
     std::vector<int32_t> ce((size_t)ninc);
     std::vector<uint8_t> ca((size_t)ninc);
@@ -165,7 +167,7 @@ static soptx_status setup_contract(soptx_mesh_s &m, const RefElement &ref, cudaS
         std::vector<int64_t> lane_mark((size_t)h.nn, -1), cell_mark((size_t)h.nn, -1);
         std::vector<int32_t> cell_loc((size_t)h.nn, 0);
         std::vector<int32_t> lanes(nb), next(nb);
-        std::vector<char> used, taken(nb);
+        std::vector<char> used, taken(nb), seen;
         int64_t stamp = 0;
         for (int64_t n = 0; n < h.nn; n++) {
             const int32_t q0 = h.inc_ptr[(size_t)n], cnt = h.inc_ptr[(size_t)n + 1] - q0;
@@ -212,9 +214,23 @@ static soptx_status setup_contract(soptx_mesh_s &m, const RefElement &ref, cudaS
                 ca[(size_t)qn] = h.inc_a[(size_t)qo];
                 for (int L = 0; L < nb; L++) {
                     lanes[L] = cn[next[L]];
-                    rec[(size_t)qn * nb + L] = (uint16_t)((next[L] << 11) | h.pos[(size_t)qo * nb + next[L]]);
+                    rec[(size_t)qn * nb + L] = (uint16_t)((next[L] << 9) | h.pos[(size_t)qo * nb + next[L]]);
                 }
             }
+            // first and last meeting of each column block along the chain
+            const int deg = (int)(h.node_off[(size_t)n + 1] - h.node_off[(size_t)n]);
+            seen.assign((size_t)deg, 0);
+            for (int64_t qn = q0; qn < q0 + cnt; qn++)
+                for (int L = 0; L < nb; L++) {
+                    uint16_t &r = rec[(size_t)qn * nb + L];
+                    if (!seen[r & 511u]) { seen[r & 511u] = 1; r = (uint16_t)(r | 0x4000u); }
+                }
+            seen.assign((size_t)deg, 0);
+            for (int64_t qn = q0 + cnt - 1; qn >= q0; qn--)
+                for (int L = 0; L < nb; L++) {
+                    uint16_t &r = rec[(size_t)qn * nb + L];
+                    if (!seen[r & 511u]) { seen[r & 511u] = 1; r = (uint16_t)(r | 0x8000u); }
+                }
         }
     }
     soptx_status s = upload(&m.d.cgeo, cg, st, m.device_bytes, "cell geometry");

@@ -59,7 +59,8 @@ struct ContractArgs {
     unsigned *__restrict__ ticket;       // [0] rounds handed out, [1] warps done (both zero between calls)
     const int32_t *__restrict__ inc_e;   // each node's cells in chain order
     const uint8_t *__restrict__ inc_a;   // the node's local index in each
-    const uint16_t *__restrict__ rec;    // per (incidence, lane): local node b << 11 | column block p
+    const uint16_t *__restrict__ rec;    // per (incidence, lane): column block p (bits 0-8), local node b
+                                         // (9-13), first (14) / last (15) meeting of the block
     const float4 *__restrict__ cgeo;
     const float *__restrict__ Mf;
     const float2 *__restrict__ Edf;
@@ -160,7 +161,7 @@ __device__ __noinline__ void contract_node_fp64(const ContractArgs &A, const flo
         const int64_t e = A.inc_e[q];
         const int a = A.inc_a[q];
         const uint32_t r = A.rec[(int64_t)q * NB + b];
-        const int p = (int)(r & 2047u), lb = (int)(r >> 11);
+        const int p = (int)(r & 511u), lb = (int)((r >> 9) & 31u);
         float G[D * D], det, M[D * D], K[D][D];
         load_cgeo<D>(A.cgeo, e, G, det);
         load_mpair<D>(Ms, a * NB + lb, M);
@@ -203,6 +204,7 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
     // that starts late, beside another kernel, simply takes fewer.  The last warp
     // to finish sets the counter back to zero.  A node's record is one 16-byte load.
     const int64_t rounds = (A.nn + NPW - 1) / NPW;
+    const bool aligned16 = (reinterpret_cast<uintptr_t>(A.vals) & 15u) == 0;
     auto grab = [&]() -> int64_t {
         unsigned t = 0;
         if (lane == 0) t = atomicAdd(A.ticket, 1u);
@@ -295,9 +297,19 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
         const int64_t off = N0.off;
         const int deg = N0.deg;
         const int32_t q0 = N0.q0, cnt = N0.cnt;
+        // 3D: no zeroing, every block of the rows is met by some cell and its first
+        // meeting starts the sums from zero; 2D (few rows, a tight register budget)
+        // zeroes the rows first
+        constexpr bool kFirst = D == 3;
+        // 2D: a block's last meeting converts it and stores it straight to the rows
+        // (few contributions per value there), so there is no output pass
+        constexpr bool kDirect = D == 2;
+        double *const out = A.vals + (int64_t)D * D * off;
         const int rowlen = D * deg, blk = D * rowlen;
-        for (int t = b; t < blk; t += NB) accs[gacc + t] = make_float2(0.f, 0.f);
-        __syncwarp();
+        if (!kFirst) {
+            for (int t = b; t < blk; t += NB) accs[gacc + t] = make_float2(0.f, 0.f);
+            __syncwarp();
+        }
 
         const int ro1 = rowlen, ro2 = 2 * rowlen;
         bool bad = false;
@@ -320,7 +332,7 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
                     G[0] = cur.g[0].x; G[1] = cur.g[0].y; G[2] = cur.g[0].z; G[3] = cur.g[0].w;
                     det = cur.g[1].x;
                 }
-                const int slot = cur.p & 2047, lb = cur.p >> 11;
+                const int slot = cur.p & 511, lb = (cur.p >> 9) & 31;
                 float M[D * D], K[D][D];
                 load_mpair<D>(Ms, cur.a * NB + lb, M);
                 contract_block<D>(M, G, det, A.lam, A.mu, K);
@@ -328,12 +340,19 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
                 // registers is no other lane's in the next cell
                 const int base = gacc + D * slot;
                 const int rbase[3] = {base, base + ro1, base + ro2};
-                const bool keep = it + 1 < cnt && (nxt.p & 2047) == slot;
+                const bool keep = it + 1 < cnt && (nxt.p & 511) == slot;
                 if (!held) {
+                    if (kFirst && (cur.p & 0x4000)) {
 #pragma unroll
-                    for (int i = 0; i < D; i++)
+                        for (int i = 0; i < D; i++)
 #pragma unroll
-                        for (int j = 0; j < D; j++) v[i][j] = accs[rbase[i] + j];
+                            for (int j = 0; j < D; j++) v[i][j] = make_float2(0.f, 0.f);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < D; i++)
+#pragma unroll
+                            for (int j = 0; j < D; j++) v[i][j] = accs[rbase[i] + j];
+                    }
                 }
 #pragma unroll
                 for (int i = 0; i < D; i++)
@@ -346,10 +365,25 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
                         acc_add(v[i][j].x, v[i][j].y, df{ph, pl});
                     }
                 if (!keep) {
+                    if (kDirect && (cur.p & 0x8000)) {
 #pragma unroll
-                    for (int i = 0; i < D; i++)
+                        for (int i = 0; i < D; i++) {
+                            double *o = out + (int64_t)i * rowlen + D * slot;
+                            const double d0 = pair_to_double(v[i][0].x, v[i][0].y);
+                            const double d1 = pair_to_double(v[i][1].x, v[i][1].y);
+                            if (aligned16) {
+                                __stcs(reinterpret_cast<double2 *>(o), make_double2(d0, d1));
+                            } else {
+                                __stcs(o, d0);
+                                __stcs(o + 1, d1);
+                            }
+                        }
+                    } else {
 #pragma unroll
-                        for (int j = 0; j < D; j++) accs[rbase[i] + j] = v[i][j];
+                        for (int i = 0; i < D; i++)
+#pragma unroll
+                            for (int j = 0; j < D; j++) accs[rbase[i] + j] = v[i][j];
+                    }
                 }
                 held = keep;
             }
@@ -369,10 +403,9 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
         const unsigned badm = __ballot_sync(kFull, bad);
         if (has && (badm & gmask)) {
             contract_node_fp64<D, NB>(A, Ms, gmask, b, off, deg, q0, cnt, reinterpret_cast<double *>(accs + gacc));
-        } else if (has) {
+        } else if (has && !kDirect) {
             // the rows leave as FP64 values, two per store where the destination is
             // 16-byte aligned (an odd 8-byte head is stored on its own)
-            double *out = A.vals + (int64_t)D * D * off;
             const int head = (int)((reinterpret_cast<uintptr_t>(out) >> 3) & 1u);
             if (head && b == 0) {
                 const float2 v = accs[gacc];
@@ -736,8 +769,8 @@ static bool contract_layout(int dim, int nb)
 // degree) fit in a CTA's share of shared memory.
 bool contract_fits(int dim, int nb, int max_deg)
 {
-    // a lane record holds the local node in 5 bits and the column block in 11
-    if (!contract_layout(dim, nb) || nb > 32 || max_deg > 2048) return false;
+    // a lane record holds the column block in 9 bits and the local node in 5
+    if (!contract_layout(dim, nb) || nb > 32 || max_deg > 512) return false;
     const size_t mbytes = (size_t)nb * nb * (dim == 3 ? 12 : 4) * sizeof(float);
     const size_t per_warp = (size_t)(32 / nb) * dim * dim * max_deg * sizeof(float2);
     const int minb = contract_minb(dim, nb);

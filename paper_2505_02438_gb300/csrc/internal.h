@@ -131,7 +131,7 @@ struct DeviceMesh {
                                    //   offset (2 ints), first incidence, cells << 16 | degree
     int32_t *cinc_e = nullptr;     //   [ninc] each node's cells in the contraction's chain order
     uint8_t *cinc_a = nullptr;     //   [ninc] the node's local index in those cells
-    uint16_t *crec = nullptr;      //   [ninc][nb] per lane: local node b << 11 | column block p
+    uint16_t *crec = nullptr;      //   [ninc][nb] per lane: block p, local node b << 9, first/last flags
     unsigned *cticket = nullptr;   //   [2] round counter and finished warps (zero between calls)
     // equilibrium solve (allocated by the first soptx_solve_cg)
     double *cg = nullptr;          // r z p q diag [ndof], scalars, partials, counters
