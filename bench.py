@@ -270,7 +270,7 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def serve_stream(n_jobs, iters, fracs, local_rank):
+def serve_stream(n_jobs, iters, fracs, local_rank, jobs=None, group_small=True):
     """n_jobs design jobs x iters assemble + sensitivity requests through the
     continuous-batching server.  Every job's mesh is made resident first (its
     setup timed apart); then a closed loop (all requests submitted at once)
@@ -284,8 +284,10 @@ def serve_stream(n_jobs, iters, fracs, local_rank):
     from paper_2505_02438_gb300.serve import Server, overlap
 
     dev = torch.device("cuda", local_rank)
-    jobs = W.serving_stream(n_jobs=n_jobs, iters=iters)
-    srv = Server(hbm_cap_bytes=120 << 30, max_slots=16, n_streams=8, max_queue=4096, device=local_rank)
+    if jobs is None:
+        jobs = W.serving_stream(n_jobs=n_jobs, iters=iters)
+    srv = Server(hbm_cap_bytes=120 << 30, max_slots=16, n_streams=8, max_queue=4096, device=local_rank,
+                 group_small=group_small)
     inputs, outs = {}, {}
     for j in jobs:
         wl = j["workload"]
@@ -357,7 +359,7 @@ def serve_stream(n_jobs, iters, fracs, local_rank):
             "closed_loop": {"requests_per_s": R, "gnnz_per_s": total_nnz / closed_s / 1e9, "wall_s": closed_s,
                             "overlap": closed_overlap},
             "open_loop": loads, "mesh_setup_s": setup_s, "peak_resident_gb": st["peak_resident_bytes"] / 1e9,
-            "evictions": st["evictions"], "total_nnz": total_nnz}
+            "evictions": st["evictions"], "total_nnz": total_nnz, "grouped_launches": st["groups"]}
 
 
 def run_serve(args, rank, world, local_rank):
@@ -382,6 +384,33 @@ def run_serve(args, rank, world, local_rank):
                        "families": sv["families"], "hbm_cap_gb": 120, "max_slots": 16, "n_streams": 8,
                        "fp32_jobs": sv["fp32_jobs"]},
             "serving": sv}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve_small(args, rank, world, local_rank):
+    """Many small design jobs (256 Q4 boxes of 16 x 16 .. 64 x 64 cells x 4
+    iterations = 1024 requests), with the grouped launch of small lattice
+    requests and without it."""
+    import torch
+    from paper_2505_02438_gb300 import build as B
+    from paper_2505_02438_gb300 import workloads as W
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local_rank)
+    B.build_library()
+    runs = {}
+    for grouped in (True, False):
+        sv = serve_stream(256, 4, (0.7,), local_rank, jobs=W.small_serving_stream(256), group_small=grouped)
+        runs["grouped" if grouped else "one_launch_per_request"] = sv
+    g = runs["grouped"]
+    line = {"metric": "served requests/s (closed loop), p50/p99 ms at 0.7 R", "value": g["closed_loop"]["requests_per_s"],
+            "unit": "requests/s", "n_gpus": 1, "steps": g["requests"], "warmup": g["jobs"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "small-request serving stream: 256 design jobs x 4 iterations = 1024 requests, "
+                                   "Q4 boxes 16x16 .. 64x64 cells (log-uniform sides), FP64, Poisson arrivals",
+                       "hbm_cap_gb": 120, "max_slots": 16, "n_streams": 8},
+            "serving": runs}
     print(json.dumps(line), flush=True)
 
 
@@ -889,7 +918,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="hex", choices=sorted(WORKLOAD_DESC) + ["serve", "solve", "to", "rates"])
+    ap.add_argument("--workload", default="hex",
+                    choices=sorted(WORKLOAD_DESC) + ["serve", "serve_small", "solve", "to", "rates"])
     ap.add_argument("--elem-prec", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the records of the other configurations")
@@ -909,6 +939,9 @@ def main():
         return
     if args.workload == "serve":
         run_serve(args, rank, world, local_rank)
+        return
+    if args.workload == "serve_small":
+        run_serve_small(args, rank, world, local_rank)
         return
     if args.workload == "solve":
         run_solve(args, rank, world, local_rank)

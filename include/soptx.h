@@ -190,6 +190,29 @@ soptx_status soptx_assemble_and_sensitivity(soptx_mesh mesh, const double *d_rho
                                             double *d_dc, double *d_c, void *stream);
 
 /*
+ * The one-call step (Sec. 2.2, Appendix D) for a group of n distinct meshes,
+ * one launch serving many small ones: per k the arguments and results of
+ * soptx_assemble_and_sensitivity(meshes[k], d_rho[k], d_u[k], d_vals[k],
+ * d_dc[k], d_c[k], stream).  2D box lattices of up to 4096 cells (Q4 up to
+ * 64 x 64) share one kernel launch per 32 meshes, a cluster of 8 CTAs each
+ * (one for the moduli, the assembly and the sensitivities in turn); the other
+ * meshes get the ordinary call on the same stream.  K and dc are bitwise the
+ * values of the ordinary call; c is summed in another fixed order (the CTA's
+ * own), so it may differ from the ordinary call's in the last bits.
+ *   n      : number of meshes (0 does nothing)
+ *   arrays : host arrays of n entries (device pointers inside); d_c[k] may be
+ *            NULL, the others as in soptx_assemble_and_sensitivity
+ * Errors: SOPTX_EINVAL (a NULL array or entry, a mesh listed twice, n < 0)
+ * before anything is launched; SOPTX_ECUDA from a launch.  No mesh of the
+ * group may have work in flight on another stream.
+ */
+soptx_status soptx_assemble_and_sensitivity_group(int32_t n, const soptx_mesh *meshes,
+                                                  const double *const *d_rho,
+                                                  const double *const *d_u,
+                                                  double *const *d_vals, double *const *d_dc,
+                                                  double *const *d_c, void *stream);
+
+/*
  * The per-iteration step from host memory: the results of
  * soptx_assemble_and_sensitivity (Sec. 2.2 and Appendix D) with rho and u
  * read from, and dc and c written to, host buffers.

@@ -35,6 +35,12 @@ typedef struct {
     int32_t n_streams;       /* stream pool size (>= 1)                       */
     int32_t max_queue;       /* pending requests accepted before SOPTX_EBUSY  */
     int32_t device;          /* CUDA device ordinal the server runs on        */
+    int32_t group_small;     /* 1: requests on small 2D box lattices (see
+                              * soptx_assemble_and_sensitivity_group) are
+                              * launched together, one kernel for all of
+                              * them that are admitted in one scheduler pass;
+                              * such a job's requests always take that kernel
+                              * and start once its previous one completed  */
 } soptx_server_opts;
 
 /*
@@ -82,6 +88,7 @@ typedef struct {
     int64_t submitted, completed, failed, evictions, mesh_setups;
     int64_t resident_bytes, peak_resident_bytes;
     int32_t resident_meshes, in_flight, queued;
+    int64_t groups;          /* grouped launches of small lattice requests */
 } soptx_server_stats;
 
 /* Starts the scheduler thread.  Errors: EINVAL (bad options), ECUDA. */

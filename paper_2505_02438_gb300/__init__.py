@@ -9,7 +9,7 @@ from . import workloads  # noqa: F401
 
 
 def __getattr__(name):
-    if name in ("Mesh", "version", "host_plan"):
+    if name in ("Mesh", "version", "host_plan", "step_group"):
         from . import api
         return getattr(api, name)
     if name == "Compliance":

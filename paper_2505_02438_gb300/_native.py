@@ -43,7 +43,7 @@ class OcOpts(ctypes.Structure):
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("hbm_cap_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int32), ("n_streams", ctypes.c_int32),
-                ("max_queue", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("max_queue", ctypes.c_int32), ("device", ctypes.c_int32), ("group_small", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -64,7 +64,7 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("evictions", ctypes.c_int64), ("mesh_setups", ctypes.c_int64), ("resident_bytes", ctypes.c_int64),
                 ("peak_resident_bytes", ctypes.c_int64), ("resident_meshes", ctypes.c_int32),
-                ("in_flight", ctypes.c_int32), ("queued", ctypes.c_int32)]
+                ("in_flight", ctypes.c_int32), ("queued", ctypes.c_int32), ("groups", ctypes.c_int64)]
 
 
 class PipeRates(ctypes.Structure):
@@ -85,6 +85,7 @@ SIGNATURES = {
     "soptx_assemble_K": (i32, [P, P, P, P]),
     "soptx_sensitivity": (i32, [P, P, P, P, P, P]),
     "soptx_assemble_and_sensitivity": (i32, [P, P, P, P, P, P, P]),
+    "soptx_assemble_and_sensitivity_group": (i32, [i32, P, P, P, P, P, P, P]),
     "soptx_step_host": (i32, [P, P, P, P, P, P, P]),
     "soptx_compliance_vjp": (i32, [P, P, P, P, P, P, P]),
     "soptx_mesh_destroy": (i32, [P]),

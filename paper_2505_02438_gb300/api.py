@@ -198,6 +198,32 @@ class Mesh:
         return u, dict(iterations=res.iterations, converged=bool(res.converged), rel_residual=res.rel_residual)
 
 
+def step_group(meshes, rhos, us, stream=None):
+    """The one-call step for several distinct meshes (soptx_assemble_and_sensitivity_group):
+    small 2D box lattices share one kernel launch, the others get the ordinary
+    call on the same stream.  Returns [(vals, dc, c)] in order, bitwise the
+    results of each mesh's own step."""
+    n = len(meshes)
+    if not (len(rhos) == n and len(us) == n):
+        raise ValueError("meshes, rhos and us must have the same length")
+    outs = []
+    P = ctypes.c_void_p * max(n, 1)
+    hm, pr, pu, pv, pd, pc = P(), P(), P(), P(), P(), P()
+    for k, (m, rho, u) in enumerate(zip(meshes, rhos, us)):
+        vals = torch.empty(m.nnz, dtype=torch.float64, device=m.device)
+        dc = torch.empty(m.n_cells, dtype=torch.float64, device=m.device)
+        c = torch.empty(1, dtype=torch.float64, device=m.device)
+        hm[k] = m._h.value
+        pr[k] = _dptr(rho, torch.float64, m.n_cells, "rho").value
+        pu[k] = _dptr(u, torch.float64, m.ndof, "u").value
+        pv[k] = _dptr(vals, torch.float64, m.nnz, "vals").value
+        pd[k] = _dptr(dc, torch.float64, m.n_cells, "dc").value
+        pc[k] = _dptr(c, torch.float64, 1, "c").value
+        outs.append((vals, dc, c))
+    N.check(N.lib().soptx_assemble_and_sensitivity_group(n, hm, pr, pu, pv, pd, pc, _stream(stream)))
+    return outs
+
+
 def version():
     return N.lib().soptx_version().decode()
 

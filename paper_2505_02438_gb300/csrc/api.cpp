@@ -618,6 +618,44 @@ soptx_status soptx_assemble_and_sensitivity(soptx_mesh m, const double *d_rho, c
                        "soptx_assemble_and_sensitivity");
 }
 
+soptx_status soptx_assemble_and_sensitivity_group(int32_t n, const soptx_mesh *meshes, const double *const *d_rho,
+                                                  const double *const *d_u, double *const *d_vals,
+                                                  double *const *d_dc, double *const *d_c, void *stream)
+{
+    if (n < 0) SOPTX_FAIL(SOPTX_EINVAL, "n must be >= 0");
+    if (n == 0) return SOPTX_OK;
+    if (!meshes || !d_rho || !d_u || !d_vals || !d_dc || !d_c) SOPTX_FAIL(SOPTX_EINVAL, "an argument array is NULL");
+    std::vector<const soptx_mesh_s *> grp;
+    std::vector<const double *> gr, gu;
+    std::vector<double *> gv, gd, gc;
+    for (int32_t k = 0; k < n; k++) {
+        soptx_mesh m = meshes[k];
+        if (!m) SOPTX_FAIL(SOPTX_EINVAL, "mesh is NULL");
+        for (int32_t k2 = 0; k2 < k; k2++)
+            if (meshes[k2] == m) SOPTX_FAIL(SOPTX_EINVAL, "a mesh appears twice in the group");
+        if ((!d_vals[k] && m->h.nnz > 0) || (m->h.nc > 0 && (!d_rho[k] || !d_u[k] || !d_dc[k])))
+            SOPTX_FAIL(SOPTX_EINVAL, "d_rho / d_u / d_vals / d_dc is NULL");
+    }
+    for (int32_t k = 0; k < n; k++) {
+        soptx_mesh m = meshes[k];
+        if (lattice_groupable(*m)) {
+            grp.push_back(m);
+            gr.push_back(d_rho[k]);
+            gu.push_back(d_u[k]);
+            gv.push_back(d_vals[k]);
+            gd.push_back(d_dc[k]);
+            gc.push_back(d_c[k]);
+            continue;
+        }
+        soptx_status s = soptx_assemble_and_sensitivity(m, d_rho[k], d_u[k], d_vals[k], d_dc[k], d_c[k], stream);
+        if (s != SOPTX_OK) return s;
+    }
+    if (grp.empty()) return SOPTX_OK;
+    return cuda_status(launch_lattice_group(grp.data(), gr.data(), gu.data(), gv.data(), gd.data(), gc.data(),
+                                            (int)grp.size(), (cudaStream_t)stream),
+                       "soptx_assemble_and_sensitivity_group");
+}
+
 soptx_status soptx_step_host(soptx_mesh m, const double *h_rho, const double *h_u, double *d_vals, double *h_dc,
                              double *h_c, void *stream)
 {

@@ -113,13 +113,15 @@ __host__ __device__ constexpr bool sector_zero(int c, int i, int j)
     return (c ^ (1 << i)) == 0 || (c ^ (1 << j)) == 0 || (i != j && ((c >> i) & 1) != ((c >> j) & 1));
 }
 
-// Sum of `mine` over the grid into *c, deterministically: each block writes its
+// Sum of `mine` over blocks 0 .. nblk - 1 (the grid, or the blocks one request
+// has in a grouped launch) into *c, deterministically: each block writes its
 // partial (a fixed-order butterfly per warp, then the warps in order), the last block to finish (an
 // atomic ticket on *counter) adds all partials in index order and resets the
 // ticket for the next call.  blockDim.x must be a power of two <= 256, and
 // calls that share `partial` / `counter` must not overlap on the device.
-__device__ __forceinline__ void grid_sum_last_block(double mine, double *__restrict__ partial,
-                                                    unsigned *__restrict__ counter, double *__restrict__ c)
+__device__ __forceinline__ void grid_sum_last_block_n(double mine, double *__restrict__ partial,
+                                                      unsigned *__restrict__ counter, double *__restrict__ c,
+                                                      unsigned bid, unsigned nblk)
 {
     __shared__ double red[256];
     __shared__ bool last;
@@ -131,15 +133,15 @@ __device__ __forceinline__ void grid_sum_last_block(double mine, double *__restr
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < nw; w++) t += red[w];
-        partial[blockIdx.x] = t;
+        partial[bid] = t;
         __threadfence();
-        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+        last = atomicAdd(counter, 1u) == nblk - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
     double t = 0.0;
-    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) t += __ldcg(partial + i);
+    for (int i = threadIdx.x; i < (int)nblk; i += blockDim.x) t += __ldcg(partial + i);
     red[threadIdx.x] = t;
     __syncthreads();
     for (int w = blockDim.x / 2; w > 0; w >>= 1) {
@@ -150,6 +152,13 @@ __device__ __forceinline__ void grid_sum_last_block(double mine, double *__restr
         *c = red[0];
         *counter = 0u;
     }
+}
+
+// The same over the launch's own grid.
+__device__ __forceinline__ void grid_sum_last_block(double mine, double *__restrict__ partial,
+                                                    unsigned *__restrict__ counter, double *__restrict__ c)
+{
+    grid_sum_last_block_n(mine, partial, counter, c, blockIdx.x, gridDim.x);
 }
 
 // Element-matrix entries: float pairs (FP64 element matrices, value h + l) or

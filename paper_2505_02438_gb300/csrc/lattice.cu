@@ -227,31 +227,31 @@ __device__ __forceinline__ float2 load_corner_pair(const float2 *__restrict__ Ed
 #ifndef SOPTX_SIMP_MINB
 #define SOPTX_SIMP_MINB 8
 #endif
-__global__ void __launch_bounds__(256, SOPTX_SIMP_MINB)
-k_simp_df(int dim, int nx, int ny, int nz, int64_t nc, const double *__restrict__ rho, SimpParams sp,
-                          float2 *__restrict__ Edf, const int64_t *__restrict__ node_off,
-                          const double *__restrict__ K0, double *__restrict__ vals, unsigned *__restrict__ flag,
-                          unsigned gen, int64_t ndof, const double *__restrict__ u, float2 *__restrict__ udf)
+__device__ __forceinline__ void simp_df_body(int dim, int nx, int ny, int nz, int64_t nc, const double *__restrict__ rho,
+                                             SimpParams sp, float2 *__restrict__ Edf,
+                                             const int64_t *__restrict__ node_off, const double *__restrict__ K0,
+                                             double *__restrict__ vals, unsigned *__restrict__ flag, unsigned gen,
+                                             int64_t ndof, const double *__restrict__ u, float2 *__restrict__ udf,
+                                             int64_t bid, int64_t nblk)
 {
-    grid_dep_launch();   // the assembly may be scheduled now; it waits for this kernel before reading
     const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t stride = nblk * blockDim.x;
     // with u given (one call doing both passes), u as float pairs for the sensitivity
     // kernel, two dofs per thread and pass (16-byte loads and stores when u allows)
     if (u) {
         const bool vec = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(udf)) & 15u) == 0u;
         const int64_t npair = vec ? ndof / 2 : 0;
-        for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < npair; r += stride) {
+        for (int64_t r = bid * blockDim.x + threadIdx.x; r < npair; r += stride) {
             const double2 x = __ldcs(reinterpret_cast<const double2 *>(u) + r);
             const df a = df_split(x.x), b = df_split(x.y);
             reinterpret_cast<float4 *>(udf)[r] = make_float4(a.h, a.l, b.h, b.l);
         }
-        for (int64_t r = 2 * npair + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < ndof; r += stride) {
+        for (int64_t r = 2 * npair + bid * blockDim.x + threadIdx.x; r < ndof; r += stride) {
             const df v = df_split(u[r]);
             udf[r] = make_float2(v.h, v.l);
         }
     }
-    for (int64_t e0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); e0 < nc; e0 += stride) {
+    for (int64_t e0 = bid * blockDim.x + (threadIdx.x & ~31); e0 < nc; e0 += stride) {
         const int64_t e = e0 + lane;
         bool isbad = false;
         if (e < nc) {
@@ -301,6 +301,16 @@ k_simp_df(int dim, int nx, int ny, int nz, int64_t nc, const double *__restrict_
             }
         }
     }
+}
+
+__global__ void __launch_bounds__(256, SOPTX_SIMP_MINB)
+k_simp_df(int dim, int nx, int ny, int nz, int64_t nc, const double *__restrict__ rho, SimpParams sp,
+          float2 *__restrict__ Edf, const int64_t *__restrict__ node_off, const double *__restrict__ K0,
+          double *__restrict__ vals, unsigned *__restrict__ flag, unsigned gen, int64_t ndof,
+          const double *__restrict__ u, float2 *__restrict__ udf)
+{
+    grid_dep_launch();   // the assembly may be scheduled now; it waits for this kernel before reading
+    simp_df_body(dim, nx, ny, nz, nc, rho, sp, Edf, node_off, K0, vals, flag, gen, ndof, u, udf, blockIdx.x, gridDim.x);
 }
 
 // 3D assembly, two nodes at a time (n, n+1 of a chunk): one corner load, one X
@@ -487,23 +497,28 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, int chunk, const int64_t
 // coalesced.  Nodes next to an out-of-range modulus were written by k_simp_df
 // and are skipped.
 // The corner moduli of the node of lane 9g + c (c < 4) at lattice index (ix, iy).
+// NC: the moduli were written by an earlier launch (read-only path); otherwise
+// by this kernel, before a barrier (coherent loads).
+template <bool NC>
 __device__ __forceinline__ float2 corner2(const float2 *__restrict__ Edf, int ix, int iy, int cl, bool live, int nx,
                                           int ny)
 {
     float2 v = make_float2(0.f, 0.f);
     if (live && cl < 4) {
         const int ex = ix - 1 + (cl & 1), ey = iy - 1 + (cl >> 1);
-        if (ex >= 0 && ex < nx && ey >= 0 && ey < ny) v = __ldg(&Edf[(int64_t)ey * nx + ex]);
+        if (ex >= 0 && ex < nx && ey >= 0 && ey < ny)
+            v = NC ? __ldg(&Edf[(int64_t)ey * nx + ex]) : __ldcg(&Edf[(int64_t)ey * nx + ex]);
     }
     return v;
 }
 
-template <int WPB>
-__global__ void __launch_bounds__(WPB * 32)
-k_lattice_assemble2(int nx, int ny, int64_t nn, int chunk, const int64_t *__restrict__ node_off,
-                    const float2 *__restrict__ Edf, const float2 *__restrict__ kappa_g,
-                    double *__restrict__ vals, const unsigned *__restrict__ flag, unsigned gen, uint32_t pbias,
-                    double kscale)
+template <int WPB, bool NC>
+__device__ __forceinline__ void lattice_assemble2_body(int nx, int ny, int64_t nn, int chunk,
+                                                       const int64_t *__restrict__ node_off,
+                                                       const float2 *__restrict__ Edf,
+                                                       const float2 *__restrict__ kappa_g, double *__restrict__ vals,
+                                                       const unsigned *__restrict__ flag, unsigned gen, uint32_t pbias,
+                                                       double kscale, int64_t bid, int64_t nblk)
 {
     __shared__ double stage_s[WPB][3 * 9 * 4];   // three nodes' rows
     const int lane = threadIdx.x & 31;
@@ -527,13 +542,13 @@ k_lattice_assemble2(int nx, int ny, int64_t nn, int chunk, const int64_t *__rest
     const bool anybad = __ldcg(flag) == gen;
     double *stage = stage_s[threadIdx.x >> 5];
     const int64_t nchunks = (nn + chunk - 1) / chunk;
-    const int64_t warps = (int64_t)gridDim.x * WPB;
-    for (int64_t ch = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5); ch < nchunks; ch += warps) {
+    const int64_t warps = nblk * WPB;
+    for (int64_t ch = bid * WPB + (threadIdx.x >> 5); ch < nchunks; ch += warps) {
         const int64_t nb = ch * chunk, ne = min(nb + (int64_t)chunk, nn);
         int ix = (int)((nb + g) % (nx + 1)), iy = (int)((nb + g) / (nx + 1));
         int64_t vbase = 4 * node_off[nb];
         // node g's corner moduli from lanes 9g .. 9g+3, fetched one pass ahead
-        float2 vn = corner2(Edf, ix, iy, cl, lane < 27 && nb + g < ne, nx, ny);
+        float2 vn = corner2<NC>(Edf, ix, iy, cl, lane < 27 && nb + g < ne, nx, ny);
         for (int64_t n0 = nb; n0 < ne; n0 += 3) {
             const int64_t n = n0 + g;
             const bool live = lane < 27 && n < ne;
@@ -544,7 +559,7 @@ k_lattice_assemble2(int nx, int ny, int64_t nn, int chunk, const int64_t *__rest
                 ix -= nx + 1;
                 iy++;
             }
-            vn = corner2(Edf, ix, iy, cl, lane < 27 && n + 3 < ne, nx, ny);
+            vn = corner2<NC>(Edf, ix, iy, cl, lane < 27 && n + 3 < ne, nx, ny);
             unsigned badm = 0u;
             if (anybad) badm = __ballot_sync(kFull, live && cl < 4 && isnan(v.y));
             df E[4];
@@ -593,6 +608,17 @@ k_lattice_assemble2(int nx, int ny, int64_t nn, int chunk, const int64_t *__rest
     }
 }
 
+template <int WPB>
+__global__ void __launch_bounds__(WPB * 32)
+k_lattice_assemble2(int nx, int ny, int64_t nn, int chunk, const int64_t *__restrict__ node_off,
+                    const float2 *__restrict__ Edf, const float2 *__restrict__ kappa_g,
+                    double *__restrict__ vals, const unsigned *__restrict__ flag, unsigned gen, uint32_t pbias,
+                    double kscale)
+{
+    lattice_assemble2_body<WPB, true>(nx, ny, nn, chunk, node_off, Edf, kappa_g, vals, flag, gen, pbias, kscale,
+                                      blockIdx.x, gridDim.x);
+}
+
 // Sensitivity on the box lattice.  The reflections of a box across its
 // mid-planes commute with K^0, so in the Walsh basis of each displacement
 // component, f_t(a) = (-1)^(t.a) over the 2^d corners a, K^0 splits into 2^d
@@ -615,16 +641,18 @@ __device__ __forceinline__ df load_u(const float2 *__restrict__ u, int64_t r)
 }
 
 template <int D, typename UT>
-__global__ void __launch_bounds__(128, SOPTX_SENS_MINB)
-k_lattice_sens(int nx, int ny, int64_t nc, const double *__restrict__ rho, const UT *__restrict__ u,
-               SimpParams sp, const SectorTable<D> B, const double *__restrict__ gscale,
-               double *__restrict__ out, double *__restrict__ partial, unsigned *__restrict__ counter,
-               double *__restrict__ c)
+__device__ __forceinline__ void lattice_sens_body(int nx, int ny, int64_t nc, const double *__restrict__ rho,
+                                                  const UT *__restrict__ u, SimpParams sp, const SectorTable<D> B,
+                                                  const double *__restrict__ gscale, double *__restrict__ out,
+                                                  double *__restrict__ partial, unsigned *__restrict__ counter,
+                                                  double *__restrict__ c, int64_t bid, int64_t nblk, int vthreads)
 {
     constexpr int NCR = 1 << D;
     const double g = gscale ? *gscale : -1.0;
     double mine = 0.0;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nc; e += (int64_t)gridDim.x * blockDim.x) {
+    // block bid of nblk blocks of vthreads threads (threads from vthreads on add nothing)
+    const int64_t e0 = (int)threadIdx.x < vthreads ? bid * vthreads + threadIdx.x : nc;
+    for (int64_t e = e0; e < nc; e += nblk * vthreads) {
         const uint32_t ue = (uint32_t)e;
         const int ex = (int)(ue % (uint32_t)nx);
         const uint32_t r = ue / (uint32_t)nx;
@@ -676,7 +704,64 @@ k_lattice_sens(int nx, int ny, int64_t nc, const double *__restrict__ rho, const
         out[e] = g * simp_dE(sp, re) * sd;
         mine += simp_E(sp, re) * sd;
     }
-    if (c) grid_sum_last_block(mine, partial, counter, c);
+    if (c) grid_sum_last_block_n(mine, partial, counter, c, (unsigned)bid, (unsigned)nblk);
+}
+
+template <int D, typename UT>
+__global__ void __launch_bounds__(128, SOPTX_SENS_MINB)
+k_lattice_sens(int nx, int ny, int64_t nc, const double *__restrict__ rho, const UT *__restrict__ u,
+               SimpParams sp, const SectorTable<D> B, const double *__restrict__ gscale,
+               double *__restrict__ out, double *__restrict__ partial, unsigned *__restrict__ counter,
+               double *__restrict__ c)
+{
+    lattice_sens_body<D, UT>(nx, ny, nc, rho, u, sp, B, gscale, out, partial, counter, c, blockIdx.x, gridDim.x,
+                             blockDim.x);
+}
+
+// Grouped step of small 2D box lattices: one cluster of kGroupCtas CTAs per
+// request of a table that arrives as the kernel's parameter.  The cluster's
+// CTAs share the moduli (and u's float pairs); after a cluster barrier they
+// share the assembly of the mesh's nodes (the warps take the node chunks; the
+// moduli come through coherent loads, having been written in this launch) and
+// the sensitivities, taking the blocks of the single step's sensitivity launch
+// (sgrid blocks of 128 threads) in turn, with the same last-block sum -- the
+// same arithmetic in the same order as the three kernels of a single step, so
+// K, dc and c are bitwise theirs; one launch serves the whole group.
+struct LatReq2 {
+    int nx, ny, chunk, sgrid;
+    unsigned gen;
+    uint32_t pbias;
+    int64_t nn, nc, ndof;
+    double kscale;
+    SimpParams sp;
+    SectorTable<2> B;
+    const double *rho, *u, *gscale, *K0;
+    double *vals, *dc, *c, *partial;
+    float2 *Edf, *udf;
+    const int64_t *node_off;
+    unsigned *flag, *counter;
+    const float2 *kappa;
+};
+constexpr int kGroupMax = 32;
+constexpr int kGroupCtas = 8;   // a portable cluster size
+struct LatGroup2 {
+    int n;
+    LatReq2 r[kGroupMax];
+};
+
+__global__ void __launch_bounds__(256) k_lattice_step_group2(const __grid_constant__ LatGroup2 G)
+{
+    const int rank = (int)(blockIdx.x % kGroupCtas);   // the CTA's rank in its cluster
+    const LatReq2 &R = G.r[blockIdx.x / kGroupCtas];
+    simp_df_body(2, R.nx, R.ny, 1, R.nc, R.rho, R.sp, R.Edf, R.node_off, R.K0, R.vals, R.flag, R.gen, R.ndof, R.u,
+                 R.udf, rank, kGroupCtas);
+    // the moduli and u's pairs of the whole cluster written before any CTA reads them
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+    lattice_assemble2_body<8, false>(R.nx, R.ny, R.nn, R.chunk, R.node_off, R.Edf, R.kappa, R.vals, R.flag, R.gen,
+                                     R.pbias, R.kscale, rank, kGroupCtas);
+    for (int vb = rank; vb < R.sgrid; vb += kGroupCtas)
+        lattice_sens_body<2, float2>(R.nx, R.ny, R.nc, R.rho, R.udf, R.sp, R.B, R.gscale, R.dc, R.partial, R.counter,
+                                     R.c, vb, R.sgrid, 128);
 }
 
 }  // namespace
@@ -926,6 +1011,81 @@ void build_lattice_kappa(int dim, const std::vector<double> &K0, int shift, std:
         const float hh = (float)x;
         kappa[t] = make_float2(hh, (float)(x - (double)hh));
     }
+}
+
+// ------------------------------------------------------------- grouped steps
+// Meshes the grouped step serves: 2D box lattices whose sensitivity splits into
+// Walsh sectors, up to kGroupCells cells (a cluster of kGroupCtas CTAs does the
+// whole step).
+constexpr int64_t kGroupCells = 4096;
+static_assert(kSensThreads == 128, "the grouped step replays the 128-thread sensitivity blocks");
+// its 256 threads then sum at most 128 block partials as the 128 of the single step do
+static_assert((kGroupCells + 127) / 128 <= 128, "the grouped step's last-block sum needs <= 128 partials");
+
+bool lattice_groupable(const soptx_mesh_s &m)
+{
+    const auto &h = m.h;
+    return m.path == SOPTX_PATH_LATTICE && h.dim == 2 && m.d.sectors && m.d.udf && m.d.Edf && h.nc > 0 &&
+           h.nc <= kGroupCells && (int)h.sectors.size() == (2 << 2) * 2;
+}
+
+cudaError_t launch_lattice_group(const soptx_mesh_s *const *ms, const double *const *rho, const double *const *u,
+                                 double *const *vals, double *const *dc, double *const *c, int n, cudaStream_t st)
+{
+    for (int k0 = 0; k0 < n; k0 += kGroupMax) {
+        LatGroup2 G{};
+        G.n = std::min(kGroupMax, n - k0);
+        for (int k = 0; k < G.n; k++) {
+            const soptx_mesh_s &m = *ms[k0 + k];
+            const auto &h = m.h;
+            LatReq2 &R = G.r[k];
+            unsigned gen = ++m.lattice_gen;
+            if (gen == 0u) gen = ++m.lattice_gen;
+            R.nx = h.lat_n[0];
+            R.ny = h.lat_n[1];
+            // node chunks of 3 .. 48 for the cluster's warps
+            const int64_t groups = (h.nn + 2) / 3;
+            R.chunk = 3 * (int)std::max<int64_t>(1, std::min<int64_t>(16, groups / (8 * kGroupCtas)));
+            R.sgrid = lattice_sens_grid(h.nc);
+            R.gen = gen;
+            R.pbias = 0x38000000u + ((uint32_t)h.lat_kshift << 20);
+            R.nn = h.nn;
+            R.nc = h.nc;
+            R.ndof = h.ndof;
+            R.kscale = std::ldexp(1.0, h.lat_kshift);
+            R.sp = simp_params(m.mat);
+            R.B = sector_table<2>(h.sectors);
+            R.rho = rho[k0 + k];
+            R.u = u[k0 + k];
+            R.gscale = nullptr;
+            R.K0 = m.d.K0;
+            R.vals = vals[k0 + k];
+            R.dc = dc[k0 + k];
+            R.c = c[k0 + k];
+            R.partial = m.d.scratch;
+            R.Edf = (float2 *)m.d.Edf;
+            R.udf = m.d.udf;
+            R.node_off = m.d.node_off;
+            R.flag = m.d.lat_bad;
+            R.counter = m.d.counter;
+            R.kappa = (const float2 *)m.d.kappa;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(G.n * kGroupCtas));
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = kGroupCtas;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        cudaError_t err = cudaLaunchKernelEx(&cfg, k_lattice_step_group2, G);
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace soptx

@@ -73,6 +73,8 @@ int64_t mesh_bytes_bound(const soptx_request &r)
 struct soptx_server_s {
     soptx_server_opts opts{};
     std::vector<cudaStream_t> streams;
+    cudaStream_t gstream = nullptr;   // the grouped launches of small lattice requests
+    std::vector<Req *> group;         // requests gathered in this scheduler pass
     cudaEvent_t t0 = nullptr;   // origin of the requests' device timeline
     std::mutex mu;
     std::condition_variable cv_sched, cv_done;
@@ -173,6 +175,68 @@ struct soptx_server_s {
         return SOPTX_OK;
     }
 
+    // A request whose job mesh takes the grouped kernel: 1 = gathered into this
+    // pass's group, 0 = not such a request, -1 = its job still has one in flight
+    // (it stays queued, so the job's requests run in order).
+    int try_group(Req *q)
+    {
+        Job *j = q->job;
+        if (!opts.group_small || !q->r.d_vals || !soptx::lattice_groupable(*j->mesh)) return 0;
+        if (j->in_flight > 0) return -1;
+        q->t_admit = Clock::now();
+        q->res.queue_us = us_between(q->t_submit, q->t_admit);
+        q->res.nnz = j->nnz;
+        // counted in flight from now on: its mesh is not evicted while the group is gathered
+        j->in_flight++;
+        j->last_use = ++use_clock;
+        group.push_back(q);
+        return 1;
+    }
+
+    // One launch for the gathered requests; each gets events at the group's start
+    // and end on the group stream.
+    void flush_group()
+    {
+        if (group.empty()) return;
+        const int n = (int)group.size();
+        std::vector<soptx_mesh> ms(n);
+        std::vector<const double *> rho(n), u(n);
+        std::vector<double *> vals(n), dc(n), c(n);
+        soptx_status s = SOPTX_OK;
+        for (int k = 0; k < n; k++) {
+            Req *q = group[k];
+            ms[k] = q->job->mesh;
+            rho[k] = q->r.d_rho;
+            u[k] = q->r.d_u;
+            vals[k] = q->r.d_vals;
+            dc[k] = q->r.d_dc;
+            c[k] = q->r.d_c;
+            if (s == SOPTX_OK && (cudaEventCreate(&q->ev0) != cudaSuccess || cudaEventCreate(&q->ev1) != cudaSuccess ||
+                                  cudaEventRecord(q->ev0, gstream) != cudaSuccess)) {
+                cudaGetLastError();
+                s = SOPTX_ECUDA;
+            }
+        }
+        if (s == SOPTX_OK)
+            s = soptx_assemble_and_sensitivity_group(n, ms.data(), rho.data(), u.data(), vals.data(), dc.data(),
+                                                     c.data(), gstream);
+        for (int k = 0; k < n && s == SOPTX_OK; k++)
+            if (cudaEventRecord(group[k]->ev1, gstream) != cudaSuccess) {
+                cudaGetLastError();
+                s = SOPTX_ECUDA;
+            }
+        for (Req *q : group) {
+            if (s != SOPTX_OK) {
+                q->job->in_flight--;
+                finish(q, s);
+                continue;
+            }
+            inflight.push_back(q);
+        }
+        stats.groups += s == SOPTX_OK ? 1 : 0;
+        group.clear();
+    }
+
     void run()
     {
         // the completion polls sleep 10 us; with the kernel's default timer slack
@@ -185,7 +249,7 @@ struct soptx_server_s {
             if (stop && queue.empty() && inflight.empty()) break;
             // admissions in arrival order; a request that does not fit yet is skipped
             bool progressed = false;
-            for (auto it = queue.begin(); it != queue.end() && (int)inflight.size() < opts.max_slots;) {
+            for (auto it = queue.begin(); it != queue.end() && (int)(inflight.size() + group.size()) < opts.max_slots;) {
                 Req *q = *it;
                 if (stop) {
                     finish(q, SOPTX_EBUSY);
@@ -248,23 +312,36 @@ struct soptx_server_s {
                     stats.peak_resident_bytes = std::max(stats.peak_resident_bytes, resident);
                     q->res.mesh_was_resident = 0;
                     // the queue may have changed while unlocked: restart the scan
-                    auto pos = std::find(queue.begin(), queue.end(), q);
-                    queue.erase(pos);
-                    soptx_status ls = launch(q);
-                    if (ls != SOPTX_OK) {
-                        j->in_flight = std::max(0, j->in_flight);
-                        finish(q, ls);
+                    const int gr = try_group(q);
+                    if (gr >= 0) {
+                        auto pos = std::find(queue.begin(), queue.end(), q);
+                        queue.erase(pos);
+                        if (gr == 0) {
+                            soptx_status ls = launch(q);
+                            if (ls != SOPTX_OK) {
+                                j->in_flight = std::max(0, j->in_flight);
+                                finish(q, ls);
+                            }
+                        }
                     }
                     it = queue.begin();
                     progressed = true;
                     continue;
                 }
                 q->res.mesh_was_resident = 1;
-                soptx_status ls = launch(q);
-                if (ls != SOPTX_OK) finish(q, ls);
+                const int gr = try_group(q);
+                if (gr < 0) {
+                    ++it;
+                    continue;
+                }
+                if (gr == 0) {
+                    soptx_status ls = launch(q);
+                    if (ls != SOPTX_OK) finish(q, ls);
+                }
                 it = queue.erase(it);
                 progressed = true;
             }
+            flush_group();
             if (progressed) continue;
             if (!inflight.empty()) {
                 lock.unlock();
@@ -304,10 +381,12 @@ soptx_status soptx_server_create(const soptx_server_opts *opts, soptx_server *ou
         }
         s->streams.push_back(st);
     }
-    if (cudaEventCreate(&s->t0) != cudaSuccess || cudaEventRecord(s->t0, s->streams[0]) != cudaSuccess ||
+    if (cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&s->t0) != cudaSuccess || cudaEventRecord(s->t0, s->streams[0]) != cudaSuccess ||
         cudaEventSynchronize(s->t0) != cudaSuccess) {
         cudaGetLastError();
         if (s->t0) cudaEventDestroy(s->t0);
+        if (s->gstream) cudaStreamDestroy(s->gstream);
         for (auto x : s->streams) cudaStreamDestroy(x);
         delete s;
         SOPTX_FAIL(SOPTX_ECUDA, "timeline event");
@@ -412,6 +491,7 @@ soptx_status soptx_server_destroy(soptx_server s)
         delete kv.second;
     }
     for (auto st : s->streams) cudaStreamDestroy(st);
+    if (s->gstream) cudaStreamDestroy(s->gstream);
     if (s->t0) cudaEventDestroy(s->t0);
     delete s;
     return SOPTX_OK;

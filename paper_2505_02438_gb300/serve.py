@@ -12,10 +12,12 @@ from . import _native as N
 
 
 class Server:
-    def __init__(self, hbm_cap_bytes=120 << 30, max_slots=16, n_streams=8, max_queue=4096, device=None):
+    def __init__(self, hbm_cap_bytes=120 << 30, max_slots=16, n_streams=8, max_queue=4096, device=None,
+                 group_small=True):
         dev = torch.cuda.current_device() if device is None else int(device)
         self.device = torch.device("cuda", dev)
-        opts = N.ServerOpts(int(hbm_cap_bytes), int(max_slots), int(n_streams), int(max_queue), dev)
+        opts = N.ServerOpts(int(hbm_cap_bytes), int(max_slots), int(n_streams), int(max_queue), dev,
+                            1 if group_small else 0)
         h = ctypes.c_void_p()
         N.check(N.lib().soptx_server_create(ctypes.byref(opts), ctypes.byref(h)))
         self._h = h

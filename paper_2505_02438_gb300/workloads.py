@@ -255,6 +255,21 @@ def serving_stream(n_jobs=64, iters=8, wl=5, scale=1.0):
     return jobs
 
 
+def small_serving_stream(n_jobs=256, wl=6):
+    """Many small design jobs: Q4 plane-stress boxes with log-uniform sides
+    from 16 x 16 to 64 x 64 cells (the sizes the grouped step serves), FP64.
+    Returns a list of jobs: dict(job, workload, elem_prec)."""
+    g = rng(wl, 4)
+    jobs = []
+    for j in range(n_jobs):
+        nx = int(round(16 * 4 ** float(g.uniform(0.0, 1.0))))
+        ny = int(round(16 * 4 ** float(g.uniform(0.0, 1.0))))
+        w = mbb_q4(nx, ny, wl=200 + j)
+        w.elem_prec = "fp64"
+        jobs.append(dict(job=j, workload=w, elem_prec="fp64"))
+    return jobs
+
+
 def poisson_arrivals(n, rate_per_s, wl=5):
     """Arrival times (seconds) of n requests at the given Poisson rate."""
     return np.cumsum(rng(wl, 3).exponential(1.0 / rate_per_s, size=n))

@@ -133,3 +133,19 @@ def test_requests_of_different_jobs_are_in_flight_together(lib):
     for j in jobs:
         iv = sorted((r["gpu_start_us"], r["gpu_end_us"]) for job, r in res if job == j["job"])
         assert all(b[0] >= a[1] - 1.0 for a, b in zip(iv, iv[1:])), iv
+
+
+@pytest.mark.parametrize("group_small", [True, False])
+def test_small_lattice_requests_share_grouped_launches(lib, group_small):
+    """Requests on small Q4 boxes admitted in one scheduler pass run as one
+    grouped launch (several requests per launch), with each result bitwise its
+    mesh's own step; a hexahedral job in the mix takes the ordinary call."""
+    jobs = [dict(job=j, workload=W.mbb_q4(8 + 7 * j, 4 + 3 * j, wl=400 + j)) for j in range(12)]
+    jobs.append(dict(job=99, workload=W.cantilever_hex(12, 4, 4, wl=499)))
+    meshes, results, stats = run_mix(lib, jobs, iters=3, max_slots=16, n_streams=4, group_small=group_small)
+    check_same_as_alone(meshes, results)
+    assert stats["completed"] == 39 and stats["failed"] == 0
+    if group_small:
+        assert 1 <= stats["groups"] < 36, stats
+    else:
+        assert stats["groups"] == 0
