@@ -224,11 +224,7 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
             N.deg = r.w & 0xffff;
         }
     };
-    auto warp_max = [](int x) {
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) x = max(x, __shfl_xor_sync(kFull, x, o));
-        return x;
-    };
+    auto warp_max = [](int x) { return (int)__reduce_max_sync(kFull, (unsigned)x); };
     struct Cell {
         float4 g[G4];
         float2 E;
@@ -369,8 +365,19 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
 #pragma unroll
                         for (int i = 0; i < D; i++) {
                             double *o = out + (int64_t)i * rowlen + D * slot;
-                            const double d0 = pair_to_double(v[i][0].x, v[i][0].y);
-                            const double d1 = pair_to_double(v[i][1].x, v[i][1].y);
+                            // row 0 widens on the FP64 pipe, row 1 with integer operations
+                            // only: the two pipes share the conversions
+                            double d0, d1;
+                            if (i == 0) {
+                                d0 = pair_to_double(v[i][0].x, v[i][0].y);
+                                d1 = pair_to_double(v[i][1].x, v[i][1].y);
+                            } else {
+                                float h, l;
+                                two_sum(v[i][0].x, v[i][0].y, h, l);
+                                d0 = df_to_double(h, l);
+                                two_sum(v[i][1].x, v[i][1].y, h, l);
+                                d1 = df_to_double(h, l);
+                            }
                             if (aligned16) {
                                 __stcs(reinterpret_cast<double2 *>(o), make_double2(d0, d1));
                             } else {
@@ -749,6 +756,9 @@ cudaError_t contract_launch(const soptx_mesh_s &m, const double *rho, double *va
     if (err != cudaSuccess) return err;
     const int64_t groups = (h.nn + NPW - 1) / NPW;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((groups + wpb - 1) / wpb, (int64_t)sms * std::max(per_sm, 1)));
+    // (as a dependent launch of the moduli kernel the separate call was 3% faster,
+    // but in the one-call step its CTAs took the SMs the strain-energy kernel
+    // beside it had been getting: slower steps)
     kern<<<grid, wpb * 32, smem, st>>>(A);
     return cudaGetLastError();
 }
