@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
         // 3D: no zeroing, every block of the rows is met by some cell and its first
         // meeting starts the sums from zero; 2D (few rows, a tight register budget)
         // zeroes the rows first
-        constexpr bool kFirst = D == 3;
+        constexpr bool kFirst = D == 3;   // (in 2D it spilled at the 80-register cap: P3 236 -> 254 us)
         // 2D: a block's last meeting converts it and stores it straight to the rows
         // (few contributions per value there), so there is no output pass
         constexpr bool kDirect = D == 2;
