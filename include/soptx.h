@@ -193,12 +193,12 @@ soptx_status soptx_assemble_and_sensitivity(soptx_mesh mesh, const double *d_rho
  * The one-call step (Sec. 2.2, Appendix D) for a group of n distinct meshes,
  * one launch serving many small ones: per k the arguments and results of
  * soptx_assemble_and_sensitivity(meshes[k], d_rho[k], d_u[k], d_vals[k],
- * d_dc[k], d_c[k], stream).  2D box lattices of up to 4096 cells (Q4 up to
- * 64 x 64) share one kernel launch per 32 meshes, a cluster of 8 CTAs each
- * (one for the moduli, the assembly and the sensitivities in turn); the other
- * meshes get the ordinary call on the same stream.  K and dc are bitwise the
- * values of the ordinary call; c is summed in another fixed order (the CTA's
- * own), so it may differ from the ordinary call's in the last bits.
+ * d_dc[k], d_c[k], stream).  Box lattices of up to 4096 cells (Q4 up to
+ * 64 x 64, hex Q1 up to 16 x 16 x 16) share one kernel launch per 32 meshes of
+ * a dimension, a cluster of 8 CTAs each (the moduli, then the assembly and the
+ * sensitivities); the other meshes get the ordinary call on the same stream.
+ * K, dc and c are bitwise the values of the ordinary call (the same
+ * arithmetic, c summed over the same blocks in the same order).
  *   n      : number of meshes (0 does nothing)
  *   arrays : host arrays of n entries (device pointers inside); d_c[k] may be
  *            NULL, the others as in soptx_assemble_and_sensitivity

@@ -35,7 +35,7 @@ typedef struct {
     int32_t n_streams;       /* stream pool size (>= 1)                       */
     int32_t max_queue;       /* pending requests accepted before SOPTX_EBUSY  */
     int32_t device;          /* CUDA device ordinal the server runs on        */
-    int32_t group_small;     /* 1: requests on small 2D box lattices (see
+    int32_t group_small;     /* 1: requests on small box lattices (see
                               * soptx_assemble_and_sensitivity_group) are
                               * launched together, one kernel for all of
                               * them that are admitted in one scheduler pass;

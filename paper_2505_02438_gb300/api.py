@@ -200,8 +200,8 @@ class Mesh:
 
 def step_group(meshes, rhos, us, stream=None):
     """The one-call step for several distinct meshes (soptx_assemble_and_sensitivity_group):
-    small 2D box lattices share one kernel launch, the others get the ordinary
-    call on the same stream.  Returns [(vals, dc, c)] in order, bitwise the
+    small 2D and 3D box lattices share one kernel launch, the others get the
+    ordinary call on the same stream.  Returns [(vals, dc, c)] in order, bitwise the
     results of each mesh's own step."""
     n = len(meshes)
     if not (len(rhos) == n and len(us) == n):

@@ -186,8 +186,8 @@ cudaError_t launch_lattice_sensitivity(const soptx_mesh_s &m, const double *rho,
 int lattice_sens_grid(int64_t nc);
 cudaError_t launch_lattice_step(const soptx_mesh_s &m, const double *rho, const double *u, double *vals, double *dc,
                                 double *c, cudaStream_t st, const double *gscale = nullptr);
-// Grouped one-call steps of small 2D box lattices (a cluster of 8 CTAs each, one launch per
-// 32 meshes); the meshes must be distinct and lattice_groupable.
+// Grouped one-call steps of small 2D and 3D box lattices (a cluster of 8 CTAs each, one launch
+// per 32 meshes of a dimension); the meshes must be distinct and lattice_groupable.
 bool lattice_groupable(const soptx_mesh_s &m);
 cudaError_t launch_lattice_group(const soptx_mesh_s *const *ms, const double *const *rho, const double *const *u,
                                  double *const *vals, double *const *dc, double *const *c, int n, cudaStream_t st);

@@ -199,6 +199,9 @@ struct NodeIter {
 };
 
 // Corner moduli of two nodes: lanes 0..7 those of node a, lanes 8..15 those of node b.
+// NC: the moduli were written by an earlier launch (read-only path); otherwise by
+// this kernel, before a barrier (coherent loads).
+template <bool NC>
 __device__ __forceinline__ float2 load_corner_pair(const float2 *__restrict__ Edf, const int ia[3], const int ib[3],
                                                    bool has_b, int lane, int nx, int ny, int nz)
 {
@@ -209,7 +212,7 @@ __device__ __forceinline__ float2 load_corner_pair(const float2 *__restrict__ Ed
         const int *idx = second ? ib : ia;
         const int ex = idx[0] - 1 + (l & 1), ey = idx[1] - 1 + ((l >> 1) & 1), ez = idx[2] - 1 + (l >> 2);
         if (ex >= 0 && ex < nx && ey >= 0 && ey < ny && ez >= 0 && ez < nz)
-            v = __ldg(&Edf[((int64_t)ez * ny + ey) * nx + ex]);
+            v = NC ? __ldg(&Edf[((int64_t)ez * ny + ey) * nx + ex]) : __ldcg(&Edf[((int64_t)ez * ny + ey) * nx + ex]);
     }
     return v;
 }
@@ -325,13 +328,15 @@ k_simp_df(int dim, int nx, int ny, int nz, int64_t nc, const double *__restrict_
 // phase of its destination; before it is refilled the warp waits until the
 // copy engine has read the previous pair (one node at a time with two
 // buffers was 12% more instructions: 409 against 358 per node).
-template <int WPB>
-__global__ void __launch_bounds__(WPB * 32, SOPTX_LATTICE_MINBLOCKS)
-k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, int chunk, const int64_t *__restrict__ node_off,
-                          const float2 *__restrict__ Edf, const float2 *__restrict__ kappa_g,
-                          const double *__restrict__ K0, const double *__restrict__ rho, SimpParams sp,
-                          double *__restrict__ vals, const unsigned *__restrict__ flag, unsigned gen,
-                          uint32_t pbias, double kscale)
+template <int WPB, bool NC>
+__device__ __forceinline__ void lattice_assemble3_body(int nx, int ny, int nz, int64_t nn, int chunk,
+                                                       const int64_t *__restrict__ node_off,
+                                                       const float2 *__restrict__ Edf,
+                                                       const float2 *__restrict__ kappa_g,
+                                                       const double *__restrict__ K0, const double *__restrict__ rho,
+                                                       SimpParams sp, double *__restrict__ vals,
+                                                       const unsigned *__restrict__ flag, unsigned gen,
+                                                       uint32_t pbias, double kscale, int64_t bid, int64_t nblk)
 {
     const int lane = threadIdx.x & 31;
     const int dl = lane < 27 ? lane : 26;
@@ -375,15 +380,15 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, int chunk, const int64_t
     float2(*tab)[64] = tab_s[threadIdx.x >> 5];
 
     const int64_t nchunks = (nn + chunk - 1) / chunk;
-    const int64_t warps = (int64_t)gridDim.x * WPB;
-    for (int64_t ch = (int64_t)blockIdx.x * WPB + (threadIdx.x >> 5); ch < nchunks; ch += warps) {
+    const int64_t warps = nblk * WPB;
+    for (int64_t ch = bid * WPB + (threadIdx.x >> 5); ch < nchunks; ch += warps) {
         const int64_t n_begin = ch * chunk;
         const int64_t n_end = min(n_begin + (int64_t)chunk, nn);
         NodeIter ia;
         ia.decode((uint32_t)n_begin, nx, ny);
         NodeIter ib = ia;
         ib.step(nx, ny);
-        float2 cur = load_corner_pair(Edf, ia.idx, ib.idx, n_begin + 1 < n_end, lane, nx, ny, nz);
+        float2 cur = load_corner_pair<NC>(Edf, ia.idx, ib.idx, n_begin + 1 < n_end, lane, nx, ny, nz);
         int64_t off = node_off[n_begin];
         for (int64_t n = n_begin; n < n_end; n += 2) {
             const bool has_b = n + 1 < n_end;
@@ -397,7 +402,7 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, int chunk, const int64_t
             float2 nxt = make_float2(0.f, 0.f);
             int64_t off_next = 0;
             if (n + 2 < n_end) {
-                nxt = load_corner_pair(Edf, ia.idx, ib.idx, n + 3 < n_end, lane, nx, ny, nz);
+                nxt = load_corner_pair<NC>(Edf, ia.idx, ib.idx, n + 3 < n_end, lane, nx, ny, nz);
                 off_next = node_off[n + 2];
             }
             const df Ec = df{cur.x, cur.y};
@@ -485,6 +490,18 @@ k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, int chunk, const int64_t
         }
     }
     if (lane == 0) bulk_wait_all();
+}
+
+template <int WPB>
+__global__ void __launch_bounds__(WPB * 32, SOPTX_LATTICE_MINBLOCKS)
+k_lattice_assemble3(int nx, int ny, int nz, int64_t nn, int chunk, const int64_t *__restrict__ node_off,
+                    const float2 *__restrict__ Edf, const float2 *__restrict__ kappa_g,
+                    const double *__restrict__ K0, const double *__restrict__ rho, SimpParams sp,
+                    double *__restrict__ vals, const unsigned *__restrict__ flag, unsigned gen, uint32_t pbias,
+                    double kscale)
+{
+    lattice_assemble3_body<WPB, true>(nx, ny, nz, nn, chunk, node_off, Edf, kappa_g, K0, rho, sp, vals, flag, gen,
+                                      pbias, kscale, blockIdx.x, gridDim.x);
 }
 
 // 2D: a warp takes chunks of up to 48 consecutive nodes, three at a time, lanes
@@ -718,7 +735,7 @@ k_lattice_sens(int nx, int ny, int64_t nc, const double *__restrict__ rho, const
                              blockDim.x);
 }
 
-// Grouped step of small 2D box lattices: one cluster of kGroupCtas CTAs per
+// Grouped step of small box lattices (2D and 3D): one cluster of kGroupCtas CTAs per
 // request of a table that arrives as the kernel's parameter.  The cluster's
 // CTAs share the moduli (and u's float pairs); after a cluster barrier they
 // share the assembly of the mesh's nodes (the warps take the node chunks; the
@@ -727,14 +744,14 @@ k_lattice_sens(int nx, int ny, int64_t nc, const double *__restrict__ rho, const
 // (sgrid blocks of 128 threads) in turn, with the same last-block sum -- the
 // same arithmetic in the same order as the three kernels of a single step, so
 // K, dc and c are bitwise theirs; one launch serves the whole group.
-struct LatReq2 {
-    int nx, ny, chunk, sgrid;
+template <int D> struct LatReq {
+    int nx, ny, nz, chunk, sgrid;
     unsigned gen;
     uint32_t pbias;
     int64_t nn, nc, ndof;
     double kscale;
     SimpParams sp;
-    SectorTable<2> B;
+    SectorTable<D> B;
     const double *rho, *u, *gscale, *K0;
     double *vals, *dc, *c, *partial;
     float2 *Edf, *udf;
@@ -744,23 +761,29 @@ struct LatReq2 {
 };
 constexpr int kGroupMax = 32;
 constexpr int kGroupCtas = 8;   // a portable cluster size
-struct LatGroup2 {
+template <int D> struct LatGroup {
     int n;
-    LatReq2 r[kGroupMax];
+    LatReq<D> r[kGroupMax];
 };
+static_assert(sizeof(LatGroup<3>) < 32000, "the request table travels as the kernel's parameter");
 
-__global__ void __launch_bounds__(256) k_lattice_step_group2(const __grid_constant__ LatGroup2 G)
+template <int D>
+__global__ void __launch_bounds__(256) k_lattice_step_group(const __grid_constant__ LatGroup<D> G)
 {
     const int rank = (int)(blockIdx.x % kGroupCtas);   // the CTA's rank in its cluster
-    const LatReq2 &R = G.r[blockIdx.x / kGroupCtas];
-    simp_df_body(2, R.nx, R.ny, 1, R.nc, R.rho, R.sp, R.Edf, R.node_off, R.K0, R.vals, R.flag, R.gen, R.ndof, R.u,
+    const LatReq<D> &R = G.r[blockIdx.x / kGroupCtas];
+    simp_df_body(D, R.nx, R.ny, R.nz, R.nc, R.rho, R.sp, R.Edf, R.node_off, R.K0, R.vals, R.flag, R.gen, R.ndof, R.u,
                  R.udf, rank, kGroupCtas);
     // the moduli and u's pairs of the whole cluster written before any CTA reads them
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-    lattice_assemble2_body<8, false>(R.nx, R.ny, R.nn, R.chunk, R.node_off, R.Edf, R.kappa, R.vals, R.flag, R.gen,
-                                     R.pbias, R.kscale, rank, kGroupCtas);
+    if constexpr (D == 2)
+        lattice_assemble2_body<8, false>(R.nx, R.ny, R.nn, R.chunk, R.node_off, R.Edf, R.kappa, R.vals, R.flag, R.gen,
+                                         R.pbias, R.kscale, rank, kGroupCtas);
+    else
+        lattice_assemble3_body<8, false>(R.nx, R.ny, R.nz, R.nn, R.chunk, R.node_off, R.Edf, R.kappa, R.K0, R.rho,
+                                         R.sp, R.vals, R.flag, R.gen, R.pbias, R.kscale, rank, kGroupCtas);
     for (int vb = rank; vb < R.sgrid; vb += kGroupCtas)
-        lattice_sens_body<2, float2>(R.nx, R.ny, R.nc, R.rho, R.udf, R.sp, R.B, R.gscale, R.dc, R.partial, R.counter,
+        lattice_sens_body<D, float2>(R.nx, R.ny, R.nc, R.rho, R.udf, R.sp, R.B, R.gscale, R.dc, R.partial, R.counter,
                                      R.c, vb, R.sgrid, 128);
 }
 
@@ -1014,9 +1037,9 @@ void build_lattice_kappa(int dim, const std::vector<double> &K0, int shift, std:
 }
 
 // ------------------------------------------------------------- grouped steps
-// Meshes the grouped step serves: 2D box lattices whose sensitivity splits into
-// Walsh sectors, up to kGroupCells cells (a cluster of kGroupCtas CTAs does the
-// whole step).
+// Meshes the grouped step serves: 2D and 3D box lattices whose sensitivity
+// splits into Walsh sectors, up to kGroupCells cells (a cluster of kGroupCtas
+// CTAs does the whole step).
 constexpr int64_t kGroupCells = 4096;
 static_assert(kSensThreads == 128, "the grouped step replays the 128-thread sensitivity blocks");
 // its 256 threads then sum at most 128 block partials as the 128 of the single step do
@@ -1025,27 +1048,41 @@ static_assert((kGroupCells + 127) / 128 <= 128, "the grouped step's last-block s
 bool lattice_groupable(const soptx_mesh_s &m)
 {
     const auto &h = m.h;
-    return m.path == SOPTX_PATH_LATTICE && h.dim == 2 && m.d.sectors && m.d.udf && m.d.Edf && h.nc > 0 &&
-           h.nc <= kGroupCells && (int)h.sectors.size() == (2 << 2) * 2;
+    return m.path == SOPTX_PATH_LATTICE && (h.dim == 2 || h.dim == 3) && m.d.sectors && m.d.udf && m.d.Edf &&
+           h.nc > 0 && h.nc <= kGroupCells && (int)h.sectors.size() == (h.dim << h.dim) * h.dim;
 }
 
-cudaError_t launch_lattice_group(const soptx_mesh_s *const *ms, const double *const *rho, const double *const *u,
-                                 double *const *vals, double *const *dc, double *const *c, int n, cudaStream_t st)
+template <int D>
+static cudaError_t launch_group_d(const std::vector<int> &ks, const soptx_mesh_s *const *ms, const double *const *rho,
+                                  const double *const *u, double *const *vals, double *const *dc, double *const *c,
+                                  cudaStream_t st)
 {
+    const int n = (int)ks.size();
     for (int k0 = 0; k0 < n; k0 += kGroupMax) {
-        LatGroup2 G{};
+        static thread_local LatGroup<D> G;   // ~24 KB: off the stack
+        G = LatGroup<D>{};
         G.n = std::min(kGroupMax, n - k0);
         for (int k = 0; k < G.n; k++) {
-            const soptx_mesh_s &m = *ms[k0 + k];
+            const int j = ks[k0 + k];
+            const soptx_mesh_s &m = *ms[j];
             const auto &h = m.h;
-            LatReq2 &R = G.r[k];
+            LatReq<D> &R = G.r[k];
             unsigned gen = ++m.lattice_gen;
             if (gen == 0u) gen = ++m.lattice_gen;
             R.nx = h.lat_n[0];
             R.ny = h.lat_n[1];
-            // node chunks of 3 .. 48 for the cluster's warps
-            const int64_t groups = (h.nn + 2) / 3;
-            R.chunk = 3 * (int)std::max<int64_t>(1, std::min<int64_t>(16, groups / (8 * kGroupCtas)));
+            R.nz = D == 3 ? h.lat_n[2] : 1;
+            constexpr int warps = 8 * kGroupCtas;
+            if (D == 2) {
+                // node chunks of 3 .. 48 for the cluster's warps
+                const int64_t groups = (h.nn + 2) / 3;
+                R.chunk = 3 * (int)std::max<int64_t>(1, std::min<int64_t>(16, groups / warps));
+            } else {
+                // even chunks of at most kChunk nodes, about as many per warp (as in the single step)
+                const int64_t rounds = (h.nn + warps * kChunk - 1) / (warps * kChunk);
+                int chunk = (int)std::max<int64_t>(1, (h.nn + warps * rounds - 1) / (warps * rounds));
+                R.chunk = chunk + (chunk & 1);
+            }
             R.sgrid = lattice_sens_grid(h.nc);
             R.gen = gen;
             R.pbias = 0x38000000u + ((uint32_t)h.lat_kshift << 20);
@@ -1054,14 +1091,14 @@ cudaError_t launch_lattice_group(const soptx_mesh_s *const *ms, const double *co
             R.ndof = h.ndof;
             R.kscale = std::ldexp(1.0, h.lat_kshift);
             R.sp = simp_params(m.mat);
-            R.B = sector_table<2>(h.sectors);
-            R.rho = rho[k0 + k];
-            R.u = u[k0 + k];
+            R.B = sector_table<D>(h.sectors);
+            R.rho = rho[j];
+            R.u = u[j];
             R.gscale = nullptr;
             R.K0 = m.d.K0;
-            R.vals = vals[k0 + k];
-            R.dc = dc[k0 + k];
-            R.c = c[k0 + k];
+            R.vals = vals[j];
+            R.dc = dc[j];
+            R.c = c[j];
             R.partial = m.d.scratch;
             R.Edf = (float2 *)m.d.Edf;
             R.udf = m.d.udf;
@@ -1082,10 +1119,20 @@ cudaError_t launch_lattice_group(const soptx_mesh_s *const *ms, const double *co
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        cudaError_t err = cudaLaunchKernelEx(&cfg, k_lattice_step_group2, G);
+        cudaError_t err = cudaLaunchKernelEx(&cfg, k_lattice_step_group<D>, G);
         if (err != cudaSuccess) return err;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_lattice_group(const soptx_mesh_s *const *ms, const double *const *rho, const double *const *u,
+                                 double *const *vals, double *const *dc, double *const *c, int n, cudaStream_t st)
+{
+    std::vector<int> k2, k3;
+    for (int k = 0; k < n; k++) (ms[k]->h.dim == 2 ? k2 : k3).push_back(k);
+    cudaError_t err = k2.empty() ? cudaSuccess : launch_group_d<2>(k2, ms, rho, u, vals, dc, c, st);
+    if (err == cudaSuccess && !k3.empty()) err = launch_group_d<3>(k3, ms, rho, u, vals, dc, c, st);
+    return err;
 }
 
 }  // namespace soptx

@@ -1,7 +1,8 @@
-"""The grouped one-call step (soptx_assemble_and_sensitivity_group): small 2D
-box lattices share one launch, one CTA each.  Each mesh's K, dc and c must be
-bitwise those of its own step (the same arithmetic in the same order), and
-therefore match the oracle; other meshes in the group take the ordinary call."""
+"""The grouped one-call step (soptx_assemble_and_sensitivity_group): small 2D and
+3D box lattices share one launch, a cluster of CTAs each.  Each mesh's K, dc and
+c must be bitwise those of its own step (the same arithmetic in the same order),
+and therefore match the oracle; other meshes in the group take the ordinary
+call."""
 import numpy as np
 import pytest
 import torch
@@ -24,12 +25,14 @@ def inputs(m, seed):
     return g.uniform(0.001, 1.0, m.n_cells), g.standard_normal(m.ndof)
 
 
-# Q4 boxes: one cell, one row and one column of cells, ragged node chunks,
-# exactly 4096 cells (the largest grouped size); then meshes that are not
-# grouped (4097 cells, a 3D box, a distorted quad mesh)
+# Q4 and hex Q1 boxes: one cell, one row and one column of cells, ragged node
+# chunks, exactly 4096 cells (the largest grouped size); then meshes that are
+# not grouped (4097 and 4352 cells, distorted quads and hexes)
 GROUPED = [(1, 1), (7, 1), (1, 9), (60, 20), (17, 9), (64, 64), (128, 32), (3, 50)]
-ORDINARY = [("quad", lambda: W.structured_quad(4097, 1)), ("hex", lambda: W.structured_hex(4, 3, 2)),
-            ("quad", lambda: W.quad_grid(9, 6, jitter=0.2, g=np.random.default_rng(3)))]
+GROUPED3 = [(1, 1, 1), (5, 4, 3), (16, 16, 16), (30, 10, 10), (17, 9, 5), (1, 1, 40)]
+ORDINARY = [("quad", lambda: W.structured_quad(4097, 1)), ("hex", lambda: W.structured_hex(17, 16, 16)),
+            ("quad", lambda: W.quad_grid(9, 6, jitter=0.2, g=np.random.default_rng(3))),
+            ("hex", lambda: W.hex_grid(4, 3, 2, jitter=0.15, g=np.random.default_rng(4)))]
 
 
 def make_meshes(lib, mat=MAT):
@@ -37,6 +40,9 @@ def make_meshes(lib, mat=MAT):
     for nx, ny in GROUPED:
         c, cl = W.structured_quad(nx, ny)
         ms.append(("quad", c, cl, lib.Mesh("quad", 1, c, cl, *mat)))
+    for nx, ny, nz in GROUPED3:
+        c, cl = W.structured_hex(nx, ny, nz)
+        ms.append(("hex", c, cl, lib.Mesh("hex", 1, c, cl, *mat)))
     for cell, mk in ORDINARY:
         c, cl = mk()
         ms.append((cell, c, cl, lib.Mesh(cell, 1, c, cl, *mat)))
@@ -46,7 +52,7 @@ def make_meshes(lib, mat=MAT):
 def test_group_is_bitwise_each_meshs_own_step(lib):
     from paper_2505_02438_gb300 import step_group
     ms = make_meshes(lib)
-    assert all(m.path == "lattice" for _, _, _, m in ms[:len(GROUPED)])
+    assert all(m.path == "lattice" for _, _, _, m in ms[:len(GROUPED) + len(GROUPED3)])
     ins = [inputs(m, 10 + k) for k, (_, _, _, m) in enumerate(ms)]
     rhos = [to_dev(r) for r, _ in ins]
     us = [to_dev(u) for _, u in ins]
@@ -63,21 +69,22 @@ def test_group_is_bitwise_each_meshs_own_step(lib):
 
 def test_group_matches_oracle(lib):
     from paper_2505_02438_gb300 import step_group
-    shapes = [(60, 20), (64, 64), (5, 3)]
+    shapes = [("quad", W.structured_quad(60, 20)), ("quad", W.structured_quad(64, 64)),
+              ("quad", W.structured_quad(5, 3)), ("hex", W.structured_hex(12, 8, 6)),
+              ("hex", W.structured_hex(3, 2, 2))]
     meshes, rhos, us, data = [], [], [], []
-    for k, (nx, ny) in enumerate(shapes):
-        c, cl = W.structured_quad(nx, ny)
-        m = lib.Mesh("quad", 1, c, cl, *MAT)
+    for k, (cell, (c, cl)) in enumerate(shapes):
+        m = lib.Mesh(cell, 1, c, cl, *MAT)
         rho, u = inputs(m, 40 + k)
         meshes.append(m)
         rhos.append(to_dev(rho))
         us.append(to_dev(u))
-        data.append((c, cl, rho, u))
+        data.append((cell, c, cl, rho, u))
     got = step_group(meshes, rhos, us)
-    for (c, cl, rho, u), m, (vals, dc, cc) in zip(data, meshes, got):
-        rp, ci, v, va, _ = oracle_csr("quad", 1, c, cl, MAT, rho)
+    for (cell, c, cl, rho, u), m, (vals, dc, cc) in zip(data, meshes, got):
+        rp, ci, v, va, _ = oracle_csr(cell, 1, c, cl, MAT, rho)
         assert np.all(np.abs(vals.cpu().numpy() - v) <= TOL64 * va + 1e-15 * va.max())
-        dco, so, co, sabs = oracle.sensitivity("quad", 1, c, cl, MAT, rho, u, with_abs=True)
+        dco, so, co, sabs = oracle.sensitivity(cell, 1, c, cl, MAT, rho, u, with_abs=True)
         E0, Emin, nu, p, ps = MAT
         dE = p * rho ** (p - 1) * (E0 - Emin)
         E = Emin + rho ** p * (E0 - Emin)
@@ -91,9 +98,10 @@ def test_group_out_of_range_moduli(lib):
     from paper_2505_02438_gb300 import step_group
     mat = (1.0, 0.0, 0.3, 3.0, 0)
     meshes, rhos, us = [], [], []
-    for k, (nx, ny) in enumerate([(9, 7), (33, 20)]):
-        c, cl = W.structured_quad(nx, ny)
-        m = lib.Mesh("quad", 1, c, cl, *mat)
+    shapes = [("quad", W.structured_quad(9, 7)), ("quad", W.structured_quad(33, 20)),
+              ("hex", W.structured_hex(5, 4, 3)), ("hex", W.structured_hex(14, 10, 9))]
+    for k, (cell, (c, cl)) in enumerate(shapes):
+        m = lib.Mesh(cell, 1, c, cl, *mat)
         rho, u = inputs(m, 60 + k)
         rho[::5] = 1e-9
         rho[1::7] = 0.0

@@ -137,15 +137,16 @@ def test_requests_of_different_jobs_are_in_flight_together(lib):
 
 @pytest.mark.parametrize("group_small", [True, False])
 def test_small_lattice_requests_share_grouped_launches(lib, group_small):
-    """Requests on small Q4 boxes admitted in one scheduler pass run as one
-    grouped launch (several requests per launch), with each result bitwise its
-    mesh's own step; a hexahedral job in the mix takes the ordinary call."""
+    """Requests on small Q4 and hex boxes admitted in one scheduler pass run as
+    grouped launches (several requests per launch), with each result bitwise its
+    mesh's own step; a larger hexahedral job in the mix takes the ordinary call."""
     jobs = [dict(job=j, workload=W.mbb_q4(8 + 7 * j, 4 + 3 * j, wl=400 + j)) for j in range(12)]
-    jobs.append(dict(job=99, workload=W.cantilever_hex(12, 4, 4, wl=499)))
+    jobs += [dict(job=50 + j, workload=W.cantilever_hex(6 + 4 * j, 4, 4, wl=450 + j)) for j in range(3)]
+    jobs.append(dict(job=99, workload=W.cantilever_hex(30, 12, 12, wl=499)))
     meshes, results, stats = run_mix(lib, jobs, iters=3, max_slots=16, n_streams=4, group_small=group_small)
     check_same_as_alone(meshes, results)
-    assert stats["completed"] == 39 and stats["failed"] == 0
+    assert stats["completed"] == 48 and stats["failed"] == 0
     if group_small:
-        assert 1 <= stats["groups"] < 36, stats
+        assert 1 <= stats["groups"] < 45, stats
     else:
         assert stats["groups"] == 0
