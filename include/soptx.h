@@ -183,8 +183,10 @@ soptx_status soptx_sensitivity(soptx_mesh mesh, const double *d_rho, const doubl
 /* One pass that produces both K(rho) and the sensitivities (the per-iteration
  * step); same arguments and results as the two calls above.  On a 2D box
  * lattice the sensitivities run on a second, mesh-owned stream beside the
- * assembly (made by the first such call, with two events); everything is
- * ordered on `stream` when the call returns. */
+ * assembly; on other meshes of affine cells the assembly runs on that stream
+ * (created at the highest stream priority) beside the sensitivities on
+ * `stream` (the stream and two events are made by the first such call);
+ * everything is ordered on `stream` when the call returns. */
 soptx_status soptx_assemble_and_sensitivity(soptx_mesh mesh, const double *d_rho,
                                             const double *d_u, double *d_vals,
                                             double *d_dc, double *d_c, void *stream);

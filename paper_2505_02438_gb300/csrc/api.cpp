@@ -54,7 +54,12 @@ static cudaError_t ensure_side(soptx_mesh_s &m)
     if (d.side) return cudaSuccess;
     cudaStream_t side = nullptr;
     cudaEvent_t ev[2] = {};
-    cudaError_t e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+    // meshes with the strain-energy sensitivities run their assembly on this
+    // stream in the one-call step, at the highest priority (see launch_step)
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, d.strain ? greatest : least);
     for (int i = 0; i < 2 && e == cudaSuccess; i++) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         for (cudaEvent_t x : ev)

@@ -289,13 +289,15 @@ cudaError_t launch_step(const soptx_mesh_s &m, const double *rho, const double *
     if (m.path == SOPTX_PATH_LATTICE && m.d.sectors && m.h.nc > 0)
         return launch_lattice_step(m, rho, u, vals, dc, c, st, gscale);
     if (m.d.strain && m.d.side && m.h.nc > 0 && m.h.nnz > 0) {
-        // affine cells: the sensitivities need rho and u but not K, so they run on
-        // the mesh's second stream beside the assembly
+        // affine cells: the sensitivities need rho and u but not K.  The assembly
+        // runs on the mesh's second stream, created at the highest priority and
+        // launched first, so the block scheduler gives free SM slots to its blocks
+        // and the sensitivities on `stream` fill the slots it leaves
         cudaError_t err = cudaEventRecord(m.d.ev[0], st);
         if (err == cudaSuccess) err = cudaStreamWaitEvent(m.d.side, m.d.ev[0], 0);
-        if (err == cudaSuccess) err = launch_strain_sensitivity(m, rho, u, dc, c, gscale, m.d.side);
+        if (err == cudaSuccess) err = launch_assemble(m, rho, vals, m.d.side);
         if (err == cudaSuccess) err = cudaEventRecord(m.d.ev[1], m.d.side);
-        if (err == cudaSuccess) err = launch_assemble(m, rho, vals, st);
+        if (err == cudaSuccess) err = launch_strain_sensitivity(m, rho, u, dc, c, gscale, st);
         if (err == cudaSuccess) err = cudaStreamWaitEvent(st, m.d.ev[1], 0);
         return err;
     }
