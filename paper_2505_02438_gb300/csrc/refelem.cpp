@@ -392,6 +392,16 @@ void build_simplex_quadrature(const RefElement &ref, RefQuad &q)
         // lam_0 = alpha (the origin vertex), then alpha on each unit vertex
         pts = {{be, be, be}, {al, be, be}, {be, al, be}, {be, be, al}};
         wts.assign(4, 1.0 / 24);
+    } else if (k == 3 && dim == 2) {
+        // Radon's seven-point rule (Stroud T2:5-1), exact for degree 5 (the
+        // energy density of P3 is degree 4): the centroid and two orbits of three
+        // points (a, a, b) in barycentric coordinates, area 1/2
+        const double r = std::sqrt(15.0);
+        const double a1 = (6.0 - r) / 21.0, b1 = (9.0 + 2.0 * r) / 21.0, w1 = (155.0 - r) / 2400.0;
+        const double a2 = (6.0 + r) / 21.0, b2 = (9.0 - 2.0 * r) / 21.0, w2 = (155.0 + r) / 2400.0;
+        pts = {{1.0 / 3, 1.0 / 3, 0.0}, {a1, a1, 0.0}, {a1, b1, 0.0}, {b1, a1, 0.0},
+               {a2, a2, 0.0}, {a2, b2, 0.0}, {b2, a2, 0.0}};
+        wts = {9.0 / 80, w1, w1, w1, w2, w2, w2};
     } else {
         std::vector<double> tu, wu, tv, wv;
         gauss_legendre01(dim == 3 ? 4 : 3, tu, wu);
