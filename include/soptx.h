@@ -195,8 +195,8 @@ soptx_status soptx_assemble_and_sensitivity(soptx_mesh mesh, const double *d_rho
  * The one-call step (Sec. 2.2, Appendix D) for a group of n distinct meshes,
  * one launch serving many small ones: per k the arguments and results of
  * soptx_assemble_and_sensitivity(meshes[k], d_rho[k], d_u[k], d_vals[k],
- * d_dc[k], d_c[k], stream).  Box lattices of up to 4096 cells (Q4 up to
- * 64 x 64, hex Q1 up to 16 x 16 x 16) share one kernel launch per 32 meshes of
+ * d_dc[k], d_c[k], stream).  Box lattices of up to 4096 cells in 2D (Q4 up
+ * to 64 x 64) and 1024 in 3D (hex Q1, e.g. 16 x 8 x 8) share one kernel launch per 32 meshes of
  * a dimension, a cluster of 8 CTAs each (the moduli, then the assembly and the
  * sensitivities); the other meshes get the ordinary call on the same stream.
  * K, dc and c are bitwise the values of the ordinary call (the same

@@ -1038,9 +1038,11 @@ void build_lattice_kappa(int dim, const std::vector<double> &K0, int shift, std:
 
 // ------------------------------------------------------------- grouped steps
 // Meshes the grouped step serves: 2D and 3D box lattices whose sensitivity
-// splits into Walsh sectors, up to kGroupCells cells (a cluster of kGroupCtas
-// CTAs does the whole step).
+// splits into Walsh sectors, up to kGroupCells cells in 2D and kGroupCells3 in
+// 3D (a cluster of kGroupCtas CTAs does the whole step; a larger 3D mesh's step
+// takes longer on one cluster than its three launches across the GPU).
 constexpr int64_t kGroupCells = 4096;
+constexpr int64_t kGroupCells3 = 1024;
 static_assert(kSensThreads == 128, "the grouped step replays the 128-thread sensitivity blocks");
 // its 256 threads then sum at most 128 block partials as the 128 of the single step do
 static_assert((kGroupCells + 127) / 128 <= 128, "the grouped step's last-block sum needs <= 128 partials");
@@ -1049,7 +1051,8 @@ bool lattice_groupable(const soptx_mesh_s &m)
 {
     const auto &h = m.h;
     return m.path == SOPTX_PATH_LATTICE && (h.dim == 2 || h.dim == 3) && m.d.sectors && m.d.udf && m.d.Edf &&
-           h.nc > 0 && h.nc <= kGroupCells && (int)h.sectors.size() == (h.dim << h.dim) * h.dim;
+           h.nc > 0 && h.nc <= (h.dim == 2 ? kGroupCells : kGroupCells3) &&
+           (int)h.sectors.size() == (h.dim << h.dim) * h.dim;
 }
 
 template <int D>

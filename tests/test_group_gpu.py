@@ -26,11 +26,11 @@ def inputs(m, seed):
 
 
 # Q4 and hex Q1 boxes: one cell, one row and one column of cells, ragged node
-# chunks, exactly 4096 cells (the largest grouped size); then meshes that are
-# not grouped (4097 and 4352 cells, distorted quads and hexes)
+# chunks, exactly the largest grouped size (4096 cells in 2D, 1024 in 3D); then
+# meshes that are not grouped (4097 and 1088 cells, distorted quads and hexes)
 GROUPED = [(1, 1), (7, 1), (1, 9), (60, 20), (17, 9), (64, 64), (128, 32), (3, 50)]
-GROUPED3 = [(1, 1, 1), (5, 4, 3), (16, 16, 16), (30, 10, 10), (17, 9, 5), (1, 1, 40)]
-ORDINARY = [("quad", lambda: W.structured_quad(4097, 1)), ("hex", lambda: W.structured_hex(17, 16, 16)),
+GROUPED3 = [(1, 1, 1), (5, 4, 3), (16, 8, 8), (10, 10, 10), (17, 9, 5), (1, 1, 40)]
+ORDINARY = [("quad", lambda: W.structured_quad(4097, 1)), ("hex", lambda: W.structured_hex(17, 8, 8)),
             ("quad", lambda: W.quad_grid(9, 6, jitter=0.2, g=np.random.default_rng(3))),
             ("hex", lambda: W.hex_grid(4, 3, 2, jitter=0.15, g=np.random.default_rng(4)))]
 
