@@ -1,5 +1,6 @@
 // The C ABI (include/soptx.h): argument validation, device residency of a mesh
 // and dispatch to the kernels.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -35,7 +36,8 @@ static void free_device(DeviceMesh &d)
     void *ptrs[] = {d.indptr, d.indices, d.cell_node, d.node_off, d.inc_ptr, d.inc,
                     d.pos, d.geo, d.M, d.K, d.scratch, d.Edf, d.kappa, d.K0, d.sectors, d.udf, d.part,
                     d.inc_e, d.inc_a, d.counter, d.xcell, d.qw, d.qdphi, d.qdgeo, d.cg, d.lat_bad, d.stage,
-                    d.kvals, d.sgeo, d.sq, d.cgeo, d.Mf, d.cnrec, d.cinc_e, d.cinc_a, d.crec, d.cticket};
+                    d.kvals, d.sgeo, d.sq, d.cgeo, d.Mf, d.ptoff, d.pia, d.pib, d.pmeta, d.pre, d.prm,
+                    d.cnrec, d.cinc_e, d.cinc_a, d.crec, d.cticket};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (d.cg_exec) cudaGraphExecDestroy(d.cg_exec);
@@ -54,8 +56,9 @@ static cudaError_t ensure_side(soptx_mesh_s &m)
     if (d.side) return cudaSuccess;
     cudaStream_t side = nullptr;
     cudaEvent_t ev[2] = {};
-    // meshes with the strain-energy sensitivities run their assembly on this
-    // stream in the one-call step, at the highest priority (see launch_step)
+    // meshes with the strain-energy sensitivities run their assembly (3D) or
+    // their sensitivities (2D) on this stream in the one-call step, at the
+    // highest priority (see launch_step)
     int least = 0, greatest = 0;
     cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
     if (e == cudaSuccess)
@@ -125,9 +128,170 @@ static soptx_status setup_strain(soptx_mesh_s &m, const RefElement &ref, cudaStr
     return s;
 }
 
-// Tables of the per-call contraction (k_contract_rows): G and |det J| per cell
-// in FP32 (whole float4s), the reference integrals [a][b][k][l] in FP32.
-static soptx_status setup_contract(soptx_mesh_s &m, const RefElement &ref, cudaStream_t st)
+// Tables of the per-call contraction of 2D cells (k_contract_pairs): G and
+// |det J| per cell in FP32 (whole float4s), the reference integrals
+// [a][b][k][l] in FP32, and the node pairs.  K is symmetric, so the block pair
+// (a, b), (b, a) of two nodes
+// that share a cell is assembled once, by whichever of them comes first in the
+// processing order, and each node's diagonal block by the node itself.  The
+// order takes nodes by their first cell (then id), so it sweeps the mesh and
+// both row blocks of a pair are written close together in time.  A pair's
+// records are the cells holding both nodes, in ascending order, each with the
+// reference-integral pair a_loc nb + b_loc.  The pairs of a window of
+// consecutive owners (about kPairWindow pairs) are sorted by cell count, most
+// first, and cut into tiles of 32, so the lanes of a warp walk about as many
+// cells each; a window's last tile is padded with empty pairs (no cells).
+static constexpr size_t kPairWindow = 4096;
+
+static soptx_status setup_contract_pairs(soptx_mesh_s &m, const RefElement &ref, cudaStream_t st)
+{
+    const HostMesh &h = m.h;
+    const int d = h.dim, nb = h.nb, ng = d * d + 1, n4 = d == 3 ? 3 : 2, mp = d == 3 ? 12 : 4;
+    // a pair's cell count has 10 bits in the tables, a value index / d has 32:
+    // larger fans or matrices keep the cached gather
+    for (int64_t n = 0; n < h.nn; n++)
+        if (h.inc_ptr[(size_t)n + 1] - h.inc_ptr[(size_t)n] > 1023) return SOPTX_OK;
+    if ((int64_t)d * h.node_off[(size_t)h.nn] > (int64_t)UINT32_MAX) return SOPTX_OK;
+    std::vector<float4> cg((size_t)h.nc * n4, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int64_t e = 0; e < h.nc; e++) {
+        float *dst = reinterpret_cast<float *>(&cg[(size_t)e * n4]);
+        for (int t = 0; t < ng; t++) dst[t] = (float)h.geo[(size_t)e * ng + t];
+    }
+    std::vector<float> mf((size_t)nb * nb * mp, 0.f);
+    for (int a = 0; a < nb; a++)
+        for (int b = 0; b < nb; b++)
+            for (int k = 0; k < d; k++)
+                for (int l = 0; l < d; l++)
+                    mf[((size_t)a * nb + b) * mp + k * d + l] = (float)ref.M[(((size_t)k * d + l) * nb + a) * nb + b];
+    // processing order: nodes by first cell (the incidences are in ascending cell
+    // order), then id; a counting sort
+    std::vector<int32_t> order((size_t)h.nn), rank((size_t)h.nn);
+    {
+        auto first = [&](int64_t n) -> int64_t {
+            return h.inc_ptr[(size_t)n + 1] > h.inc_ptr[(size_t)n] ? h.inc_e[(size_t)h.inc_ptr[(size_t)n]] : h.nc;
+        };
+        std::vector<int64_t> start((size_t)h.nc + 2, 0);
+        for (int64_t n = 0; n < h.nn; n++) start[(size_t)first(n) + 1]++;
+        for (size_t c = 1; c < start.size(); c++) start[c] += start[c - 1];
+        for (int64_t n = 0; n < h.nn; n++) order[(size_t)start[(size_t)first(n)]++] = (int32_t)n;
+        for (int64_t i = 0; i < h.nn; i++) rank[(size_t)order[(size_t)i]] = (int32_t)i;
+    }
+    // the incidence of each (cell, local node)
+    std::vector<int32_t> cinc((size_t)h.nc * nb, 0);
+    for (int64_t n = 0; n < h.nn; n++)
+        for (int32_t q = h.inc_ptr[(size_t)n]; q < h.inc_ptr[(size_t)n + 1]; q++)
+            cinc[(size_t)h.inc_e[(size_t)q] * nb + h.inc_a[(size_t)q]] = q;
+    std::vector<uint32_t> ia, ib, meta, toff(1, 0u);
+    std::vector<int32_t> re;
+    std::vector<uint16_t> rm;
+    struct WPair {
+        uint32_t pa, pb, meta;
+        size_t r0;
+    };
+    std::vector<WPair> win;
+    std::vector<int32_t> wre, scnt, sstart, sfill, te;
+    std::vector<uint16_t> wrm, tm;
+    std::vector<size_t> idx;
+    auto flush = [&]() {
+        if (win.empty()) return;
+        idx.resize(win.size());
+        for (size_t k = 0; k < idx.size(); k++) idx[k] = k;
+        std::stable_sort(idx.begin(), idx.end(),
+                         [&](size_t x, size_t y) { return (win[x].meta & 1023u) > (win[y].meta & 1023u); });
+        for (size_t t0 = 0; t0 < win.size(); t0 += 32) {
+            const int ct = (int)(win[idx[t0]].meta & 1023u);
+            for (size_t l = 0; l < 32; l++) {
+                const bool real = t0 + l < win.size();
+                const WPair &w = win[idx[real ? t0 + l : t0]];
+                ia.push_back(real ? w.pa : 0u);
+                ib.push_back(real ? w.pb : 0u);
+                meta.push_back(real ? w.meta : 0u);
+            }
+            for (int k = 0; k < ct; k++)
+                for (size_t l = 0; l < 32; l++) {
+                    const bool real = t0 + l < win.size();
+                    const WPair &w = win[idx[real ? t0 + l : t0]];
+                    const bool has = real && k < (int)(w.meta & 1023u);
+                    re.push_back(has ? wre[w.r0 + (size_t)k] : 0);
+                    rm.push_back(has ? wrm[w.r0 + (size_t)k] : (uint16_t)0);
+                }
+            toff.push_back(toff.back() + (uint32_t)ct);
+        }
+        win.clear();
+        wre.clear();
+        wrm.clear();
+    };
+    for (int64_t i = 0; i < h.nn; i++) {
+        const int32_t a = order[(size_t)i];
+        const int32_t q0 = h.inc_ptr[(size_t)a], q1 = h.inc_ptr[(size_t)a + 1];
+        const int64_t off = h.node_off[(size_t)a];
+        const int deg = (int)(h.node_off[(size_t)a + 1] - off);
+        // the owner's records grouped by column block, ascending cells within each
+        scnt.assign((size_t)deg, 0);
+        for (int32_t q = q0; q < q1; q++) {
+            const int32_t *cn = &h.cell_node[(size_t)h.inc_e[(size_t)q] * nb];
+            for (int j = 0; j < nb; j++)
+                if (cn[j] == a || rank[(size_t)cn[j]] > i) scnt[h.pos[(size_t)q * nb + j]]++;
+        }
+        sstart.assign((size_t)deg + 1, 0);
+        for (int p = 0; p < deg; p++) sstart[(size_t)p + 1] = sstart[(size_t)p] + scnt[(size_t)p];
+        sfill.assign(sstart.begin(), sstart.end() - 1);
+        te.resize((size_t)sstart[(size_t)deg]);
+        tm.resize((size_t)sstart[(size_t)deg]);
+        for (int32_t q = q0; q < q1; q++) {
+            const int32_t e = h.inc_e[(size_t)q];
+            const int32_t *cn = &h.cell_node[(size_t)e * nb];
+            const int al = h.inc_a[(size_t)q];
+            for (int j = 0; j < nb; j++)
+                if (cn[j] == a || rank[(size_t)cn[j]] > i) {
+                    const int32_t f = sfill[h.pos[(size_t)q * nb + j]]++;
+                    te[(size_t)f] = e;
+                    tm[(size_t)f] = (uint16_t)(al * nb + j);
+                }
+        }
+        for (int p = 0; p < deg; p++) {
+            const int32_t c = scnt[(size_t)p];
+            if (c == 0) continue;
+            const int32_t b = h.nbr[(size_t)(off + p)];
+            // the block of a in b's rows, from the pair's first cell
+            const int32_t e = te[(size_t)sstart[(size_t)p]];
+            const int al = tm[(size_t)sstart[(size_t)p]] / nb, bl = tm[(size_t)sstart[(size_t)p]] % nb;
+            const int pba = h.pos[(size_t)cinc[(size_t)e * nb + bl] * nb + al];
+            const int64_t offb = h.node_off[(size_t)b];
+            const int degb = (int)(h.node_off[(size_t)b + 1] - offb);
+            win.push_back(WPair{(uint32_t)(d * off + p), (uint32_t)(d * offb + pba),
+                                (uint32_t)c | ((uint32_t)(d * deg) << 10) | ((uint32_t)(d * degb) << 21), wre.size()});
+            wre.insert(wre.end(), te.begin() + sstart[(size_t)p], te.begin() + sstart[(size_t)p + 1]);
+            wrm.insert(wrm.end(), tm.begin() + sstart[(size_t)p], tm.begin() + sstart[(size_t)p + 1]);
+        }
+        if (win.size() >= kPairWindow) flush();
+    }
+    flush();
+    // the kernel stages chunks of 8 tiles: whole chunks of pairs, and 16 record
+    // offsets from each chunk's first
+    const int64_t ntiles = (int64_t)toff.size() - 1, nchunks = (ntiles + 7) / 8;
+    toff.resize((size_t)(nchunks * 8 + 16), toff.back());
+    ia.resize((size_t)(nchunks * 8 * 32), 0u);
+    ib.resize((size_t)(nchunks * 8 * 32), 0u);
+    meta.resize((size_t)(nchunks * 8 * 32), 0u);
+    soptx_status s = upload(&m.d.cgeo, cg, st, m.device_bytes, "cell geometry");
+    if (s == SOPTX_OK) s = upload(&m.d.Mf, mf, st, m.device_bytes, "reference integrals (FP32)");
+    if (s == SOPTX_OK) s = upload(&m.d.ptoff, toff, st, m.device_bytes, "pair tiles");
+    if (s == SOPTX_OK) s = upload(&m.d.pia, ia, st, m.device_bytes, "pair blocks");
+    if (s == SOPTX_OK) s = upload(&m.d.pib, ib, st, m.device_bytes, "pair transposed blocks");
+    if (s == SOPTX_OK) s = upload(&m.d.pmeta, meta, st, m.device_bytes, "pair counts and row lengths");
+    if (s == SOPTX_OK) s = upload(&m.d.pre, re, st, m.device_bytes, "pair cells");
+    if (s == SOPTX_OK) s = upload(&m.d.prm, rm, st, m.device_bytes, "pair reference integrals");
+    if (s == SOPTX_OK) s = upload(&m.d.cticket, std::vector<unsigned>(2, 0u), st, m.device_bytes, "chunk counter");
+    if (s == SOPTX_OK) {
+        m.d.ptiles = ntiles;
+        m.d.contract = true;
+    }
+    return s;
+}
+
+// Tables of the node-owner contraction of 3D cells (k_contract_rows).
+static soptx_status setup_contract_rows(soptx_mesh_s &m, const RefElement &ref, cudaStream_t st)
 {
     const HostMesh &h = m.h;
     const int d = h.dim, nb = h.nb, ng = d * d + 1, n4 = d == 3 ? 3 : 2, mp = d == 3 ? 12 : 4;
@@ -254,6 +418,12 @@ static soptx_status setup_contract(soptx_mesh_s &m, const RefElement &ref, cudaS
     if (s == SOPTX_OK) s = upload(&m.d.cticket, std::vector<unsigned>(2, 0u), st, m.device_bytes, "round counter");
     if (s == SOPTX_OK) m.d.contract = true;
     return s;
+}
+
+// FP32 element matrices of affine cells: the tables of the per-call contraction.
+static soptx_status setup_contract(soptx_mesh_s &m, const RefElement &ref, cudaStream_t st)
+{
+    return m.h.dim == 2 ? setup_contract_pairs(m, ref, st) : setup_contract_rows(m, ref, st);
 }
 
 static bool material_ok(const soptx_material *m, int dim, Material &out, std::string &err)

@@ -2,24 +2,34 @@
 // registers from the reference integrals and each cell's Jacobian, and the
 // sensitivities from the strain energy at quadrature points.
 //
-//  k_contract_rows : FP32 element matrices, never stored.  A group of NB lanes
-//                    (NB = basis functions per cell) owns the d rows of one
-//                    node and walks the node's incident cells as a chain
-//                    fixed at mesh creation (each next cell shares as many
-//                    of the lanes' current column nodes as possible); for
-//                    each cell, a lane takes one local node b and forms the
-//                    d x d block K_e^0[(a,.),(b,.)] of the node's local
-//                    index a by the
-//                    fast assembly of Sec. 3.2.2: the reference integrals
+//  k_contract_pairs : FP32 element matrices of 2D cells, never stored.  K is
+//                    symmetric, so one lane serves a pair of nodes {a, b} (a
+//                    first in the processing order, or b = a): it walks the
+//                    cells that hold both, in ascending order, and for each
+//                    forms the d x d block K_e^0[(a,.),(b,.)] by the fast
+//                    assembly of Sec. 3.2.2: the reference integrals
 //                    M^{kl}_{ab} = int d_k phi_a d_l phi_b (shared memory,
 //                    FP32) contracted with the cell's G = J^-1 and |det J|,
 //                        P_ij = |det J| sum_kl G_ki G_lj M^{kl}_{ab},
 //                        K_ij = lam P_ij + mu P_ji + mu delta_ij tr P,
-//                    and adds E_e K_ij into the rows' float-pair accumulators
-//                    in shared memory (FP64-accurate sums in the chain's
-//                    fixed order, no atomics); a lane whose column block
-//                    continues into the next cell keeps its sums in
-//                    registers meanwhile.  The rows leave as FP64 values.
+//                    and adds E_e K_ij into float-pair sums held in
+//                    registers (FP64-accurate, no atomics, a fixed order).
+//                    The block leaves as FP64 values into row block (a, b)
+//                    and, transposed, into (b, a).  Each lane's pair, its
+//                    cells and both destinations come from tables made at
+//                    mesh creation; a warp's 32 pairs have about as many
+//                    cells each.
+//  k_contract_rows : the same blocks for 3D cells, with the rows of one node
+//                    owned by a group of nb lanes (nb = basis functions per
+//                    cell) that walks the node's incident cells as a chain
+//                    fixed at mesh creation (each next cell shares as many of
+//                    the lanes' current column nodes as possible); lane b takes
+//                    the cell's local node b and adds E_e K into the rows'
+//                    float-pair accumulators in shared memory, keeping them in
+//                    registers while its column block continues into the next
+//                    cell.  (The pair layout in 3D writes every transposed
+//                    block as three scattered 24-byte row pieces; the L2 then
+//                    writes partly filled sectors back and fetches them again.)
 //  k_strain_energy : s_e = u_e^T K_e^0 u_e = int_e lam (div u)^2 + 2 mu eps:eps
 //                    by a quadrature rule exact for the energy density of the
 //                    cell's order, one thread per cell: the reference
@@ -52,6 +62,31 @@ template <int D> struct MPad {
     static constexpr int n = D == 3 ? 12 : 4;
 };
 
+// The pair tables made at mesh creation.  Pairs come in tiles of 32, one per
+// lane; tile t's records are toff[t] * 32 ... toff[t + 1] * 32 - 1, record k of
+// lane l at toff[t] * 32 + 32 k + l (lanes with fewer cells than the tile's
+// longest are padded with cell 0).  The pair arrays are padded to whole chunks
+// of 8 tiles and toff by 16 entries past the last chunk.
+struct PairArgs {
+    int64_t ntiles;
+    unsigned *__restrict__ ticket;       // [0] chunks handed out, [1] CTAs done (both zero between calls)
+    const uint32_t *__restrict__ toff;   // first record of each tile / 32
+    const uint32_t *__restrict__ ia;     // [32 ntiles] value index of block (a, b), divided by d
+    const uint32_t *__restrict__ ib;     // value index of block (b, a) / d (equal to ia when b = a)
+    const uint32_t *__restrict__ meta;   // cells (bits 0-9), row length of a's rows (10-20), of b's (21-31)
+    const int32_t *__restrict__ re;      // per record: the cell
+    const uint16_t *__restrict__ rm;     // per record: reference-integral pair a_loc nb + b_loc
+    const float4 *__restrict__ cgeo;
+    const float *__restrict__ Mf;
+    int nmf;                             // floats in Mf
+    const float2 *__restrict__ Edf;
+    const double *__restrict__ rho;
+    SimpParams sp;
+    float lam, mu;
+    double *__restrict__ vals;
+};
+
+// The node-owner contraction of 3D cells (k_contract_rows).
 struct ContractArgs {
     int64_t nn;
     int max_deg;
@@ -70,8 +105,7 @@ struct ContractArgs {
     double *__restrict__ vals;
 };
 
-// The d x d block K_e^0[(a,.),(b,.)] in FP32 from the pair's reference
-// integrals M (d x d, row-major) and the cell's G and |det J|.
+
 template <int D>
 __device__ __forceinline__ void contract_block(const float *M, const float *G, float det, float lam, float mu,
                                                float K[D][D])
@@ -182,6 +216,7 @@ __device__ __noinline__ void contract_node_fp64(const ContractArgs &A, const flo
 template <int D, int NB, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs A)
 {
+    static_assert(D == 3, "the node-owner contraction serves 3D cells");
     constexpr int NPW = 32 / NB;
     constexpr int MP = MPad<D>::n;
     constexpr int G4 = CGeo<D>::n4;
@@ -204,7 +239,6 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
     // that starts late, beside another kernel, simply takes fewer.  The last warp
     // to finish sets the counter back to zero.  A node's record is one 16-byte load.
     const int64_t rounds = (A.nn + NPW - 1) / NPW;
-    const bool aligned16 = (reinterpret_cast<uintptr_t>(A.vals) & 15u) == 0;
     auto grab = [&]() -> int64_t {
         unsigned t = 0;
         if (lane == 0) t = atomicAdd(A.ticket, 1u);
@@ -293,19 +327,10 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
         const int64_t off = N0.off;
         const int deg = N0.deg;
         const int32_t q0 = N0.q0, cnt = N0.cnt;
-        // 3D: no zeroing, every block of the rows is met by some cell and its first
-        // meeting starts the sums from zero; 2D (few rows, a tight register budget)
-        // zeroes the rows first
-        constexpr bool kFirst = D == 3;   // (in 2D it spilled at the 80-register cap: P3 236 -> 254 us)
-        // 2D: a block's last meeting converts it and stores it straight to the rows
-        // (few contributions per value there), so there is no output pass
-        constexpr bool kDirect = D == 2;
+        // no zeroing: every block of the rows is met by some cell, and its first
+        // meeting starts the sums from zero
         double *const out = A.vals + (int64_t)D * D * off;
         const int rowlen = D * deg, blk = D * rowlen;
-        if (!kFirst) {
-            for (int t = b; t < blk; t += NB) accs[gacc + t] = make_float2(0.f, 0.f);
-            __syncwarp();
-        }
 
         const int ro1 = rowlen, ro2 = 2 * rowlen;
         bool bad = false;
@@ -338,7 +363,7 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
                 const int rbase[3] = {base, base + ro1, base + ro2};
                 const bool keep = it + 1 < cnt && (nxt.p & 511) == slot;
                 if (!held) {
-                    if (kFirst && (cur.p & 0x4000)) {
+                    if (cur.p & 0x4000) {
 #pragma unroll
                         for (int i = 0; i < D; i++)
 #pragma unroll
@@ -361,36 +386,10 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
                         acc_add(v[i][j].x, v[i][j].y, df{ph, pl});
                     }
                 if (!keep) {
-                    if (kDirect && (cur.p & 0x8000)) {
 #pragma unroll
-                        for (int i = 0; i < D; i++) {
-                            double *o = out + (int64_t)i * rowlen + D * slot;
-                            // row 0 widens on the FP64 pipe, row 1 with integer operations
-                            // only: the two pipes share the conversions
-                            double d0, d1;
-                            if (i == 0) {
-                                d0 = pair_to_double(v[i][0].x, v[i][0].y);
-                                d1 = pair_to_double(v[i][1].x, v[i][1].y);
-                            } else {
-                                float h, l;
-                                two_sum(v[i][0].x, v[i][0].y, h, l);
-                                d0 = df_to_double(h, l);
-                                two_sum(v[i][1].x, v[i][1].y, h, l);
-                                d1 = df_to_double(h, l);
-                            }
-                            if (aligned16) {
-                                __stcs(reinterpret_cast<double2 *>(o), make_double2(d0, d1));
-                            } else {
-                                __stcs(o, d0);
-                                __stcs(o + 1, d1);
-                            }
-                        }
-                    } else {
+                    for (int i = 0; i < D; i++)
 #pragma unroll
-                        for (int i = 0; i < D; i++)
-#pragma unroll
-                            for (int j = 0; j < D; j++) accs[rbase[i] + j] = v[i][j];
-                    }
+                        for (int j = 0; j < D; j++) accs[rbase[i] + j] = v[i][j];
                 }
                 held = keep;
             }
@@ -410,7 +409,7 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
         const unsigned badm = __ballot_sync(kFull, bad);
         if (has && (badm & gmask)) {
             contract_node_fp64<D, NB>(A, Ms, gmask, b, off, deg, q0, cnt, reinterpret_cast<double *>(accs + gacc));
-        } else if (has && !kDirect) {
+        } else if (has) {
             // the rows leave as FP64 values, two per store where the destination is
             // 16-byte aligned (an odd 8-byte head is stored on its own)
             const int head = (int)((reinterpret_cast<uintptr_t>(out) >> 3) & 1u);
@@ -442,6 +441,274 @@ __global__ void __launch_bounds__(256, MINB) k_contract_rows(const ContractArgs 
     if (lane == 0) {
         __threadfence();
         if (atomicAdd(A.ticket + 1, 1u) == gridDim.x * (unsigned)wpb - 1u) {
+            A.ticket[0] = 0u;
+            A.ticket[1] = 0u;
+        }
+    }
+}
+
+// Row i of a d x d block of FP64 values at o (row stride rl), and the block's
+// transpose at ot (row stride rlt): a block row of two values is one 16-byte
+// store when the destination is aligned.
+template <int D>
+__device__ __forceinline__ void store_block(double *o, int rl, double *ot, int rlt, bool both, bool al16,
+                                            const double (&d)[D][D])
+{
+#pragma unroll
+    for (int i = 0; i < D; i++) {
+        double *r = o + (int64_t)i * rl;
+        if (D == 2 && al16) {
+            *reinterpret_cast<double2 *>(r) = make_double2(d[i][0], d[i][1]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < D; j++) r[j] = d[i][j];
+        }
+    }
+    if (!both) return;
+#pragma unroll
+    for (int j = 0; j < D; j++) {
+        double *r = ot + (int64_t)j * rlt;
+        if (D == 2 && al16) {
+            *reinterpret_cast<double2 *>(r) = make_double2(d[0][j], d[1][j]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < D; i++) r[i] = d[i][j];
+        }
+    }
+}
+
+// Plain-FP64 redo of one lane's pair (a modulus outside the float-pair range):
+// the same FP32 blocks times E(rho_e) in FP64, summed in the same cell order.
+template <int D>
+__device__ __noinline__ void pair_fp64(const PairArgs &A, const float *Ms, int64_t rb, int cnt, uint32_t pa,
+                                       uint32_t pb, uint32_t meta, bool al16)
+{
+    double acc[D][D];
+#pragma unroll
+    for (int i = 0; i < D; i++)
+#pragma unroll
+        for (int j = 0; j < D; j++) acc[i][j] = 0.0;
+    for (int k = 0; k < cnt; k++) {
+        const int64_t r = rb + (int64_t)k * 32;
+        const int32_t e = A.re[r];
+        float G[D * D], det, M[D * D], K[D][D];
+        load_cgeo<D>(A.cgeo, e, G, det);
+        load_mpair<D>(Ms, A.rm[r], M);
+        contract_block<D>(M, G, det, A.lam, A.mu, K);
+        const double E = simp_E(A.sp, A.rho[e]);
+#pragma unroll
+        for (int i = 0; i < D; i++)
+#pragma unroll
+            for (int j = 0; j < D; j++) acc[i][j] += E * (double)K[i][j];
+    }
+    store_block<D>(A.vals + (int64_t)D * pa, (int)((meta >> 10) & 2047u), A.vals + (int64_t)D * pb,
+                   (int)(meta >> 21), pa != pb, al16, acc);
+}
+
+// Asynchronous 16-byte copies global -> shared (cp.async); the waits are the
+// hardware's (cp.async.wait_group), no polling.
+__device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// A chunk is kChunkTiles consecutive tiles, one per warp of a CTA.  Its tables
+// are staged in shared memory: the tiles' record offsets, the lanes' pairs, and
+// the chunk's first kChunkRecs records (a tile's records past those are read
+// from global memory).
+constexpr int kChunkTiles = 8;
+constexpr int kChunkRecs = 2048;
+struct ChunkBuf {
+    uint32_t toff[16];
+    uint32_t meta[kChunkTiles * 32], pa[kChunkTiles * 32], pb[kChunkTiles * 32];
+    int32_t re[kChunkRecs];
+    uint16_t rm[kChunkRecs];
+};
+
+// A persistent grid (the CTAs that fit); each CTA takes chunks in increasing
+// order from a counter, so at any time the GPU works through a contiguous range
+// of tiles and the two destinations of a pair's block meet in L2.  The next
+// chunk's tables are copied into the other buffer while this one is worked;
+// within a tile the cell one position ahead is loaded while the current one is
+// contracted.
+template <int D>
+__global__ void __launch_bounds__(256, D == 2 ? 4 : 3) k_contract_pairs(const PairArgs A)
+{
+    constexpr int G4 = CGeo<D>::n4;
+    extern __shared__ float4 csm4[];
+    ChunkBuf *bufs = reinterpret_cast<ChunkBuf *>(csm4);
+    float *Ms = reinterpret_cast<float *>(bufs + 2);
+    for (int t = threadIdx.x; t < A.nmf; t += blockDim.x) Ms[t] = A.Mf[t];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool al16 = (reinterpret_cast<uintptr_t>(A.vals) & 15u) == 0;
+    const int64_t nchunks = (A.ntiles + kChunkTiles - 1) / kChunkTiles;
+    // a chunk's first record / 32 and the next chunk's, loaded a chunk ahead of
+    // their use
+    auto bounds = [&](int64_t c, uint32_t &r0, uint32_t &r1) {
+        r0 = r1 = 0u;
+        if (c < nchunks) {
+            r0 = __ldg(A.toff + c * kChunkTiles);
+            r1 = __ldg(A.toff + min((c + 1) * kChunkTiles, A.ntiles));
+        }
+    };
+    auto issue = [&](int64_t c, uint32_t r0, uint32_t r1, ChunkBuf &B) {
+        const int64_t t0 = c * kChunkTiles;
+        const int nrec = (int)min((r1 - r0) * 32u, (uint32_t)kChunkRecs);
+        const int nre = nrec / 4, nrm = nrec / 8;   // 16-byte pieces
+        const int64_t rbase = (int64_t)r0 * 32;
+        for (int p = threadIdx.x; p < 4 + 3 * 64 + nre + nrm; p += blockDim.x) {
+            if (p < 4) {
+                cp_async16(B.toff + 4 * p, A.toff + t0 + 4 * p);
+            } else if (p < 4 + 3 * 64) {
+                const int q = p - 4, w = q >> 6, o = (q & 63) * 4;
+                const uint32_t *src = (w == 0 ? A.meta : w == 1 ? A.ia : A.ib) + t0 * 32 + o;
+                cp_async16((w == 0 ? B.meta : w == 1 ? B.pa : B.pb) + o, src);
+            } else if (p < 4 + 3 * 64 + nre) {
+                const int o = (p - 4 - 3 * 64) * 4;
+                cp_async16(B.re + o, A.re + rbase + o);
+            } else {
+                const int o = (p - 4 - 3 * 64 - nre) * 8;
+                cp_async16(B.rm + o, A.rm + rbase + o);
+            }
+        }
+    };
+    struct Cell {
+        float4 g[G4];
+        float2 E;
+    };
+    auto fetch = [&](int32_t e, Cell &c) {
+        const float4 *gp = A.cgeo + (int64_t)G4 * e;
+#pragma unroll
+        for (int w = 0; w < G4; w++) c.g[w] = __ldg(gp + w);
+        c.E = __ldg(A.Edf + e);
+    };
+    // chunks are taken from a counter, so a CTA that starts late beside another
+    // kernel simply takes fewer; three ahead: the chunk being worked (c), the one
+    // being copied (cn), the one whose bounds are loading (cnn), and the ticket
+    // of the next in flight meanwhile
+    __shared__ unsigned s_ticket;
+    auto grab = [&]() -> int64_t {
+        if (threadIdx.x == 0) s_ticket = atomicAdd(A.ticket, 1u);
+        __syncthreads();
+        const int64_t v = s_ticket;
+        __syncthreads();
+        return v;
+    };
+    int64_t c = grab(), cn = grab(), cnn = grab();
+    int cur = 0;
+    uint32_t a0, a1, b0, b1;
+    bounds(c, a0, a1);
+    bounds(cn, b0, b1);
+    if (c < nchunks) issue(c, a0, a1, bufs[0]);
+    cp_async_commit();
+    while (c < nchunks) {
+        if (cn < nchunks) issue(cn, b0, b1, bufs[cur ^ 1]);
+        cp_async_commit();
+        bounds(cnn, b0, b1);
+        unsigned tk = 0u;
+        if (threadIdx.x == 0) tk = atomicAdd(A.ticket, 1u);
+        cp_async_wait_1();
+        __syncthreads();
+        const ChunkBuf &B = bufs[cur];
+        const int64_t t = c * kChunkTiles + warp;
+        if (t < A.ntiles) {
+            const int ct = (int)(B.toff[warp + 1] - B.toff[warp]);
+            const int rel = (int)(B.toff[warp] - B.toff[0]) * 32 + lane;
+            const uint32_t meta = B.meta[warp * 32 + lane], pa = B.pa[warp * 32 + lane], pb = B.pb[warp * 32 + lane];
+            const int cnt = (int)(meta & 1023u);
+            const int64_t gbase = (int64_t)B.toff[0] * 32;
+            auto rec = [&](int k, int32_t &e, int &m) {
+                const int r = rel + min(k, ct - 1) * 32;
+                if (r < kChunkRecs) {
+                    e = B.re[r];
+                    m = B.rm[r];
+                } else {
+                    e = __ldg(A.re + gbase + r);
+                    m = __ldg(A.rm + gbase + r);
+                }
+            };
+            int32_t e0, e1;
+            int m0, m1;
+            rec(0, e0, m0);
+            rec(1, e1, m1);
+            Cell c0;
+            fetch(e0, c0);
+            float2 v[D][D];
+            bool bad = false;
+            for (int k = 0; k < ct; k++) {
+                Cell c1;
+                fetch(e1, c1);
+                if (k < cnt) {
+                    bad |= isnan(c0.E.y);
+                    float G[D * D], det;
+                    if (D == 3) {
+                        G[0] = c0.g[0].x; G[1] = c0.g[0].y; G[2] = c0.g[0].z; G[3] = c0.g[0].w;
+                        G[4] = c0.g[1].x; G[5] = c0.g[1].y; G[6] = c0.g[1].z; G[7] = c0.g[1].w;
+                        G[8] = c0.g[2].x;
+                        det = c0.g[2].y;
+                    } else {
+                        G[0] = c0.g[0].x; G[1] = c0.g[0].y; G[2] = c0.g[0].z; G[3] = c0.g[0].w;
+                        det = c0.g[1].x;
+                    }
+                    float M[D * D], K[D][D];
+                    load_mpair<D>(Ms, m0, M);
+                    contract_block<D>(M, G, det, A.lam, A.mu, K);
+#pragma unroll
+                    for (int i = 0; i < D; i++)
+#pragma unroll
+                        for (int j = 0; j < D; j++) {
+                            // E K as a pair: TwoProd of the head, the tail's product
+                            const float kk = K[i][j];
+                            const float ph = __fmul_rn(c0.E.x, kk);
+                            const float pl = __fmaf_rn(c0.E.y, kk, __fmaf_rn(c0.E.x, kk, -ph));
+                            if (k == 0) {
+                                v[i][j] = make_float2(ph, pl);
+                            } else {
+                                acc_add(v[i][j].x, v[i][j].y, df{ph, pl});
+                            }
+                        }
+                }
+                c0 = c1;
+                m0 = m1;
+                rec(k + 2, e1, m1);
+            }
+            // a lane whose pair met an out-of-range modulus redoes it in FP64
+            if (__any_sync(kFull, bad) && bad) {
+                pair_fp64<D>(A, Ms, gbase + rel, cnt, pa, pb, meta, al16);
+            } else if (cnt > 0) {
+                // the values leave as FP64: half the entries widened and added on the
+                // FP64 pipe, half with integer operations only
+                double d[D][D];
+#pragma unroll
+                for (int i = 0; i < D; i++)
+#pragma unroll
+                    for (int j = 0; j < D; j++) {
+                        if (((i * D + j) & 1) == 0) {
+                            d[i][j] = pair_to_double(v[i][j].x, v[i][j].y);
+                        } else {
+                            float hh, ll;
+                            two_sum(v[i][j].x, v[i][j].y, hh, ll);
+                            d[i][j] = df_to_double(hh, ll);
+                        }
+                    }
+                store_block<D>(A.vals + (int64_t)D * pa, (int)((meta >> 10) & 2047u), A.vals + (int64_t)D * pb,
+                               (int)(meta >> 21), pa != pb, al16, d);
+            }
+        }
+        if (threadIdx.x == 0) s_ticket = tk;
+        __syncthreads();
+        c = cn;
+        cn = cnn;
+        cnn = s_ticket;
+        cur ^= 1;
+    }
+    // the last CTA to finish sets the counter back to zero for the next call
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(A.ticket + 1, 1u) == gridDim.x - 1u) {
             A.ticket[0] = 0u;
             A.ticket[1] = 0u;
         }
@@ -717,8 +984,46 @@ __global__ void __launch_bounds__(128) k_strain_energy_warp(const StrainArgs A)
     if (A.c) grid_sum_last_block(mine, A.partial, A.counter, A.c);
 }
 
+template <int D>
+cudaError_t pairs_launch(const soptx_mesh_s &m, const double *rho, double *vals, cudaStream_t st)
+{
+    const auto &h = m.h;
+    PairArgs A;
+    A.ntiles = m.d.ptiles;
+    A.ticket = m.d.cticket;
+    A.toff = m.d.ptoff;
+    A.ia = m.d.pia;
+    A.ib = m.d.pib;
+    A.meta = m.d.pmeta;
+    A.re = m.d.pre;
+    A.rm = m.d.prm;
+    A.cgeo = m.d.cgeo;
+    A.Mf = m.d.Mf;
+    A.nmf = h.nb * h.nb * MPad<D>::n;
+    A.Edf = m.d.Edf;
+    A.rho = rho;
+    A.sp = simp_params(m.mat);
+    A.lam = (float)m.mat.lam;
+    A.mu = (float)m.mat.mu;
+    A.vals = vals;
+    const size_t smem = 2 * sizeof(ChunkBuf) + (size_t)A.nmf * sizeof(float);
+    auto kern = k_contract_pairs<D>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    // the CTAs that fit at once, each taking chunks from the counter
+    int dev = 0, sms = 0, per_sm = 0;
+    err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    if (err != cudaSuccess) return err;
+    const int64_t nchunks = (A.ntiles + kChunkTiles - 1) / kChunkTiles;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nchunks, (int64_t)sms * std::max(per_sm, 1)));
+    kern<<<grid, 256, smem, st>>>(A);
+    return cudaGetLastError();
+}
+
 template <int D, int NB, int MINB>
-cudaError_t contract_launch(const soptx_mesh_s &m, const double *rho, double *vals, cudaStream_t st)
+cudaError_t rows_launch(const soptx_mesh_s &m, const double *rho, double *vals, cudaStream_t st)
 {
     const auto &h = m.h;
     ContractArgs A;
@@ -763,28 +1068,25 @@ cudaError_t contract_launch(const soptx_mesh_s &m, const double *rho, double *va
     return cudaGetLastError();
 }
 
+
 }  // namespace
 
-// CTAs per SM each contraction layout is compiled for (its register cap).
-static int contract_minb(int dim, int nb) { return dim == 2 ? 3 : (nb >= 20 ? 1 : 2); }
+// CTAs per SM each node-owner layout (3D) is compiled for (its register cap).
+static int rows_minb(int nb) { return nb >= 20 ? 1 : 2; }
 
-static bool contract_layout(int dim, int nb)
-{
-    if (dim == 2) return nb == 3 || nb == 4 || nb == 6 || nb == 9 || nb == 10 || nb == 16;
-    return dim == 3 && (nb == 4 || nb == 8 || nb == 10 || nb == 20 || nb == 27);
-}
-
-// Whether the contraction serves this cell type: a compiled layout, and the
-// reference integrals plus one warp's accumulators (at the largest node
-// degree) fit in a CTA's share of shared memory.
+// Whether the contraction serves this cell type.  2D (the pair kernel): the
+// reference integrals fit in shared memory and a node's block row, twice its
+// degree, fits the tables' 11 bits.  3D (the node-owner kernel): a compiled
+// layout, and the reference integrals plus one warp's row accumulators (at the
+// largest node degree) fit in a CTA's share of shared memory.
 bool contract_fits(int dim, int nb, int max_deg)
 {
+    if (dim == 2) return nb <= 16 && 2 * max_deg <= 2047;
     // a lane record holds the column block in 9 bits and the local node in 5
-    if (!contract_layout(dim, nb) || nb > 32 || max_deg > 512) return false;
-    const size_t mbytes = (size_t)nb * nb * (dim == 3 ? 12 : 4) * sizeof(float);
-    const size_t per_warp = (size_t)(32 / nb) * dim * dim * max_deg * sizeof(float2);
-    const int minb = contract_minb(dim, nb);
-    const size_t cta_smem = std::min<size_t>(200 * 1024, (228 * 1024) / minb - 1024);
+    if (dim != 3 || !(nb == 4 || nb == 8 || nb == 10 || nb == 20 || nb == 27) || max_deg > 512) return false;
+    const size_t mbytes = (size_t)nb * nb * 12 * sizeof(float);
+    const size_t per_warp = (size_t)(32 / nb) * 9 * max_deg * sizeof(float2);
+    const size_t cta_smem = std::min<size_t>(200 * 1024, (228 * 1024) / rows_minb(nb) - 1024);
     return mbytes + per_warp <= cta_smem;
 }
 
@@ -794,18 +1096,17 @@ cudaError_t launch_contract_assemble(const soptx_mesh_s &m, const double *rho, d
     const auto &h = m.h;
     cudaError_t err = launch_prep(m, rho, nullptr, st);
     if (err != cudaSuccess) return err;
+    if (h.dim == 2) return m.d.ptiles == 0 ? cudaSuccess : pairs_launch<2>(m, rho, vals, st);
     if (h.nn == 0 || h.nnz == 0) return cudaSuccess;
-    const int nb = h.nb;
-#define SOPTX_CT(DD, NBB, MINB)                                     \
-    if (h.dim == DD && nb == NBB) return contract_launch<DD, NBB, MINB>(m, rho, vals, st);
-    SOPTX_CT(2, 3, 3) SOPTX_CT(2, 4, 3) SOPTX_CT(2, 6, 3) SOPTX_CT(2, 9, 3) SOPTX_CT(2, 10, 3) SOPTX_CT(2, 16, 3)
-    SOPTX_CT(3, 4, 2) SOPTX_CT(3, 8, 2) SOPTX_CT(3, 10, 2) SOPTX_CT(3, 20, 1) SOPTX_CT(3, 27, 1)
+#define SOPTX_CT(NBB, MINB)                                     \
+    if (h.nb == NBB) return rows_launch<3, NBB, MINB>(m, rho, vals, st);
+    SOPTX_CT(4, 2) SOPTX_CT(8, 2) SOPTX_CT(10, 2) SOPTX_CT(20, 1) SOPTX_CT(27, 1)
 #undef SOPTX_CT
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_strain_sensitivity(const soptx_mesh_s &m, const double *rho, const double *u, double *out,
-                                      double *c, const double *gscale, cudaStream_t st)
+                                      double *c, const double *gscale, cudaStream_t st, int max_grid)
 {
     const auto &h = m.h;
     if (h.nc == 0) return c ? cudaMemsetAsync(c, 0, sizeof(double), st) : cudaSuccess;
@@ -837,19 +1138,21 @@ cudaError_t launch_strain_sensitivity(const soptx_mesh_s &m, const double *rho, 
     if ((int64_t)h.nb * A.nq >= 256) {
         // a warp per cell: 4 warps per block, each staging one cell's displacements
         const size_t smem = (size_t)4 * h.nb * h.dim * vb;
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((h.nc + 3) / 4, m.d.scratch_len));
+        int64_t grid = std::max<int64_t>(1, std::min<int64_t>((h.nc + 3) / 4, m.d.scratch_len));
+        if (max_grid > 0) grid = std::min<int64_t>(grid, max_grid);
         auto k = h.dim == 3 ? (f32 ? k_strain_energy_warp<3, false> : k_strain_energy_warp<3, true>)
                             : (f32 ? k_strain_energy_warp<2, false> : k_strain_energy_warp<2, true>);
         cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
-        k<<<grid, 128, smem, st>>>(A);
+        k<<<(int)grid, 128, smem, st>>>(A);
         return cudaGetLastError();
     }
     // threads per block: a power of two whose staging fits in 96 KiB
     int T = 128;
     while (T > 32 && (size_t)T * h.nb * h.dim * vb > 96 * 1024) T >>= 1;
     const size_t smem = (size_t)T * h.nb * h.dim * vb;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((h.nc + T - 1) / T, m.d.scratch_len));
+    int64_t grid = std::max<int64_t>(1, std::min<int64_t>((h.nc + T - 1) / T, m.d.scratch_len));
+    if (max_grid > 0) grid = std::min<int64_t>(grid, max_grid);
     void (*k)(StrainArgs) = nullptr;
 #define SOPTX_SE(DD, NBB)                                                                                     \
     if (h.dim == DD && (NBB == 0 || h.nb == NBB) && !k)                                                      \
@@ -859,7 +1162,7 @@ cudaError_t launch_strain_sensitivity(const soptx_mesh_s &m, const double *rho, 
 #undef SOPTX_SE
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    k<<<grid, T, smem, st>>>(A);
+    k<<<(int)grid, T, smem, st>>>(A);
     return cudaGetLastError();
 }
 

@@ -124,15 +124,24 @@ struct DeviceMesh {
     float2 *sq = nullptr;          //   quadrature: weights [snq], reference gradients [snq][nb][d]
     int snq = 0;
     // FP32 element matrices of affine cells: assembled by contraction per call
-    bool contract = false;         // the assembly takes k_contract_rows
+    bool contract = false;         // the assembly takes k_contract_pairs (2D) or k_contract_rows (3D)
     float4 *cgeo = nullptr;        //   [nc][2 or 3] G and |det J| in FP32
     float *Mf = nullptr;           //   [nb][nb][4 or 12] reference integrals in FP32
+    // 2D: node pairs {a, b} (b = a, or b after a), in tiles of 32
+    int64_t ptiles = 0;            //   tiles
+    uint32_t *ptoff = nullptr;     //   [8 chunks + 16] first record of each tile / 32
+    uint32_t *pia = nullptr;       //   [256 chunks] value index of block (a, b) / 2
+    uint32_t *pib = nullptr;       //   [256 chunks] value index of block (b, a) / 2
+    uint32_t *pmeta = nullptr;     //   [256 chunks] cells | a's row length << 10 | b's << 21
+    int32_t *pre = nullptr;        //   per record: the cell (ascending per pair)
+    uint16_t *prm = nullptr;       //   per record: a_loc nb + b_loc
+    // 3D: each node's cells as a chain, walked by the node's group of lanes
     int4 *cnrec = nullptr;         //   [nn] nodes by incident-cell count, largest first: row block
                                    //   offset (2 ints), first incidence, cells << 16 | degree
     int32_t *cinc_e = nullptr;     //   [ninc] each node's cells in the contraction's chain order
     uint8_t *cinc_a = nullptr;     //   [ninc] the node's local index in those cells
     uint16_t *crec = nullptr;      //   [ninc][nb] per lane: block p, local node b << 9, first/last flags
-    unsigned *cticket = nullptr;   //   [2] round counter and finished warps (zero between calls)
+    unsigned *cticket = nullptr;   //   [2] work counter and finished warps or CTAs (zero between calls)
     // equilibrium solve (allocated by the first soptx_solve_cg)
     double *cg = nullptr;          // r z p q diag [ndof], scalars, partials, counters
     cudaGraphExec_t cg_exec = nullptr; // the CG iterations between two checks, as a graph
@@ -198,8 +207,10 @@ cudaError_t launch_prep(const soptx_mesh_s &m, const double *rho, const double *
 // contract.cu
 bool contract_fits(int dim, int nb, int max_deg);
 cudaError_t launch_contract_assemble(const soptx_mesh_s &m, const double *rho, double *vals, cudaStream_t st);
+// max_grid > 0 caps the blocks (the kernel loops over the cells): beside a
+// persistent assembly, a block per SM leaves it the rest of the GPU
 cudaError_t launch_strain_sensitivity(const soptx_mesh_s &m, const double *rho, const double *u, double *out,
-                                      double *c, const double *gscale, cudaStream_t st);
+                                      double *c, const double *gscale, cudaStream_t st, int max_grid = 0);
 cudaError_t launch_step(const soptx_mesh_s &m, const double *rho, const double *u, double *vals, double *dc,
                         double *c, cudaStream_t st, const double *gscale = nullptr);
 __global__ void k_reduce_partials(int n, const double *__restrict__ partial, double *__restrict__ c);

@@ -288,6 +288,22 @@ cudaError_t launch_step(const soptx_mesh_s &m, const double *rho, const double *
 {
     if (m.path == SOPTX_PATH_LATTICE && m.d.sectors && m.h.nc > 0)
         return launch_lattice_step(m, rho, u, vals, dc, c, st, gscale);
+    if (m.d.strain && m.d.side && m.h.nc > 0 && m.h.nnz > 0 && m.d.contract && m.h.dim == 2) {
+        // the 2D pair contraction fills every SM with a persistent grid that takes
+        // its work from a counter: the sensitivities go first, on the mesh's second
+        // stream (highest priority) with one block per SM, and the contraction's
+        // CTAs take the rest of the GPU and, as those blocks finish, their slots
+        int dev = 0, sms = 0;
+        cudaError_t err = cudaGetDevice(&dev);
+        if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (err == cudaSuccess) err = cudaEventRecord(m.d.ev[0], st);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(m.d.side, m.d.ev[0], 0);
+        if (err == cudaSuccess) err = launch_strain_sensitivity(m, rho, u, dc, c, gscale, m.d.side, sms);
+        if (err == cudaSuccess) err = cudaEventRecord(m.d.ev[1], m.d.side);
+        if (err == cudaSuccess) err = launch_assemble(m, rho, vals, st);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(st, m.d.ev[1], 0);
+        return err;
+    }
     if (m.d.strain && m.d.side && m.h.nc > 0 && m.h.nnz > 0) {
         // affine cells: the sensitivities need rho and u but not K.  The assembly
         // runs on the mesh's second stream, created at the highest priority and
