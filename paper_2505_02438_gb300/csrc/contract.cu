@@ -638,20 +638,22 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) k_contract_pairs(const Pa
             fetch(e0, c0);
             float2 v[D][D];
             bool bad = false;
-            for (int k = 0; k < ct; k++) {
-                Cell c1;
-                fetch(e1, c1);
+            // cell k in cur, cell k + 1 loaded into nxt meanwhile (the two swap roles,
+            // so the loop copies no cell)
+            Cell c1;
+            auto step = [&](const Cell &cur, Cell &nxt, int k) {
+                fetch(e1, nxt);
                 if (k < cnt) {
-                    bad |= isnan(c0.E.y);
+                    bad |= isnan(cur.E.y);
                     float G[D * D], det;
                     if (D == 3) {
-                        G[0] = c0.g[0].x; G[1] = c0.g[0].y; G[2] = c0.g[0].z; G[3] = c0.g[0].w;
-                        G[4] = c0.g[1].x; G[5] = c0.g[1].y; G[6] = c0.g[1].z; G[7] = c0.g[1].w;
-                        G[8] = c0.g[2].x;
-                        det = c0.g[2].y;
+                        G[0] = cur.g[0].x; G[1] = cur.g[0].y; G[2] = cur.g[0].z; G[3] = cur.g[0].w;
+                        G[4] = cur.g[1].x; G[5] = cur.g[1].y; G[6] = cur.g[1].z; G[7] = cur.g[1].w;
+                        G[8] = cur.g[2].x;
+                        det = cur.g[2].y;
                     } else {
-                        G[0] = c0.g[0].x; G[1] = c0.g[0].y; G[2] = c0.g[0].z; G[3] = c0.g[0].w;
-                        det = c0.g[1].x;
+                        G[0] = cur.g[0].x; G[1] = cur.g[0].y; G[2] = cur.g[0].z; G[3] = cur.g[0].w;
+                        det = cur.g[1].x;
                     }
                     float M[D * D], K[D][D];
                     load_mpair<D>(Ms, m0, M);
@@ -662,8 +664,8 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) k_contract_pairs(const Pa
                         for (int j = 0; j < D; j++) {
                             // E K as a pair: TwoProd of the head, the tail's product
                             const float kk = K[i][j];
-                            const float ph = __fmul_rn(c0.E.x, kk);
-                            const float pl = __fmaf_rn(c0.E.y, kk, __fmaf_rn(c0.E.x, kk, -ph));
+                            const float ph = __fmul_rn(cur.E.x, kk);
+                            const float pl = __fmaf_rn(cur.E.y, kk, __fmaf_rn(cur.E.x, kk, -ph));
                             if (k == 0) {
                                 v[i][j] = make_float2(ph, pl);
                             } else {
@@ -671,9 +673,12 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) k_contract_pairs(const Pa
                             }
                         }
                 }
-                c0 = c1;
                 m0 = m1;
                 rec(k + 2, e1, m1);
+            };
+            for (int k = 0; k < ct; k += 2) {
+                step(c0, c1, k);
+                if (k + 1 < ct) step(c1, c0, k + 1);
             }
             // a lane whose pair met an out-of-range modulus redoes it in FP64
             if (__any_sync(kFull, bad) && bad) {

@@ -293,12 +293,15 @@ cudaError_t launch_step(const soptx_mesh_s &m, const double *rho, const double *
         // its work from a counter: the sensitivities go first, on the mesh's second
         // stream (highest priority) with one block per SM, and the contraction's
         // CTAs take the rest of the GPU and, as those blocks finish, their slots
+        // (in 3D, with one block of 64 threads per SM beside the node-owner
+        // contraction, the sensitivities outlasted it: P2 tets 304.5 -> 345.8 us)
         int dev = 0, sms = 0;
         cudaError_t err = cudaGetDevice(&dev);
         if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (err == cudaSuccess) err = cudaEventRecord(m.d.ev[0], st);
         if (err == cudaSuccess) err = cudaStreamWaitEvent(m.d.side, m.d.ev[0], 0);
-        if (err == cudaSuccess) err = launch_strain_sensitivity(m, rho, u, dc, c, gscale, m.d.side, sms);
+        if (err == cudaSuccess)
+            err = launch_strain_sensitivity(m, rho, u, dc, c, gscale, m.d.side, sms);
         if (err == cudaSuccess) err = cudaEventRecord(m.d.ev[1], m.d.side);
         if (err == cudaSuccess) err = launch_assemble(m, rho, vals, st);
         if (err == cudaSuccess) err = cudaStreamWaitEvent(st, m.d.ev[1], 0);
