@@ -590,6 +590,8 @@ def assembly_kernel(mesh, wl, prec):
         return ("k_lattice_assemble3" if wl.dim == 3 else "k_lattice_assemble2"), "lattice.cu"
     if mesh.routes["assembly"] == "contract":
         return ("k_contract_rows" if wl.dim == 3 else "k_contract_pairs"), "contract.cu"
+    if mesh.routes["assembly"] == "pairs":
+        return "k_contract_pairs", "contract.cu"
     if (wl.dim, mesh.nb) in ((3, 10), (3, 8), (2, 10), (2, 4)):
         return "k_gather_rows", "gather.cu"
     return "k_gather_nodes", "gather.cu"

@@ -144,7 +144,10 @@ soptx_status soptx_mesh_path(soptx_mesh mesh, soptx_path *path);
  *   *assembly    : 0 box lattice (k_lattice_assemble2/3), 1 row gather of
  *                  element matrices (cached, or one shared matrix), 2
  *                  per-call contraction of the reference integrals in FP32
- *                  (k_contract_rows: FP32 element matrices of affine cells)
+ *                  (FP32 element matrices of affine cells: k_contract_pairs
+ *                  in 2D, k_contract_rows in 3D), 3 node pairs over the
+ *                  cached FP64 element matrices (2D affine cells:
+ *                  k_contract_pairs reading each pair's blocks once)
  *   *sensitivity : 0 box lattice (Walsh sectors), 1 fused into the row
  *                  gather, 2 strain energy at quadrature points
  *                  (k_strain_energy: affine cells)
@@ -181,12 +184,17 @@ soptx_status soptx_sensitivity(soptx_mesh mesh, const double *d_rho, const doubl
                                double *d_dc, double *d_c, void *stream);
 
 /* One pass that produces both K(rho) and the sensitivities (the per-iteration
- * step); same arguments and results as the two calls above.  On a 2D box
- * lattice the sensitivities run on a second, mesh-owned stream beside the
- * assembly; on other meshes of affine cells the assembly runs on that stream
- * (created at the highest stream priority) beside the sensitivities on
- * `stream` (the stream and two events are made by the first such call);
- * everything is ordered on `stream` when the call returns. */
+ * step); same arguments and results as the two calls above: K and dc bitwise,
+ * c the same fixed-order sum of block partials (on 2D meshes of affine cells
+ * other than box lattices over one block per SM, so its last bits may differ
+ * from the separate call's when the mesh has more cells than the SMs' blocks
+ * hold).  On a 2D box lattice the sensitivities run on a second, mesh-owned
+ * stream beside the assembly; on other 2D meshes of affine cells they run
+ * first on that stream (created at the highest stream priority), one block per
+ * SM, beside the assembly on `stream`; on 3D meshes of affine cells the
+ * assembly runs on that stream beside the sensitivities on `stream` (the
+ * stream and two events are made by the first such call); everything is
+ * ordered on `stream` when the call returns. */
 soptx_status soptx_assemble_and_sensitivity(soptx_mesh mesh, const double *d_rho,
                                             const double *d_u, double *d_vals,
                                             double *d_dc, double *d_c, void *stream);

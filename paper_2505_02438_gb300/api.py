@@ -73,7 +73,7 @@ class Mesh:
         ra, rs = ctypes.c_int32(), ctypes.c_int32()
         N.check(L.soptx_mesh_routes(h, ctypes.byref(ra), ctypes.byref(rs)))
         # the kernels serving the per-call work (soptx_mesh_routes)
-        self.routes = {"assembly": ("lattice", "gather", "contract")[ra.value],
+        self.routes = {"assembly": ("lattice", "gather", "contract", "pairs")[ra.value],
                        "sensitivity": ("lattice", "gather", "strain")[rs.value]}
 
     @classmethod

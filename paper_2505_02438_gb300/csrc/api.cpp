@@ -36,7 +36,7 @@ static void free_device(DeviceMesh &d)
     void *ptrs[] = {d.indptr, d.indices, d.cell_node, d.node_off, d.inc_ptr, d.inc,
                     d.pos, d.geo, d.M, d.K, d.scratch, d.Edf, d.kappa, d.K0, d.sectors, d.udf, d.part,
                     d.inc_e, d.inc_a, d.counter, d.xcell, d.qw, d.qdphi, d.qdgeo, d.cg, d.lat_bad, d.stage,
-                    d.kvals, d.sgeo, d.sq, d.cgeo, d.Mf, d.ptoff, d.pia, d.pib, d.pmeta, d.pre, d.prm,
+                    d.kvals, d.sgeo, d.sq, d.cgeo, d.Mf, d.ptoff, d.pia, d.pib, d.pmeta, d.pre, d.prm, d.pblk,
                     d.cnrec, d.cinc_e, d.cinc_a, d.crec, d.cticket};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -143,7 +143,7 @@ static soptx_status setup_strain(soptx_mesh_s &m, const RefElement &ref, cudaStr
 // cells each; a window's last tile is padded with empty pairs (no cells).
 static constexpr size_t kPairWindow = 4096;
 
-static soptx_status setup_contract_pairs(soptx_mesh_s &m, const RefElement &ref, cudaStream_t st)
+static soptx_status setup_contract_pairs(soptx_mesh_s &m, const RefElement &ref, cudaStream_t st, bool cached)
 {
     const HostMesh &h = m.h;
     const int d = h.dim, nb = h.nb, ng = d * d + 1, n4 = d == 3 ? 3 : 2, mp = d == 3 ? 12 : 4;
@@ -246,7 +246,7 @@ static soptx_status setup_contract_pairs(soptx_mesh_s &m, const RefElement &ref,
                 if (cn[j] == a || rank[(size_t)cn[j]] > i) {
                     const int32_t f = sfill[h.pos[(size_t)q * nb + j]]++;
                     te[(size_t)f] = e;
-                    tm[(size_t)f] = (uint16_t)(al * nb + j);
+                    tm[(size_t)f] = (uint16_t)(cached ? al << 8 | j : al * nb + j);
                 }
         }
         for (int p = 0; p < deg; p++) {
@@ -255,7 +255,8 @@ static soptx_status setup_contract_pairs(soptx_mesh_s &m, const RefElement &ref,
             const int32_t b = h.nbr[(size_t)(off + p)];
             // the block of a in b's rows, from the pair's first cell
             const int32_t e = te[(size_t)sstart[(size_t)p]];
-            const int al = tm[(size_t)sstart[(size_t)p]] / nb, bl = tm[(size_t)sstart[(size_t)p]] % nb;
+            const int t0 = tm[(size_t)sstart[(size_t)p]];
+            const int al = cached ? t0 >> 8 : t0 / nb, bl = cached ? t0 & 255 : t0 % nb;
             const int pba = h.pos[(size_t)cinc[(size_t)e * nb + bl] * nb + al];
             const int64_t offb = h.node_off[(size_t)b];
             const int degb = (int)(h.node_off[(size_t)b + 1] - offb);
@@ -274,8 +275,9 @@ static soptx_status setup_contract_pairs(soptx_mesh_s &m, const RefElement &ref,
     ia.resize((size_t)(nchunks * 8 * 32), 0u);
     ib.resize((size_t)(nchunks * 8 * 32), 0u);
     meta.resize((size_t)(nchunks * 8 * 32), 0u);
-    soptx_status s = upload(&m.d.cgeo, cg, st, m.device_bytes, "cell geometry");
-    if (s == SOPTX_OK) s = upload(&m.d.Mf, mf, st, m.device_bytes, "reference integrals (FP32)");
+    soptx_status s = SOPTX_OK;
+    if (!cached) s = upload(&m.d.cgeo, cg, st, m.device_bytes, "cell geometry");
+    if (s == SOPTX_OK && !cached) s = upload(&m.d.Mf, mf, st, m.device_bytes, "reference integrals (FP32)");
     if (s == SOPTX_OK) s = upload(&m.d.ptoff, toff, st, m.device_bytes, "pair tiles");
     if (s == SOPTX_OK) s = upload(&m.d.pia, ia, st, m.device_bytes, "pair blocks");
     if (s == SOPTX_OK) s = upload(&m.d.pib, ib, st, m.device_bytes, "pair transposed blocks");
@@ -283,9 +285,22 @@ static soptx_status setup_contract_pairs(soptx_mesh_s &m, const RefElement &ref,
     if (s == SOPTX_OK) s = upload(&m.d.pre, re, st, m.device_bytes, "pair cells");
     if (s == SOPTX_OK) s = upload(&m.d.prm, rm, st, m.device_bytes, "pair reference integrals");
     if (s == SOPTX_OK) s = upload(&m.d.cticket, std::vector<unsigned>(2, 0u), st, m.device_bytes, "chunk counter");
+    if (s == SOPTX_OK && cached) {
+        // each record's block of the cache, gathered once here so the kernel reads
+        // them in record order
+        const int64_t nrec = (int64_t)re.size();
+        cudaError_t e = dev_alloc((void **)&m.d.pblk, (size_t)std::max<int64_t>(nrec, 1) * 2 * sizeof(float4));
+        if (e == cudaSuccess) e = launch_pair_blocks(m, nrec, st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            s = cuda_status(e, "pair blocks");
+        } else {
+            m.device_bytes += std::max<int64_t>(nrec, 1) * 2 * (int64_t)sizeof(float4);
+        }
+    }
     if (s == SOPTX_OK) {
         m.d.ptiles = ntiles;
-        m.d.contract = true;
+        (cached ? m.d.pcached : m.d.contract) = true;
     }
     return s;
 }
@@ -423,7 +438,7 @@ static soptx_status setup_contract_rows(soptx_mesh_s &m, const RefElement &ref, 
 // FP32 element matrices of affine cells: the tables of the per-call contraction.
 static soptx_status setup_contract(soptx_mesh_s &m, const RefElement &ref, cudaStream_t st)
 {
-    return m.h.dim == 2 ? setup_contract_pairs(m, ref, st) : setup_contract_rows(m, ref, st);
+    return m.h.dim == 2 ? setup_contract_pairs(m, ref, st, false) : setup_contract_rows(m, ref, st);
 }
 
 static bool material_ok(const soptx_material *m, int dim, Material &out, std::string &err)
@@ -621,6 +636,11 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
         if (s == SOPTX_OK && prec == SOPTX_ELEM_FP32 && m->path == SOPTX_PATH_CACHED &&
             contract_fits(h.dim, h.nb, h.max_deg))
             s = setup_contract(*m, ref, st);
+        // FP64 element matrices of 2D cells: the pair kernel reads each node pair's
+        // blocks of the cache once for both row blocks
+        if (s == SOPTX_OK && prec == SOPTX_ELEM_FP64 && m->path == SOPTX_PATH_CACHED && h.dim == 2 &&
+            contract_fits(h.dim, h.nb, h.max_deg))
+            s = setup_contract_pairs(*m, ref, st, true);
     }
     if (s == SOPTX_OK && (m->path != SOPTX_PATH_LATTICE || !d.sectors)) {
         // per-call float-pair moduli and displacements, per-(cell, node) partials
@@ -751,7 +771,7 @@ soptx_status soptx_mesh_path(soptx_mesh m, soptx_path *path)
 soptx_status soptx_mesh_routes(soptx_mesh m, int32_t *assembly, int32_t *sensitivity)
 {
     if (!m) SOPTX_FAIL(SOPTX_EINVAL, "mesh is NULL");
-    if (assembly) *assembly = m->path == SOPTX_PATH_LATTICE ? 0 : (m->d.contract ? 2 : 1);
+    if (assembly) *assembly = m->path == SOPTX_PATH_LATTICE ? 0 : m->d.contract ? 2 : m->d.pcached ? 3 : 1;
     if (sensitivity) *sensitivity = (m->path == SOPTX_PATH_LATTICE && m->d.sectors) ? 0 : (m->d.strain ? 2 : 1);
     return SOPTX_OK;
 }

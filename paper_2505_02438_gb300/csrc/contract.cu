@@ -75,10 +75,13 @@ struct PairArgs {
     const uint32_t *__restrict__ ib;     // value index of block (b, a) / d (equal to ia when b = a)
     const uint32_t *__restrict__ meta;   // cells (bits 0-9), row length of a's rows (10-20), of b's (21-31)
     const int32_t *__restrict__ re;      // per record: the cell
-    const uint16_t *__restrict__ rm;     // per record: reference-integral pair a_loc nb + b_loc
+    const uint16_t *__restrict__ rm;     // per record: a_loc nb + b_loc (contraction), a_loc << 8 | b_loc (cached)
     const float4 *__restrict__ cgeo;
     const float *__restrict__ Mf;
     int nmf;                             // floats in Mf
+    const float2 *__restrict__ Kc;       // cached FP64 element matrices as float pairs [nc][ldof][ldof]
+    int ldof;
+    const float4 *__restrict__ blk;      // per record: its 2 x 2 block of Kc, two rows of two float pairs
     const float2 *__restrict__ Edf;
     const double *__restrict__ rho;
     SimpParams sp;
@@ -505,6 +508,29 @@ __device__ __noinline__ void pair_fp64(const PairArgs &A, const float *Ms, int64
                    (int)(meta >> 21), pa != pb, al16, acc);
 }
 
+// The same redo over cached FP64 element matrices (float pairs, 2D).
+__device__ __noinline__ void pair_fp64_cached(const PairArgs &A, int64_t rb, int cnt, uint32_t pa, uint32_t pb,
+                                              uint32_t meta, bool al16)
+{
+    double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    for (int k = 0; k < cnt; k++) {
+        const int64_t r = rb + (int64_t)k * 32;
+        const int32_t e = A.re[r];
+        const int m = A.rm[r];
+        const double E = simp_E(A.sp, A.rho[e]);
+        const float2 *kb = A.Kc + (int64_t)e * A.ldof * A.ldof + (int64_t)(2 * (m >> 8)) * A.ldof + 2 * (m & 255);
+#pragma unroll
+        for (int i = 0; i < 2; i++)
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+                const float2 kk = kb[i * A.ldof + j];
+                acc[i][j] += E * ((double)kk.x + (double)kk.y);
+            }
+    }
+    store_block<2>(A.vals + (int64_t)2 * pa, (int)((meta >> 10) & 2047u), A.vals + (int64_t)2 * pb,
+                   (int)(meta >> 21), pa != pb, al16, acc);
+}
+
 // Asynchronous 16-byte copies global -> shared (cp.async); the waits are the
 // hardware's (cp.async.wait_group), no polling.
 __device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc)
@@ -534,9 +560,10 @@ struct ChunkBuf {
 // chunk's tables are copied into the other buffer while this one is worked;
 // within a tile the cell one position ahead is loaded while the current one is
 // contracted.
-template <int D>
+template <int D, bool CACHED>
 __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) k_contract_pairs(const PairArgs A)
 {
+    static_assert(D == 2 || !CACHED, "cached blocks are read as whole float4s in 2D only");
     constexpr int G4 = CGeo<D>::n4;
     extern __shared__ float4 csm4[];
     ChunkBuf *bufs = reinterpret_cast<ChunkBuf *>(csm4);
@@ -575,14 +602,22 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) k_contract_pairs(const Pa
             }
         }
     };
+    // a record's cell: its geometry (contraction) or its cached block
+    // K_e^0[(a,.),(b,.)] (two rows of two float pairs), and its modulus
     struct Cell {
         float4 g[G4];
         float2 E;
     };
-    auto fetch = [&](int32_t e, Cell &c) {
+    auto fetch_geo = [&](int32_t e, Cell &c) {
         const float4 *gp = A.cgeo + (int64_t)G4 * e;
 #pragma unroll
         for (int w = 0; w < G4; w++) c.g[w] = __ldg(gp + w);
+        c.E = __ldg(A.Edf + e);
+    };
+    // the cached block of record r (the lanes of a warp read consecutive records)
+    auto fetch_blk = [&](int64_t r, int32_t e, Cell &c) {
+        c.g[0] = __ldcs(A.blk + 2 * r);
+        c.g[1] = __ldcs(A.blk + 2 * r + 1);
         c.E = __ldg(A.Edf + e);
     };
     // chunks are taken from a counter, so a CTA that starts late beside another
@@ -635,15 +670,38 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) k_contract_pairs(const Pa
             rec(0, e0, m0);
             rec(1, e1, m1);
             Cell c0;
-            fetch(e0, c0);
+            const int64_t rabs = gbase + rel;   // the lane's first record
+            if constexpr (CACHED) fetch_blk(rabs, e0, c0); else fetch_geo(e0, c0);
             float2 v[D][D];
             bool bad = false;
             // cell k in cur, cell k + 1 loaded into nxt meanwhile (the two swap roles,
             // so the loop copies no cell)
             Cell c1;
             auto step = [&](const Cell &cur, Cell &nxt, int k) {
-                fetch(e1, nxt);
-                if (k < cnt) {
+                if constexpr (CACHED)
+                    fetch_blk(rabs + (int64_t)min(k + 1, ct - 1) * 32, e1, nxt);
+                else
+                    fetch_geo(e1, nxt);
+                if constexpr (CACHED) {
+                  if (k < cnt) {
+                    bad |= isnan(cur.E.y);
+                    // E K_e^0 as an unnormalised pair product, entry by entry
+                    const df E{cur.E.x, cur.E.y};
+                    const df Kb[2][2] = {{df{cur.g[0].x, cur.g[0].y}, df{cur.g[0].z, cur.g[0].w}},
+                                         {df{cur.g[1].x, cur.g[1].y}, df{cur.g[1].z, cur.g[1].w}}};
+#pragma unroll
+                    for (int i = 0; i < D; i++)
+#pragma unroll
+                        for (int j = 0; j < D; j++) {
+                            const df x = df_mul_raw(E, Kb[i & 1][j & 1]);
+                            if (k == 0) {
+                                v[i][j] = make_float2(x.h, x.l);
+                            } else {
+                                acc_add(v[i][j].x, v[i][j].y, x);
+                            }
+                        }
+                  }
+                } else if (k < cnt) {
                     bad |= isnan(cur.E.y);
                     float G[D * D], det;
                     if (D == 3) {
@@ -682,7 +740,11 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) k_contract_pairs(const Pa
             }
             // a lane whose pair met an out-of-range modulus redoes it in FP64
             if (__any_sync(kFull, bad) && bad) {
-                pair_fp64<D>(A, Ms, gbase + rel, cnt, pa, pb, meta, al16);
+                if constexpr (CACHED) {
+                    pair_fp64_cached(A, gbase + rel, cnt, pa, pb, meta, al16);
+                } else {
+                    pair_fp64<D>(A, Ms, gbase + rel, cnt, pa, pb, meta, al16);
+                }
             } else if (cnt > 0) {
                 // the values leave as FP64: half the entries widened and added on the
                 // FP64 pipe, half with integer operations only
@@ -989,7 +1051,7 @@ __global__ void __launch_bounds__(128) k_strain_energy_warp(const StrainArgs A)
     if (A.c) grid_sum_last_block(mine, A.partial, A.counter, A.c);
 }
 
-template <int D>
+template <int D, bool CACHED>
 cudaError_t pairs_launch(const soptx_mesh_s &m, const double *rho, double *vals, cudaStream_t st)
 {
     const auto &h = m.h;
@@ -1004,7 +1066,10 @@ cudaError_t pairs_launch(const soptx_mesh_s &m, const double *rho, double *vals,
     A.rm = m.d.prm;
     A.cgeo = m.d.cgeo;
     A.Mf = m.d.Mf;
-    A.nmf = h.nb * h.nb * MPad<D>::n;
+    A.nmf = CACHED ? 0 : h.nb * h.nb * MPad<D>::n;
+    A.Kc = CACHED ? static_cast<const float2 *>(m.d.K) : nullptr;
+    A.ldof = h.ldof;
+    A.blk = CACHED ? m.d.pblk : nullptr;
     A.Edf = m.d.Edf;
     A.rho = rho;
     A.sp = simp_params(m.mat);
@@ -1012,7 +1077,7 @@ cudaError_t pairs_launch(const soptx_mesh_s &m, const double *rho, double *vals,
     A.mu = (float)m.mat.mu;
     A.vals = vals;
     const size_t smem = 2 * sizeof(ChunkBuf) + (size_t)A.nmf * sizeof(float);
-    auto kern = k_contract_pairs<D>;
+    auto kern = k_contract_pairs<D, CACHED>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     // the CTAs that fit at once, each taking chunks from the counter
@@ -1095,13 +1160,39 @@ bool contract_fits(int dim, int nb, int max_deg)
     return mbytes + per_warp <= cta_smem;
 }
 
-// Element moduli as float pairs (k_prep of the gather), then the contraction.
+// At mesh creation: each pair record's 2 x 2 block of the cached FP64 element
+// matrices, in record order.
+__global__ void k_pair_blocks(int64_t nrec, const int32_t *__restrict__ re, const uint16_t *__restrict__ rm,
+                              const float2 *__restrict__ Kc, int ldof, float4 *__restrict__ blk)
+{
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrec; r += (int64_t)gridDim.x * blockDim.x) {
+        const int m = rm[r];
+        const float2 *kb = Kc + (int64_t)re[r] * ldof * ldof + (int64_t)(2 * (m >> 8)) * ldof + 2 * (m & 255);
+        blk[2 * r] = *reinterpret_cast<const float4 *>(kb);
+        blk[2 * r + 1] = *reinterpret_cast<const float4 *>(kb + ldof);
+    }
+}
+
+cudaError_t launch_pair_blocks(const soptx_mesh_s &m, int64_t nrec, cudaStream_t st)
+{
+    if (nrec == 0) return cudaSuccess;
+    const int grid = (int)std::min<int64_t>((nrec + 255) / 256, 152 * 16);
+    k_pair_blocks<<<grid, 256, 0, st>>>(nrec, m.d.pre, m.d.prm, static_cast<const float2 *>(m.d.K), m.h.ldof,
+                                        m.d.pblk);
+    return cudaGetLastError();
+}
+
+// Element moduli as float pairs (k_prep of the gather), then the contraction (or,
+// for the cached FP64 element matrices of 2D meshes, the pair kernel reading them).
 cudaError_t launch_contract_assemble(const soptx_mesh_s &m, const double *rho, double *vals, cudaStream_t st)
 {
     const auto &h = m.h;
     cudaError_t err = launch_prep(m, rho, nullptr, st);
     if (err != cudaSuccess) return err;
-    if (h.dim == 2) return m.d.ptiles == 0 ? cudaSuccess : pairs_launch<2>(m, rho, vals, st);
+    if (h.dim == 2) {
+        if (m.d.ptiles == 0) return cudaSuccess;
+        return m.d.pcached ? pairs_launch<2, true>(m, rho, vals, st) : pairs_launch<2, false>(m, rho, vals, st);
+    }
     if (h.nn == 0 || h.nnz == 0) return cudaSuccess;
 #define SOPTX_CT(NBB, MINB)                                     \
     if (h.nb == NBB) return rows_launch<3, NBB, MINB>(m, rho, vals, st);

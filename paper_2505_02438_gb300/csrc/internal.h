@@ -127,14 +127,17 @@ struct DeviceMesh {
     bool contract = false;         // the assembly takes k_contract_pairs (2D) or k_contract_rows (3D)
     float4 *cgeo = nullptr;        //   [nc][2 or 3] G and |det J| in FP32
     float *Mf = nullptr;           //   [nb][nb][4 or 12] reference integrals in FP32
-    // 2D: node pairs {a, b} (b = a, or b after a), in tiles of 32
+    // 2D: node pairs {a, b} (b = a, or b after a), in tiles of 32; also for the cached
+    // FP64 element matrices of 2D affine meshes (pcached: the pair kernel reads them)
+    bool pcached = false;
     int64_t ptiles = 0;            //   tiles
     uint32_t *ptoff = nullptr;     //   [8 chunks + 16] first record of each tile / 32
     uint32_t *pia = nullptr;       //   [256 chunks] value index of block (a, b) / 2
     uint32_t *pib = nullptr;       //   [256 chunks] value index of block (b, a) / 2
     uint32_t *pmeta = nullptr;     //   [256 chunks] cells | a's row length << 10 | b's << 21
     int32_t *pre = nullptr;        //   per record: the cell (ascending per pair)
-    uint16_t *prm = nullptr;       //   per record: a_loc nb + b_loc
+    uint16_t *prm = nullptr;       //   per record: a_loc nb + b_loc (pcached: a_loc << 8 | b_loc)
+    float4 *pblk = nullptr;        //   pcached: per record its 2 x 2 block of K_e^0 (2 float4s)
     // 3D: each node's cells as a chain, walked by the node's group of lanes
     int4 *cnrec = nullptr;         //   [nn] nodes by incident-cell count, largest first: row block
                                    //   offset (2 ints), first incidence, cells << 16 | degree
@@ -207,6 +210,7 @@ cudaError_t launch_prep(const soptx_mesh_s &m, const double *rho, const double *
 // contract.cu
 bool contract_fits(int dim, int nb, int max_deg);
 cudaError_t launch_contract_assemble(const soptx_mesh_s &m, const double *rho, double *vals, cudaStream_t st);
+cudaError_t launch_pair_blocks(const soptx_mesh_s &m, int64_t nrec, cudaStream_t st);
 // max_grid > 0 caps the blocks (the kernel loops over the cells): beside a
 // persistent assembly, a block per SM leaves it the rest of the GPU
 cudaError_t launch_strain_sensitivity(const soptx_mesh_s &m, const double *rho, const double *u, double *out,
