@@ -143,10 +143,15 @@ static soptx_status setup_strain(soptx_mesh_s &m, const RefElement &ref, cudaStr
 // cells each; a window's last tile is padded with empty pairs (no cells).
 static constexpr size_t kPairWindow = 4096;
 
-static soptx_status setup_contract_pairs(soptx_mesh_s &m, const RefElement &ref, cudaStream_t st, bool cached)
+static soptx_status setup_contract_pairs(soptx_mesh_s &m, const RefElement &ref, cudaStream_t st, bool cached,
+                                        bool unif = false)
 {
     const HostMesh &h = m.h;
     const int d = h.dim, nb = h.nb, ng = d * d + 1, n4 = d == 3 ? 3 : 2, mp = d == 3 ? 12 : 4;
+    // 3D: every node assembles all of its own row blocks (the symmetric layout's
+    // transposed 24-byte pieces leave L2 sectors partly filled)
+    const bool sym = d == 2;
+    const bool bytes = cached || unif;   // local pair as a_loc << 8 | b_loc
     // a pair's cell count has 10 bits in the tables, a value index / d has 32:
     // larger fans or matrices keep the cached gather
     for (int64_t n = 0; n < h.nn; n++)
@@ -231,7 +236,7 @@ static soptx_status setup_contract_pairs(soptx_mesh_s &m, const RefElement &ref,
         for (int32_t q = q0; q < q1; q++) {
             const int32_t *cn = &h.cell_node[(size_t)h.inc_e[(size_t)q] * nb];
             for (int j = 0; j < nb; j++)
-                if (cn[j] == a || rank[(size_t)cn[j]] > i) scnt[h.pos[(size_t)q * nb + j]]++;
+                if (!sym || cn[j] == a || rank[(size_t)cn[j]] > i) scnt[h.pos[(size_t)q * nb + j]]++;
         }
         sstart.assign((size_t)deg + 1, 0);
         for (int p = 0; p < deg; p++) sstart[(size_t)p + 1] = sstart[(size_t)p] + scnt[(size_t)p];
@@ -243,10 +248,10 @@ static soptx_status setup_contract_pairs(soptx_mesh_s &m, const RefElement &ref,
             const int32_t *cn = &h.cell_node[(size_t)e * nb];
             const int al = h.inc_a[(size_t)q];
             for (int j = 0; j < nb; j++)
-                if (cn[j] == a || rank[(size_t)cn[j]] > i) {
+                if (!sym || cn[j] == a || rank[(size_t)cn[j]] > i) {
                     const int32_t f = sfill[h.pos[(size_t)q * nb + j]]++;
                     te[(size_t)f] = e;
-                    tm[(size_t)f] = (uint16_t)(cached ? al << 8 | j : al * nb + j);
+                    tm[(size_t)f] = (uint16_t)(bytes ? al << 8 | j : al * nb + j);
                 }
         }
         for (int p = 0; p < deg; p++) {
@@ -256,12 +261,13 @@ static soptx_status setup_contract_pairs(soptx_mesh_s &m, const RefElement &ref,
             // the block of a in b's rows, from the pair's first cell
             const int32_t e = te[(size_t)sstart[(size_t)p]];
             const int t0 = tm[(size_t)sstart[(size_t)p]];
-            const int al = cached ? t0 >> 8 : t0 / nb, bl = cached ? t0 & 255 : t0 % nb;
+            const int al = bytes ? t0 >> 8 : t0 / nb, bl = bytes ? t0 & 255 : t0 % nb;
             const int pba = h.pos[(size_t)cinc[(size_t)e * nb + bl] * nb + al];
             const int64_t offb = h.node_off[(size_t)b];
             const int degb = (int)(h.node_off[(size_t)b + 1] - offb);
-            win.push_back(WPair{(uint32_t)(d * off + p), (uint32_t)(d * offb + pba),
-                                (uint32_t)c | ((uint32_t)(d * deg) << 10) | ((uint32_t)(d * degb) << 21), wre.size()});
+            const uint32_t pa = (uint32_t)(d * off + p), pb = sym ? (uint32_t)(d * offb + pba) : pa;
+            win.push_back(WPair{pa, pb, (uint32_t)c | ((uint32_t)(d * deg) << 10) | ((uint32_t)(d * (sym ? degb : deg)) << 21),
+                                wre.size()});
             wre.insert(wre.end(), te.begin() + sstart[(size_t)p], te.begin() + sstart[(size_t)p + 1]);
             wrm.insert(wrm.end(), tm.begin() + sstart[(size_t)p], tm.begin() + sstart[(size_t)p + 1]);
         }
@@ -276,8 +282,8 @@ static soptx_status setup_contract_pairs(soptx_mesh_s &m, const RefElement &ref,
     ib.resize((size_t)(nchunks * 8 * 32), 0u);
     meta.resize((size_t)(nchunks * 8 * 32), 0u);
     soptx_status s = SOPTX_OK;
-    if (!cached) s = upload(&m.d.cgeo, cg, st, m.device_bytes, "cell geometry");
-    if (s == SOPTX_OK && !cached) s = upload(&m.d.Mf, mf, st, m.device_bytes, "reference integrals (FP32)");
+    if (!bytes) s = upload(&m.d.cgeo, cg, st, m.device_bytes, "cell geometry");
+    if (s == SOPTX_OK && !bytes) s = upload(&m.d.Mf, mf, st, m.device_bytes, "reference integrals (FP32)");
     if (s == SOPTX_OK) s = upload(&m.d.ptoff, toff, st, m.device_bytes, "pair tiles");
     if (s == SOPTX_OK) s = upload(&m.d.pia, ia, st, m.device_bytes, "pair blocks");
     if (s == SOPTX_OK) s = upload(&m.d.pib, ib, st, m.device_bytes, "pair transposed blocks");
@@ -300,7 +306,7 @@ static soptx_status setup_contract_pairs(soptx_mesh_s &m, const RefElement &ref,
     }
     if (s == SOPTX_OK) {
         m.d.ptiles = ntiles;
-        (cached ? m.d.pcached : m.d.contract) = true;
+        (unif ? m.d.puniform : cached ? m.d.pcached : m.d.contract) = true;
     }
     return s;
 }
@@ -641,6 +647,11 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
         if (s == SOPTX_OK && prec == SOPTX_ELEM_FP64 && m->path == SOPTX_PATH_CACHED && h.dim == 2 &&
             contract_fits(h.dim, h.nb, h.max_deg))
             s = setup_contract_pairs(*m, ref, st, true);
+        // FP64 element matrix of a uniform mesh (boxes of order 2 and 3): the pair
+        // kernel reads its blocks through L1
+        if (s == SOPTX_OK && prec == SOPTX_ELEM_FP64 && m->path == SOPTX_PATH_UNIFORM &&
+            pairs_fit(h.dim, h.nb, h.max_deg))
+            s = setup_contract_pairs(*m, ref, st, false, true);
     }
     if (s == SOPTX_OK && (m->path != SOPTX_PATH_LATTICE || !d.sectors)) {
         // per-call float-pair moduli and displacements, per-(cell, node) partials
@@ -771,7 +782,8 @@ soptx_status soptx_mesh_path(soptx_mesh m, soptx_path *path)
 soptx_status soptx_mesh_routes(soptx_mesh m, int32_t *assembly, int32_t *sensitivity)
 {
     if (!m) SOPTX_FAIL(SOPTX_EINVAL, "mesh is NULL");
-    if (assembly) *assembly = m->path == SOPTX_PATH_LATTICE ? 0 : m->d.contract ? 2 : m->d.pcached ? 3 : 1;
+    if (assembly)
+        *assembly = m->path == SOPTX_PATH_LATTICE ? 0 : m->d.contract ? 2 : (m->d.pcached || m->d.puniform) ? 3 : 1;
     if (sensitivity) *sensitivity = (m->path == SOPTX_PATH_LATTICE && m->d.sectors) ? 0 : (m->d.strain ? 2 : 1);
     return SOPTX_OK;
 }

@@ -531,6 +531,34 @@ __device__ __noinline__ void pair_fp64_cached(const PairArgs &A, int64_t rb, int
                    (int)(meta >> 21), pa != pb, al16, acc);
 }
 
+// The same redo over the one element matrix of a uniform mesh (float pairs).
+template <int D>
+__device__ __noinline__ void pair_fp64_unif(const PairArgs &A, int64_t rb, int cnt, uint32_t pa, uint32_t pb,
+                                            uint32_t meta, bool al16)
+{
+    double acc[D][D];
+#pragma unroll
+    for (int i = 0; i < D; i++)
+#pragma unroll
+        for (int j = 0; j < D; j++) acc[i][j] = 0.0;
+    for (int k = 0; k < cnt; k++) {
+        const int64_t r = rb + (int64_t)k * 32;
+        const int32_t e = A.re[r];
+        const int m = A.rm[r];
+        const double E = simp_E(A.sp, A.rho[e]);
+        const float2 *kb = A.Kc + (int64_t)(D * (m >> 8)) * A.ldof + D * (m & 255);
+#pragma unroll
+        for (int i = 0; i < D; i++)
+#pragma unroll
+            for (int j = 0; j < D; j++) {
+                const float2 kk = kb[i * A.ldof + j];
+                acc[i][j] += E * ((double)kk.x + (double)kk.y);
+            }
+    }
+    store_block<D>(A.vals + (int64_t)D * pa, (int)((meta >> 10) & 2047u), A.vals + (int64_t)D * pb,
+                   (int)(meta >> 21), pa != pb, al16, acc);
+}
+
 // Asynchronous 16-byte copies global -> shared (cp.async); the waits are the
 // hardware's (cp.async.wait_group), no polling.
 __device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc)
@@ -560,10 +588,11 @@ struct ChunkBuf {
 // chunk's tables are copied into the other buffer while this one is worked;
 // within a tile the cell one position ahead is loaded while the current one is
 // contracted.
-template <int D, bool CACHED>
+template <int D, bool CACHED, bool UNIF>
 __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) k_contract_pairs(const PairArgs A)
 {
     static_assert(D == 2 || !CACHED, "cached blocks are read as whole float4s in 2D only");
+    static_assert(!(CACHED && UNIF), "one source of element matrices");
     constexpr int G4 = CGeo<D>::n4;
     extern __shared__ float4 csm4[];
     ChunkBuf *bufs = reinterpret_cast<ChunkBuf *>(csm4);
@@ -671,7 +700,13 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) k_contract_pairs(const Pa
             rec(1, e1, m1);
             Cell c0;
             const int64_t rabs = gbase + rel;   // the lane's first record
-            if constexpr (CACHED) fetch_blk(rabs, e0, c0); else fetch_geo(e0, c0);
+            if constexpr (CACHED) {
+                fetch_blk(rabs, e0, c0);
+            } else if constexpr (UNIF) {
+                c0.E = __ldg(A.Edf + e0);
+            } else {
+                fetch_geo(e0, c0);
+            }
             float2 v[D][D];
             bool bad = false;
             // cell k in cur, cell k + 1 loaded into nxt meanwhile (the two swap roles,
@@ -680,9 +715,31 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) k_contract_pairs(const Pa
             auto step = [&](const Cell &cur, Cell &nxt, int k) {
                 if constexpr (CACHED)
                     fetch_blk(rabs + (int64_t)min(k + 1, ct - 1) * 32, e1, nxt);
+                else if constexpr (UNIF)
+                    nxt.E = __ldg(A.Edf + e1);
                 else
                     fetch_geo(e1, nxt);
-                if constexpr (CACHED) {
+                if constexpr (UNIF) {
+                  if (k < cnt) {
+                    bad |= isnan(cur.E.y);
+                    // E K^0 (the mesh's one element matrix, read through L1) as an
+                    // unnormalised pair product, entry by entry
+                    const df E{cur.E.x, cur.E.y};
+                    const float2 *kb = A.Kc + (int64_t)(D * (m0 >> 8)) * A.ldof + D * (m0 & 255);
+#pragma unroll
+                    for (int i = 0; i < D; i++)
+#pragma unroll
+                        for (int j = 0; j < D; j++) {
+                            const float2 kk = __ldg(kb + i * A.ldof + j);
+                            const df x = df_mul_raw(E, df{kk.x, kk.y});
+                            if (k == 0) {
+                                v[i][j] = make_float2(x.h, x.l);
+                            } else {
+                                acc_add(v[i][j].x, v[i][j].y, x);
+                            }
+                        }
+                  }
+                } else if constexpr (CACHED) {
                   if (k < cnt) {
                     bad |= isnan(cur.E.y);
                     // E K_e^0 as an unnormalised pair product, entry by entry
@@ -742,6 +799,8 @@ __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) k_contract_pairs(const Pa
             if (__any_sync(kFull, bad) && bad) {
                 if constexpr (CACHED) {
                     pair_fp64_cached(A, gbase + rel, cnt, pa, pb, meta, al16);
+                } else if constexpr (UNIF) {
+                    pair_fp64_unif<D>(A, gbase + rel, cnt, pa, pb, meta, al16);
                 } else {
                     pair_fp64<D>(A, Ms, gbase + rel, cnt, pa, pb, meta, al16);
                 }
@@ -1051,7 +1110,7 @@ __global__ void __launch_bounds__(128) k_strain_energy_warp(const StrainArgs A)
     if (A.c) grid_sum_last_block(mine, A.partial, A.counter, A.c);
 }
 
-template <int D, bool CACHED>
+template <int D, bool CACHED, bool UNIF>
 cudaError_t pairs_launch(const soptx_mesh_s &m, const double *rho, double *vals, cudaStream_t st)
 {
     const auto &h = m.h;
@@ -1066,8 +1125,8 @@ cudaError_t pairs_launch(const soptx_mesh_s &m, const double *rho, double *vals,
     A.rm = m.d.prm;
     A.cgeo = m.d.cgeo;
     A.Mf = m.d.Mf;
-    A.nmf = CACHED ? 0 : h.nb * h.nb * MPad<D>::n;
-    A.Kc = CACHED ? static_cast<const float2 *>(m.d.K) : nullptr;
+    A.nmf = CACHED || UNIF ? 0 : h.nb * h.nb * MPad<D>::n;
+    A.Kc = CACHED || UNIF ? static_cast<const float2 *>(m.d.K) : nullptr;
     A.ldof = h.ldof;
     A.blk = CACHED ? m.d.pblk : nullptr;
     A.Edf = m.d.Edf;
@@ -1077,7 +1136,7 @@ cudaError_t pairs_launch(const soptx_mesh_s &m, const double *rho, double *vals,
     A.mu = (float)m.mat.mu;
     A.vals = vals;
     const size_t smem = 2 * sizeof(ChunkBuf) + (size_t)A.nmf * sizeof(float);
-    auto kern = k_contract_pairs<D, CACHED>;
+    auto kern = k_contract_pairs<D, CACHED, UNIF>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     // the CTAs that fit at once, each taking chunks from the counter
@@ -1182,6 +1241,13 @@ cudaError_t launch_pair_blocks(const soptx_mesh_s &m, int64_t nrec, cudaStream_t
     return cudaGetLastError();
 }
 
+// Whether the pair kernel can read a uniform or cached mesh's element matrices:
+// local indices in 8 bits each, a block row (d times the degree) in 11 bits.
+bool pairs_fit(int dim, int nb, int max_deg)
+{
+    return (dim == 2 || dim == 3) && nb <= 255 && (int64_t)dim * max_deg <= 2047;
+}
+
 // Element moduli as float pairs (k_prep of the gather), then the contraction (or,
 // for the cached FP64 element matrices of 2D meshes, the pair kernel reading them).
 cudaError_t launch_contract_assemble(const soptx_mesh_s &m, const double *rho, double *vals, cudaStream_t st)
@@ -1189,9 +1255,15 @@ cudaError_t launch_contract_assemble(const soptx_mesh_s &m, const double *rho, d
     const auto &h = m.h;
     cudaError_t err = launch_prep(m, rho, nullptr, st);
     if (err != cudaSuccess) return err;
+    if (m.d.puniform) {
+        if (m.d.ptiles == 0) return cudaSuccess;
+        return h.dim == 3 ? pairs_launch<3, false, true>(m, rho, vals, st)
+                          : pairs_launch<2, false, true>(m, rho, vals, st);
+    }
     if (h.dim == 2) {
         if (m.d.ptiles == 0) return cudaSuccess;
-        return m.d.pcached ? pairs_launch<2, true>(m, rho, vals, st) : pairs_launch<2, false>(m, rho, vals, st);
+        return m.d.pcached ? pairs_launch<2, true, false>(m, rho, vals, st)
+                           : pairs_launch<2, false, false>(m, rho, vals, st);
     }
     if (h.nn == 0 || h.nnz == 0) return cudaSuccess;
 #define SOPTX_CT(NBB, MINB)                                     \
@@ -1234,8 +1306,9 @@ cudaError_t launch_strain_sensitivity(const soptx_mesh_s &m, const double *rho, 
     if ((int64_t)h.nb * A.nq >= 256) {
         // a warp per cell: 4 warps per block, each staging one cell's displacements
         const size_t smem = (size_t)4 * h.nb * h.dim * vb;
-        int64_t grid = std::max<int64_t>(1, std::min<int64_t>((h.nc + 3) / 4, m.d.scratch_len));
-        if (max_grid > 0) grid = std::min<int64_t>(grid, max_grid);
+        // (the cap is not applied here: four cells per block, a block per SM would
+        // leave this kernel far behind the assembly beside it)
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((h.nc + 3) / 4, m.d.scratch_len));
         auto k = h.dim == 3 ? (f32 ? k_strain_energy_warp<3, false> : k_strain_energy_warp<3, true>)
                             : (f32 ? k_strain_energy_warp<2, false> : k_strain_energy_warp<2, true>);
         cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -130,6 +130,7 @@ struct DeviceMesh {
     // 2D: node pairs {a, b} (b = a, or b after a), in tiles of 32; also for the cached
     // FP64 element matrices of 2D affine meshes (pcached: the pair kernel reads them)
     bool pcached = false;
+    bool puniform = false;         //   the pair kernel over the one element matrix of a uniform mesh
     int64_t ptiles = 0;            //   tiles
     uint32_t *ptoff = nullptr;     //   [8 chunks + 16] first record of each tile / 32
     uint32_t *pia = nullptr;       //   [256 chunks] value index of block (a, b) / 2
@@ -209,6 +210,7 @@ int gather_finalize_grid(int64_t nc);
 cudaError_t launch_prep(const soptx_mesh_s &m, const double *rho, const double *u, cudaStream_t st);
 // contract.cu
 bool contract_fits(int dim, int nb, int max_deg);
+bool pairs_fit(int dim, int nb, int max_deg);
 cudaError_t launch_contract_assemble(const soptx_mesh_s &m, const double *rho, double *vals, cudaStream_t st);
 cudaError_t launch_pair_blocks(const soptx_mesh_s &m, int64_t nrec, cudaStream_t st);
 // max_grid > 0 caps the blocks (the kernel loops over the cells): beside a

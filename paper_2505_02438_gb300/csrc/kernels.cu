@@ -266,7 +266,7 @@ cudaError_t launch_assemble(const soptx_mesh_s &m, const double *rho, double *va
 {
     if (m.h.nn == 0 || m.h.nnz == 0) return cudaSuccess;
     if (m.path == SOPTX_PATH_LATTICE) return launch_lattice_assemble(m, rho, vals, st);
-    if (m.d.contract || m.d.pcached) return launch_contract_assemble(m, rho, vals, st);
+    if (m.d.contract || m.d.pcached || m.d.puniform) return launch_contract_assemble(m, rho, vals, st);
     return launch_gather(m, rho, nullptr, vals, nullptr, nullptr, nullptr, st);
 }
 
@@ -288,7 +288,8 @@ cudaError_t launch_step(const soptx_mesh_s &m, const double *rho, const double *
 {
     if (m.path == SOPTX_PATH_LATTICE && m.d.sectors && m.h.nc > 0)
         return launch_lattice_step(m, rho, u, vals, dc, c, st, gscale);
-    if (m.d.strain && m.d.side && m.h.nc > 0 && m.h.nnz > 0 && (m.d.contract || m.d.pcached) && m.h.dim == 2) {
+    if (m.d.strain && m.d.side && m.h.nc > 0 && m.h.nnz > 0 &&
+        (((m.d.contract || m.d.pcached) && m.h.dim == 2) || m.d.puniform)) {
         // the 2D pair kernel fills every SM with a persistent grid that takes
         // its work from a counter: the sensitivities go first, on the mesh's second
         // stream (highest priority) with one block per SM, and the contraction's
