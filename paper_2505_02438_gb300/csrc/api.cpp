@@ -141,6 +141,12 @@ static soptx_status setup_strain(soptx_mesh_s &m, const RefElement &ref, cudaStr
 // consecutive owners (about kPairWindow pairs) are sorted by cell count, most
 // first, and cut into tiles of 32, so the lanes of a warp walk about as many
 // cells each; a window's last tile is padded with empty pairs (no cells).
+// The same tables serve the cached FP64 element matrices of 2D cells (cached:
+// each record's 2 x 2 block is also gathered into record order) and the one
+// FP64 matrix of a uniform mesh (unif); for those the local pair is stored as
+// a_loc << 8 | b_loc.  In 3D (uniform meshes) every node takes all of its own
+// column blocks instead of the pairs after it, so no block is written
+// transposed.
 static constexpr size_t kPairWindow = 4096;
 
 static soptx_status setup_contract_pairs(soptx_mesh_s &m, const RefElement &ref, cudaStream_t st, bool cached,

@@ -19,6 +19,12 @@
 //                    cells and both destinations come from tables made at
 //                    mesh creation; a warp's 32 pairs have about as many
 //                    cells each.
+//                    The same kernel reads the blocks instead for the cached
+//                    FP64 element matrices of 2D affine cells (each record's
+//                    block gathered into record order at mesh creation) and
+//                    for the one FP64 matrix of a uniform mesh (boxes of order
+//                    2 and 3; in 3D each node then assembles all of its own
+//                    rows, no transposed writes).
 //  k_contract_rows : the same blocks for 3D cells, with the rows of one node
 //                    owned by a group of nb lanes (nb = basis functions per
 //                    cell) that walks the node's incident cells as a chain
@@ -75,11 +81,12 @@ struct PairArgs {
     const uint32_t *__restrict__ ib;     // value index of block (b, a) / d (equal to ia when b = a)
     const uint32_t *__restrict__ meta;   // cells (bits 0-9), row length of a's rows (10-20), of b's (21-31)
     const int32_t *__restrict__ re;      // per record: the cell
-    const uint16_t *__restrict__ rm;     // per record: a_loc nb + b_loc (contraction), a_loc << 8 | b_loc (cached)
+    const uint16_t *__restrict__ rm;     // per record: a_loc nb + b_loc (contraction), a_loc << 8 | b_loc (the others)
     const float4 *__restrict__ cgeo;
     const float *__restrict__ Mf;
     int nmf;                             // floats in Mf
-    const float2 *__restrict__ Kc;       // cached FP64 element matrices as float pairs [nc][ldof][ldof]
+    const float2 *__restrict__ Kc;       // FP64 element matrices as float pairs: the cache [nc][ldof][ldof]
+                                         // or a uniform mesh's one matrix [ldof][ldof]
     int ldof;
     const float4 *__restrict__ blk;      // per record: its 2 x 2 block of Kc, two rows of two float pairs
     const float2 *__restrict__ Edf;
@@ -587,7 +594,10 @@ struct ChunkBuf {
 // of tiles and the two destinations of a pair's block meet in L2.  The next
 // chunk's tables are copied into the other buffer while this one is worked;
 // within a tile the cell one position ahead is loaded while the current one is
-// contracted.
+// summed.  A record's block is formed by the contraction (FP32 element
+// matrices), read from its place in record order (CACHED: the cached FP64
+// matrices of 2D cells) or read through L1 from the one matrix of a uniform
+// mesh (UNIF).
 template <int D, bool CACHED, bool UNIF>
 __global__ void __launch_bounds__(256, D == 2 ? 4 : 3) k_contract_pairs(const PairArgs A)
 {
