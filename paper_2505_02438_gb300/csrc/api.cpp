@@ -36,7 +36,7 @@ static void free_device(DeviceMesh &d)
     void *ptrs[] = {d.indptr, d.indices, d.cell_node, d.node_off, d.inc_ptr, d.inc,
                     d.pos, d.geo, d.M, d.K, d.scratch, d.Edf, d.kappa, d.K0, d.sectors, d.udf, d.part,
                     d.inc_e, d.inc_a, d.counter, d.xcell, d.qw, d.qdphi, d.qdgeo, d.cg, d.lat_bad, d.stage,
-                    d.kvals, d.sgeo, d.sq, d.cgeo, d.Mf, d.ptoff, d.pia, d.pib, d.pmeta, d.pre, d.prm, d.pblk,
+                    d.kvals, d.sgeo, d.sq, d.ssf, d.cgeo, d.Mf, d.ptoff, d.pia, d.pib, d.pmeta, d.pre, d.prm, d.pblk,
                     d.cnrec, d.cinc_e, d.cinc_a, d.crec, d.cticket};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -121,6 +121,20 @@ static soptx_status setup_strain(soptx_mesh_s &m, const RefElement &ref, cudaStr
     for (size_t t = 0; t < sg.size(); t++) sg[t] = split_pair(h.geo[t]);
     soptx_status s = upload(&m.d.sq, tab, st, m.device_bytes, "quadrature table");
     if (s == SOPTX_OK) s = upload(&m.d.sgeo, sg, st, m.device_bytes, "cell geometry pairs");
+    if (s == SOPTX_OK && h.dim == 3 && !is_simplex(h.cell) && (h.order == 2 || h.order == 3)) {
+        // the 1D factors of the tensor rule, for the sum-factorised kernel
+        std::vector<double> w1, val, der;
+        tensor_1d_factors(h.order, w1, val, der);
+        const int n = h.order + 1;
+        std::vector<float2> sf;
+        for (double x : w1) sf.push_back(split_pair(x));
+        for (double x : val) sf.push_back(split_pair(x));
+        for (double x : der) sf.push_back(split_pair(x));
+        for (int a = 0; a < h.nb; a++)
+            sf.push_back(make_float2((float)(ref.lat[(size_t)a][0] + n * ref.lat[(size_t)a][1] + n * n * ref.lat[(size_t)a][2]),
+                                     0.f));
+        s = upload(&m.d.ssf, sf, st, m.device_bytes, "1D factors of the rule");
+    }
     if (s == SOPTX_OK) {
         m.d.snq = q.nq;
         m.d.strain = true;

@@ -56,6 +56,8 @@ struct RefQuad {
     std::vector<double> dgeo;   // [nq][nvc][dim]
 };
 void build_tensor_quadrature(const RefElement &ref, RefQuad &q);
+// its 1D factors: Gauss weights [n] and the basis values / derivatives [n][n]
+void tensor_1d_factors(int order, std::vector<double> &w, std::vector<double> &val, std::vector<double> &der);
 // Quadrature of the reference simplex exact for degree 2 (order - 1), with the
 // reference gradients of the basis at its points (dgeo left empty).
 void build_simplex_quadrature(const RefElement &ref, RefQuad &q);
@@ -123,6 +125,8 @@ struct DeviceMesh {
     float2 *sgeo = nullptr;        //   [nc, or 1 when uniform][d*d + 1] G and |det J| as float pairs
     float2 *sq = nullptr;          //   quadrature: weights [snq], reference gradients [snq][nb][d]
     int snq = 0;
+    float2 *ssf = nullptr;         //   hexahedra of order 2, 3: 1D weights, basis values and derivatives,
+                                   //   local nodes' lattice indices (k_strain_hex_sf)
     // FP32 element matrices of affine cells: assembled by contraction per call
     bool contract = false;         // the assembly takes k_contract_pairs (2D) or k_contract_rows (3D)
     float4 *cgeo = nullptr;        //   [nc][2 or 3] G and |det J| in FP32

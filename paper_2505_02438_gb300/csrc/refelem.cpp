@@ -288,6 +288,20 @@ static void lagrange1d(int k, int i, double t, double &val, double &der)
     }
 }
 
+// The one-dimensional factors of the tensor rule below: weights w[q] of the
+// order + 1 Gauss points t_q on [0, 1], and val[q][j] = l_j(t_q),
+// der[q][j] = l_j'(t_q) for the Lagrange polynomials on the nodes j / order.
+void tensor_1d_factors(int order, std::vector<double> &w, std::vector<double> &val, std::vector<double> &der)
+{
+    const int n = order + 1;
+    std::vector<double> t;
+    gauss_legendre01(n, t, w);
+    val.assign((size_t)n * n, 0.0);
+    der.assign((size_t)n * n, 0.0);
+    for (int q = 0; q < n; q++)
+        for (int j = 0; j < n; j++) lagrange1d(order, j, t[q], val[(size_t)q * n + j], der[(size_t)q * n + j]);
+}
+
 void build_tensor_quadrature(const RefElement &ref, RefQuad &q)
 {
     const int dim = ref.dim, k = ref.order, n = k + 1, nb = ref.nb;
