@@ -155,7 +155,7 @@ def test_traffic_records_are_keyed_on_kernel_workload_and_precision():
     assert lines
     src = {"k_lattice_assemble3": "lattice.cu", "k_lattice_assemble2": "lattice.cu", "k_lattice_sens": "lattice.cu",
            "k_gather_rows": "gather.cu", "k_gather_nodes": "gather.cu", "k_contract_rows": "contract.cu",
-           "k_contract_pairs": "contract.cu",
+           "k_contract_pairs": "contract.cu", "k_strain_hex_sf": "contract.cu",
            "k_strain_energy": "contract.cu", "k_spmv": "solve.cu", "k_simp_df": "lattice.cu", "k_prep": "gather.cu",
            "k_sens_finalize": "gather.cu"}
     for kv in lines:
