@@ -310,3 +310,27 @@ def test_step_host_matches_device_step(P, name, cell, k, coords, cells):
     with pytest.raises(N.SoptxError):
         N.check(N.lib().soptx_step_host(m._h, None, ctypes.c_void_p(u_h.data_ptr()),
                                         ctypes.c_void_p(vals2.data_ptr()), ctypes.c_void_p(dc2.data_ptr()), None, st))
+
+
+@pytest.mark.parametrize("k", [2, 3])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_hex_sensitivities_by_sum_factorisation(P, k, prec):
+    """Hexahedra of order 2 and 3 take the sum-factorised strain-energy kernel:
+    a sheared box (parallelepipeds, so G is a full matrix) against the oracle,
+    both element precisions."""
+    c, cl = W.structured_hex(3, 2, 2)
+    shear = np.array([[1.0, 0.3, -0.2], [0.1, 0.9, 0.25], [-0.15, 0.2, 1.1]])
+    coords = c @ shear.T + np.array([0.5, -1.0, 2.0])
+    m = P.Mesh("hex", k, coords, cl, *MAT, elem_prec=prec)
+    assert m.routes["sensitivity"] == "strain"
+    g = np.random.default_rng(20 + k)
+    rho = g.uniform(0.001, 1.0, len(cl))
+    u = g.standard_normal(m.ndof)
+    dc, cc = m.sensitivity(to_dev(rho), to_dev(u))
+    dco, so, co, sabs = oracle.sensitivity("hex", k, coords, cl, MAT, rho, u, with_abs=True)
+    E0, Emin, nu, p, ps = MAT
+    dE = p * rho ** (p - 1) * (E0 - Emin)
+    E = Emin + rho ** p * (E0 - Emin)
+    tol = TOL64 if prec == "fp64" else TOL32
+    assert np.all(np.abs(dc.cpu().numpy() - dco) <= tol * dE * sabs + 1e-300)
+    assert abs(cc.item() - co) <= tol * np.dot(E, sabs)
