@@ -309,6 +309,44 @@ soptx_status soptx_host_plan(int dim, soptx_cell cell, int order, int64_t n_vert
                              int64_t *ndof, int64_t *nnz, int32_t *nb, soptx_path *path,
                              int64_t *indptr, int32_t *indices, int32_t *cell_nodes);
 
+/*
+ * Host-only inspection (no device work, usable without a GPU) of the node-pair
+ * schedule by which the pair kernel forms K(rho) = sum_e E(rho_e) K_e^0
+ * (Sec. 2.2) on 2D affine meshes and uniform meshes.  Built exactly as
+ * soptx_mesh_create builds it for a mesh; the mesh arguments are those of
+ * soptx_host_plan.
+ *
+ * A pair is two nodes a, b that share a cell (or a = b).  In 2D K is
+ * symmetric, so each unordered pair appears once, owned by whichever node
+ * comes first in the processing order (nodes by first cell, then id), and its
+ * block is written into row block (a, b) and, transposed, into (b, a); in 3D
+ * every ordered pair appears, each node writing its own row blocks.  Pairs come
+ * in tiles of 32 (one per lane of a warp); lanes past a window's last pair are
+ * empty (count 0).  Per pair (int32 / uint32 arrays of n_tiles * 32 entries):
+ *   pair_block[t*32+l]   the CSR value index of entry (d a, d b) of block (a, b), divided by d;
+ *   pair_block_t[t*32+l] the same for block (b, a) (2D; 3D: equal to pair_block);
+ *   pair_meta[t*32+l]    cell count | (row length of a's rows) << 10 | (of b's rows) << 21.
+ * tile_offsets (uint32 [n_tiles + 1]): tile t's records are rows
+ * tile_offsets[t] .. tile_offsets[t+1] - 1 of 32 records each, record (k, l) at
+ * 32 k + l, the pair's k-th cell in ascending order (k below its count; the
+ * remaining slots are 0):
+ *   record_cell int32 [n_records]  the cell;
+ *   record_pair uint16 [n_records] the pair's local nodes in that cell, as
+ *                                  a_loc << 8 | b_loc when local_pair_bytes is
+ *                                  nonzero (the FP64 forms), else a_loc nb + b_loc.
+ * n_records = 32 * tile_offsets[n_tiles].  *n_tiles = -1 (and *n_records = 0)
+ * when the mesh is past the tables' limits (a node in more than 1023 cells,
+ * more than 255 nodes per cell, rows of more than 2047 values, value indices
+ * past 2^32 d): such meshes are assembled by the row gather.  Call once with
+ * NULL buffers for the sizes, then again with buffers of those sizes.
+ * Errors: those of soptx_host_plan.
+ */
+soptx_status soptx_host_pair_tables(int dim, soptx_cell cell, int order, int64_t n_vertices,
+                                    const double *coords, int64_t n_cells, const int32_t *cell_vertices,
+                                    int32_t local_pair_bytes, int64_t *n_tiles, int64_t *n_records,
+                                    uint32_t *tile_offsets, uint32_t *pair_block, uint32_t *pair_block_t,
+                                    uint32_t *pair_meta, int32_t *record_cell, uint16_t *record_pair);
+
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char *soptx_last_error(void);
 

@@ -247,3 +247,30 @@ def host_plan(cell, order, coords, cells):
                               indices.ctypes.data_as(ctypes.c_void_p), cn.ctypes.data_as(ctypes.c_void_p)))
     return dict(ndof=ndof.value, nnz=nnz.value, nb=nb.value, path=N.PATH[path.value], indptr=indptr,
                 indices=indices[: nnz.value], cell_nodes=cn)
+
+
+def host_pair_tables(cell, order, coords, cells, local_pair_bytes=False):
+    """Host-only node-pair schedule of the pair kernel (no GPU needed): returns
+    None for a mesh past the tables' limits, else dict(n_tiles, tile_offsets,
+    pair_block, pair_block_t, pair_meta, record_cell, record_pair) as numpy arrays."""
+    L = N.lib()
+    coords = np.ascontiguousarray(coords, np.float64)
+    cells = np.ascontiguousarray(cells, np.int32)
+    args = [coords.shape[1], N.CELL[cell], int(order), coords.shape[0], coords.ctypes.data_as(ctypes.c_void_p),
+            cells.shape[0], cells.ctypes.data_as(ctypes.c_void_p) if cells.size else None, int(bool(local_pair_bytes))]
+    nt, nr = ctypes.c_int64(), ctypes.c_int64()
+    N.check(L.soptx_host_pair_tables(*args, ctypes.byref(nt), ctypes.byref(nr), None, None, None, None, None, None))
+    if nt.value < 0:
+        return None
+    out = dict(n_tiles=nt.value, tile_offsets=np.zeros(nt.value + 1, np.uint32),
+               pair_block=np.zeros(max(nt.value, 1) * 32, np.uint32), pair_block_t=np.zeros(max(nt.value, 1) * 32, np.uint32),
+               pair_meta=np.zeros(max(nt.value, 1) * 32, np.uint32), record_cell=np.zeros(max(nr.value, 1), np.int32),
+               record_pair=np.zeros(max(nr.value, 1), np.uint16))
+    ptr = lambda k: out[k].ctypes.data_as(ctypes.c_void_p)
+    N.check(L.soptx_host_pair_tables(*args, None, None, ptr("tile_offsets"), ptr("pair_block"), ptr("pair_block_t"),
+                                     ptr("pair_meta"), ptr("record_cell"), ptr("record_pair")))
+    for k in ("pair_block", "pair_block_t", "pair_meta"):
+        out[k] = out[k][: nt.value * 32]
+    for k in ("record_cell", "record_pair"):
+        out[k] = out[k][: nr.value]
+    return out

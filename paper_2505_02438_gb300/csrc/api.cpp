@@ -163,31 +163,27 @@ static soptx_status setup_strain(soptx_mesh_s &m, const RefElement &ref, cudaStr
 // transposed.
 static constexpr size_t kPairWindow = 4096;
 
-static soptx_status setup_contract_pairs(soptx_mesh_s &m, const RefElement &ref, cudaStream_t st, bool cached,
-                                        bool unif = false)
+struct PairTables {
+    std::vector<uint32_t> ia, ib, meta;   // per pair, tiles of 32 lanes
+    std::vector<uint32_t> toff;           // [tiles + 1] record offsets / 32
+    std::vector<int32_t> re;              // per record: the cell
+    std::vector<uint16_t> rm;             // per record: the local pair
+    int64_t ntiles = 0;
+};
+
+// The pair tables, on the host.  bytes: the local pair as a_loc << 8 | b_loc,
+// else a_loc nb + b_loc.  False when a node meets more than 1023 cells or a
+// value index / d needs more than 32 bits (a pair's cell count has 10 bits in
+// the tables): such meshes keep the cached gather.
+static bool build_pair_tables(const HostMesh &h, bool bytes, PairTables &T)
 {
-    const HostMesh &h = m.h;
-    const int d = h.dim, nb = h.nb, ng = d * d + 1, n4 = d == 3 ? 3 : 2, mp = d == 3 ? 12 : 4;
+    const int d = h.dim, nb = h.nb;
     // 3D: every node assembles all of its own row blocks (the symmetric layout's
     // transposed 24-byte pieces leave L2 sectors partly filled)
     const bool sym = d == 2;
-    const bool bytes = cached || unif;   // local pair as a_loc << 8 | b_loc
-    // a pair's cell count has 10 bits in the tables, a value index / d has 32:
-    // larger fans or matrices keep the cached gather
     for (int64_t n = 0; n < h.nn; n++)
-        if (h.inc_ptr[(size_t)n + 1] - h.inc_ptr[(size_t)n] > 1023) return SOPTX_OK;
-    if ((int64_t)d * h.node_off[(size_t)h.nn] > (int64_t)UINT32_MAX) return SOPTX_OK;
-    std::vector<float4> cg((size_t)h.nc * n4, make_float4(0.f, 0.f, 0.f, 0.f));
-    for (int64_t e = 0; e < h.nc; e++) {
-        float *dst = reinterpret_cast<float *>(&cg[(size_t)e * n4]);
-        for (int t = 0; t < ng; t++) dst[t] = (float)h.geo[(size_t)e * ng + t];
-    }
-    std::vector<float> mf((size_t)nb * nb * mp, 0.f);
-    for (int a = 0; a < nb; a++)
-        for (int b = 0; b < nb; b++)
-            for (int k = 0; k < d; k++)
-                for (int l = 0; l < d; l++)
-                    mf[((size_t)a * nb + b) * mp + k * d + l] = (float)ref.M[(((size_t)k * d + l) * nb + a) * nb + b];
+        if (h.inc_ptr[(size_t)n + 1] - h.inc_ptr[(size_t)n] > 1023) return false;
+    if ((int64_t)d * h.node_off[(size_t)h.nn] > (int64_t)UINT32_MAX) return false;
     // processing order: nodes by first cell (the incidences are in ascending cell
     // order), then id; a counting sort
     std::vector<int32_t> order((size_t)h.nn), rank((size_t)h.nn);
@@ -206,9 +202,15 @@ static soptx_status setup_contract_pairs(soptx_mesh_s &m, const RefElement &ref,
     for (int64_t n = 0; n < h.nn; n++)
         for (int32_t q = h.inc_ptr[(size_t)n]; q < h.inc_ptr[(size_t)n + 1]; q++)
             cinc[(size_t)h.inc_e[(size_t)q] * nb + h.inc_a[(size_t)q]] = q;
-    std::vector<uint32_t> ia, ib, meta, toff(1, 0u);
-    std::vector<int32_t> re;
-    std::vector<uint16_t> rm;
+    auto &ia = T.ia, &ib = T.ib, &meta = T.meta, &toff = T.toff;
+    auto &re = T.re;
+    auto &rm = T.rm;
+    ia.clear();
+    ib.clear();
+    meta.clear();
+    toff.assign(1, 0u);
+    re.clear();
+    rm.clear();
     struct WPair {
         uint32_t pa, pb, meta;
         size_t r0;
@@ -301,20 +303,43 @@ static soptx_status setup_contract_pairs(soptx_mesh_s &m, const RefElement &ref,
     ia.resize((size_t)(nchunks * 8 * 32), 0u);
     ib.resize((size_t)(nchunks * 8 * 32), 0u);
     meta.resize((size_t)(nchunks * 8 * 32), 0u);
+    T.ntiles = ntiles;
+    return true;
+}
+
+static soptx_status setup_contract_pairs(soptx_mesh_s &m, const RefElement &ref, cudaStream_t st, bool cached,
+                                        bool unif = false)
+{
+    const HostMesh &h = m.h;
+    const int d = h.dim, nb = h.nb, ng = d * d + 1, n4 = d == 3 ? 3 : 2, mp = d == 3 ? 12 : 4;
+    const bool bytes = cached || unif;   // local pair as a_loc << 8 | b_loc
+    PairTables T;
+    if (!build_pair_tables(h, bytes, T)) return SOPTX_OK;
+    std::vector<float4> cg((size_t)h.nc * n4, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int64_t e = 0; e < h.nc; e++) {
+        float *dst = reinterpret_cast<float *>(&cg[(size_t)e * n4]);
+        for (int t = 0; t < ng; t++) dst[t] = (float)h.geo[(size_t)e * ng + t];
+    }
+    std::vector<float> mf((size_t)nb * nb * mp, 0.f);
+    for (int a = 0; a < nb; a++)
+        for (int b = 0; b < nb; b++)
+            for (int k = 0; k < d; k++)
+                for (int l = 0; l < d; l++)
+                    mf[((size_t)a * nb + b) * mp + k * d + l] = (float)ref.M[(((size_t)k * d + l) * nb + a) * nb + b];
     soptx_status s = SOPTX_OK;
     if (!bytes) s = upload(&m.d.cgeo, cg, st, m.device_bytes, "cell geometry");
     if (s == SOPTX_OK && !bytes) s = upload(&m.d.Mf, mf, st, m.device_bytes, "reference integrals (FP32)");
-    if (s == SOPTX_OK) s = upload(&m.d.ptoff, toff, st, m.device_bytes, "pair tiles");
-    if (s == SOPTX_OK) s = upload(&m.d.pia, ia, st, m.device_bytes, "pair blocks");
-    if (s == SOPTX_OK) s = upload(&m.d.pib, ib, st, m.device_bytes, "pair transposed blocks");
-    if (s == SOPTX_OK) s = upload(&m.d.pmeta, meta, st, m.device_bytes, "pair counts and row lengths");
-    if (s == SOPTX_OK) s = upload(&m.d.pre, re, st, m.device_bytes, "pair cells");
-    if (s == SOPTX_OK) s = upload(&m.d.prm, rm, st, m.device_bytes, "pair reference integrals");
+    if (s == SOPTX_OK) s = upload(&m.d.ptoff, T.toff, st, m.device_bytes, "pair tiles");
+    if (s == SOPTX_OK) s = upload(&m.d.pia, T.ia, st, m.device_bytes, "pair blocks");
+    if (s == SOPTX_OK) s = upload(&m.d.pib, T.ib, st, m.device_bytes, "pair transposed blocks");
+    if (s == SOPTX_OK) s = upload(&m.d.pmeta, T.meta, st, m.device_bytes, "pair counts and row lengths");
+    if (s == SOPTX_OK) s = upload(&m.d.pre, T.re, st, m.device_bytes, "pair cells");
+    if (s == SOPTX_OK) s = upload(&m.d.prm, T.rm, st, m.device_bytes, "pair reference integrals");
     if (s == SOPTX_OK) s = upload(&m.d.cticket, std::vector<unsigned>(2, 0u), st, m.device_bytes, "chunk counter");
     if (s == SOPTX_OK && cached) {
         // each record's block of the cache, gathered once here so the kernel reads
         // them in record order
-        const int64_t nrec = (int64_t)re.size();
+        const int64_t nrec = (int64_t)T.re.size();
         cudaError_t e = dev_alloc((void **)&m.d.pblk, (size_t)std::max<int64_t>(nrec, 1) * 2 * sizeof(float4));
         if (e == cudaSuccess) e = launch_pair_blocks(m, nrec, st);
         if (e != cudaSuccess) {
@@ -325,7 +350,7 @@ static soptx_status setup_contract_pairs(soptx_mesh_s &m, const RefElement &ref,
         }
     }
     if (s == SOPTX_OK) {
-        m.d.ptiles = ntiles;
+        m.d.ptiles = T.ntiles;
         (unif ? m.d.puniform : cached ? m.d.pcached : m.d.contract) = true;
     }
     return s;
@@ -706,10 +731,9 @@ soptx_status soptx_mesh_create(int dim, soptx_cell cell, int order, int64_t n_ve
     return SOPTX_OK;
 }
 
-soptx_status soptx_host_plan(int dim, soptx_cell cell, int order, int64_t n_vertices, const double *coords,
-                             int64_t n_cells, const int32_t *cell_vertices, int64_t *ndof, int64_t *nnz,
-                             int32_t *nb, soptx_path *path, int64_t *indptr, int32_t *indices,
-                             int32_t *cell_nodes)
+// The validation, numbering and pattern of soptx_mesh_create, on the host.
+static soptx_status plan_on_host(int dim, soptx_cell cell, int order, int64_t n_vertices, const double *coords,
+                                 int64_t n_cells, const int32_t *cell_vertices, RefElement &ref, HostMesh &h)
 {
     g_last_error.clear();
     if ((int)cell < SOPTX_TRI || (int)cell > SOPTX_HEX) SOPTX_FAIL(SOPTX_EINVAL, "unknown cell type");
@@ -717,13 +741,23 @@ soptx_status soptx_host_plan(int dim, soptx_cell cell, int order, int64_t n_vert
     if (order < 1 || order > 3) SOPTX_FAIL(SOPTX_EINVAL, "order must be 1, 2 or 3");
     if (n_vertices < 1 || n_cells < 0) SOPTX_FAIL(SOPTX_EINVAL, "need n_vertices >= 1 and n_cells >= 0");
     if (!coords || (n_cells > 0 && !cell_vertices)) SOPTX_FAIL(SOPTX_EINVAL, "coords / cell_vertices is NULL");
+    std::string err;
+    if (!build_ref_element(cell, order, ref, err) ||
+        !setup_host_mesh(dim, cell, order, n_vertices, coords, n_cells, cell_vertices, ref, h, err))
+        SOPTX_FAIL(SOPTX_EINVAL, err);
+    return SOPTX_OK;
+}
+
+soptx_status soptx_host_plan(int dim, soptx_cell cell, int order, int64_t n_vertices, const double *coords,
+                             int64_t n_cells, const int32_t *cell_vertices, int64_t *ndof, int64_t *nnz,
+                             int32_t *nb, soptx_path *path, int64_t *indptr, int32_t *indices,
+                             int32_t *cell_nodes)
+{
     RefElement ref;
     HostMesh h;
-    std::string err;
     try {
-        if (!build_ref_element(cell, order, ref, err) ||
-            !setup_host_mesh(dim, cell, order, n_vertices, coords, n_cells, cell_vertices, ref, h, err))
-            SOPTX_FAIL(SOPTX_EINVAL, err);
+        const soptx_status s = plan_on_host(dim, cell, order, n_vertices, coords, n_cells, cell_vertices, ref, h);
+        if (s != SOPTX_OK) return s;
         if (ndof) *ndof = h.ndof;
         if (nnz) *nnz = h.nnz;
         if (nb) *nb = h.nb;
@@ -737,6 +771,38 @@ soptx_status soptx_host_plan(int dim, soptx_cell cell, int order, int64_t n_vert
         }
         if (cell_nodes && !h.cell_node.empty())
             std::memcpy(cell_nodes, h.cell_node.data(), h.cell_node.size() * sizeof(int32_t));
+    } catch (const std::bad_alloc &) {
+        SOPTX_FAIL(SOPTX_ENOMEM, "host allocation failed");
+    }
+    return SOPTX_OK;
+}
+
+soptx_status soptx_host_pair_tables(int dim, soptx_cell cell, int order, int64_t n_vertices, const double *coords,
+                                    int64_t n_cells, const int32_t *cell_vertices, int32_t local_pair_bytes,
+                                    int64_t *n_tiles, int64_t *n_records, uint32_t *tile_offsets,
+                                    uint32_t *pair_block, uint32_t *pair_block_t, uint32_t *pair_meta,
+                                    int32_t *record_cell, uint16_t *record_pair)
+{
+    RefElement ref;
+    HostMesh h;
+    try {
+        const soptx_status s = plan_on_host(dim, cell, order, n_vertices, coords, n_cells, cell_vertices, ref, h);
+        if (s != SOPTX_OK) return s;
+        PairTables T;
+        if (!pairs_fit(h.dim, h.nb, h.max_deg) || !build_pair_tables(h, local_pair_bytes != 0, T)) {
+            if (n_tiles) *n_tiles = -1;
+            if (n_records) *n_records = 0;
+            return SOPTX_OK;
+        }
+        const int64_t nt = T.ntiles, nrec = (int64_t)T.toff[(size_t)nt] * 32;
+        if (n_tiles) *n_tiles = nt;
+        if (n_records) *n_records = nrec;
+        if (tile_offsets) std::memcpy(tile_offsets, T.toff.data(), (size_t)(nt + 1) * sizeof(uint32_t));
+        if (pair_block && nt) std::memcpy(pair_block, T.ia.data(), (size_t)nt * 32 * sizeof(uint32_t));
+        if (pair_block_t && nt) std::memcpy(pair_block_t, T.ib.data(), (size_t)nt * 32 * sizeof(uint32_t));
+        if (pair_meta && nt) std::memcpy(pair_meta, T.meta.data(), (size_t)nt * 32 * sizeof(uint32_t));
+        if (record_cell && nrec) std::memcpy(record_cell, T.re.data(), (size_t)nrec * sizeof(int32_t));
+        if (record_pair && nrec) std::memcpy(record_pair, T.rm.data(), (size_t)nrec * sizeof(uint16_t));
     } catch (const std::bad_alloc &) {
         SOPTX_FAIL(SOPTX_ENOMEM, "host allocation failed");
     }
