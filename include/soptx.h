@@ -347,6 +347,40 @@ soptx_status soptx_host_pair_tables(int dim, soptx_cell cell, int order, int64_t
                                     uint32_t *tile_offsets, uint32_t *pair_block, uint32_t *pair_block_t,
                                     uint32_t *pair_meta, int32_t *record_cell, uint16_t *record_pair);
 
+/*
+ * Host-only inspection (no device work, usable without a GPU) of the
+ * node-owner schedule by which 3D meshes with FP32 element matrices form
+ * K(rho) = sum_e E(rho_e) K_e^0 (Sec. 2.2): a group of nb lanes owns the d rows
+ * of one node and walks the node's cells as a chain.  Built exactly as
+ * soptx_mesh_create builds it; the mesh arguments are those of soptx_host_plan.
+ *   node_records int32 [n_nodes][4], in processing order (cell count
+ *     descending, then node id): the node's first row block offset (low and
+ *     high 32-bit words; the value index of its entry (d n, .) is d^2 times
+ *     it), its first incidence q0, and cell count << 16 | degree (the number
+ *     of column blocks in its rows).
+ *   chain_cell int32 [n_incidences], chain_local uint8 [n_incidences]: for
+ *     each node, at q0 .. q0 + count - 1, its cells in chain order (the first
+ *     is its lowest cell; then the unvisited cell holding the most of the
+ *     nodes the lanes hold, lowest id on ties) and its local index there.
+ *   lane_records uint16 [n_incidences][nb]: per chain position and lane, the
+ *     column block p (bits 0-8, its position in the node's rows), the lane's
+ *     local node b in that cell (bits 9-13; a lane keeps its node when the
+ *     next cell holds it, the other nodes go to the free lanes in local
+ *     order), and whether this is the first (bit 14) or the last (bit 15)
+ *     (position, lane) of the chain that meets block p.
+ * *n_nodes = -1 (and *n_incidences = 0) for a 2D mesh or one past the
+ * schedule's limits (other than 4, 8, 10, 20 or 27 nodes per cell, more than
+ * 512 column blocks per row, 65536 or more cells at a node, or accumulators
+ * past shared memory): such meshes are assembled otherwise.  *nb is set
+ * whenever the call succeeds.  Call once with NULL buffers for the sizes, then
+ * again with buffers of those sizes.  Errors: those of soptx_host_plan.
+ */
+soptx_status soptx_host_row_tables(int dim, soptx_cell cell, int order, int64_t n_vertices,
+                                   const double *coords, int64_t n_cells, const int32_t *cell_vertices,
+                                   int64_t *n_nodes, int64_t *n_incidences, int32_t *nb,
+                                   int32_t *node_records, int32_t *chain_cell, uint8_t *chain_local,
+                                   uint16_t *lane_records);
+
 /* Thread-local message of the last failed call on this thread ("" if none). */
 const char *soptx_last_error(void);
 

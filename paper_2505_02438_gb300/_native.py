@@ -91,6 +91,7 @@ SIGNATURES = {
     "soptx_mesh_destroy": (i32, [P]),
     "soptx_host_plan": (i32, [i32, i32, i32, i64, P, i64, P, Pi64, Pi64, Pi32, Pi32, P, P, P]),
     "soptx_host_pair_tables": (i32, [i32, i32, i32, i64, P, i64, P, i32, Pi64, Pi64, P, P, P, P, P, P]),
+    "soptx_host_row_tables": (i32, [i32, i32, i32, i64, P, i64, P, Pi64, Pi64, Pi32, P, P, P, P]),
     "soptx_lattice_sensitivity_noalloc": (i32, [i32, P, P, ctypes.POINTER(Material), P, P, P, P, P]),
     "soptx_spmv": (i32, [P, P, P, P, P]),
     "soptx_solve_cg": (i32, [P, P, P, P, P, ctypes.POINTER(CgOpts), P, ctypes.POINTER(CgResult)]),

@@ -274,3 +274,29 @@ def host_pair_tables(cell, order, coords, cells, local_pair_bytes=False):
     for k in ("record_cell", "record_pair"):
         out[k] = out[k][: nr.value]
     return out
+
+
+def host_row_tables(cell, order, coords, cells):
+    """Host-only node-owner schedule of 3D meshes with FP32 element matrices (no
+    GPU needed): None where mesh creation builds none, else dict(nb, node_records
+    int32 [nn][4], chain_cell, chain_local, lane_records [n_incidences][nb])."""
+    L = N.lib()
+    coords = np.ascontiguousarray(coords, np.float64)
+    cells = np.ascontiguousarray(cells, np.int32)
+    args = [coords.shape[1], N.CELL[cell], int(order), coords.shape[0], coords.ctypes.data_as(ctypes.c_void_p),
+            cells.shape[0], cells.ctypes.data_as(ctypes.c_void_p) if cells.size else None]
+    nn, ni, nb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+    N.check(L.soptx_host_row_tables(*args, ctypes.byref(nn), ctypes.byref(ni), ctypes.byref(nb), None, None, None,
+                                    None))
+    if nn.value < 0:
+        return None
+    out = dict(nb=nb.value, node_records=np.zeros((max(nn.value, 1), 4), np.int32),
+               chain_cell=np.zeros(max(ni.value, 1), np.int32), chain_local=np.zeros(max(ni.value, 1), np.uint8),
+               lane_records=np.zeros((max(ni.value, 1), nb.value), np.uint16))
+    ptr = lambda k: out[k].ctypes.data_as(ctypes.c_void_p)
+    N.check(L.soptx_host_row_tables(*args, None, None, None, ptr("node_records"), ptr("chain_cell"),
+                                    ptr("chain_local"), ptr("lane_records")))
+    out["node_records"] = out["node_records"][: nn.value]
+    for k in ("chain_cell", "chain_local", "lane_records"):
+        out[k] = out[k][: ni.value]
+    return out

@@ -356,25 +356,23 @@ static soptx_status setup_contract_pairs(soptx_mesh_s &m, const RefElement &ref,
     return s;
 }
 
-// Tables of the node-owner contraction of 3D cells (k_contract_rows).
-static soptx_status setup_contract_rows(soptx_mesh_s &m, const RefElement &ref, cudaStream_t st)
+// Tables of the node-owner contraction of 3D cells (k_contract_rows), on the
+// host.  False when a node meets 65536 cells or more (a node record holds the
+// incident-cell count in 16 bits): such fans keep the cached gather.
+struct RowTables {
+    // per node in processing order: its row block offset (node_off, low and
+    // high words), first incidence, cell count << 16 | degree
+    std::vector<int4> nrec;
+    std::vector<int32_t> ce;      // per incidence, each node's cells in chain order
+    std::vector<uint8_t> ca;      // the node's local index in that cell
+    std::vector<uint16_t> rec;    // per (incidence, lane): p | b << 9 | first << 14 | last << 15
+};
+
+static bool build_row_tables(const HostMesh &h, RowTables &T)
 {
-    const HostMesh &h = m.h;
-    const int d = h.dim, nb = h.nb, ng = d * d + 1, n4 = d == 3 ? 3 : 2, mp = d == 3 ? 12 : 4;
-    // a node record holds the incident-cell count in 16 bits: larger fans keep the cached gather
+    const int nb = h.nb;
     for (int64_t n = 0; n < h.nn; n++)
-        if (h.inc_ptr[(size_t)n + 1] - h.inc_ptr[(size_t)n] >= 65536) return SOPTX_OK;
-    std::vector<float4> cg((size_t)h.nc * n4, make_float4(0.f, 0.f, 0.f, 0.f));
-    for (int64_t e = 0; e < h.nc; e++) {
-        float *dst = reinterpret_cast<float *>(&cg[(size_t)e * n4]);
-        for (int t = 0; t < ng; t++) dst[t] = (float)h.geo[(size_t)e * ng + t];
-    }
-    std::vector<float> mf((size_t)nb * nb * mp, 0.f);
-    for (int a = 0; a < nb; a++)
-        for (int b = 0; b < nb; b++)
-            for (int k = 0; k < d; k++)
-                for (int l = 0; l < d; l++)
-                    mf[((size_t)a * nb + b) * mp + k * d + l] = (float)ref.M[(((size_t)k * d + l) * nb + a) * nb + b];
+        if (h.inc_ptr[(size_t)n + 1] - h.inc_ptr[(size_t)n] >= 65536) return false;
     // processing order: nodes by incident-cell count, largest first, ascending ids
     // within a count (a counting sort), so a warp's node groups walk as many cells
     std::vector<int32_t> order((size_t)h.nn);
@@ -395,9 +393,12 @@ static soptx_status setup_contract_rows(soptx_mesh_s &m, const RefElement &ref, 
     // local node b (bits 9-13), and whether this is the first (bit 14) or the last
     // (bit 15) time the node's chain meets that block.
     const int64_t ninc = h.inc_ptr[(size_t)h.nn];
-    std::vector<int32_t> ce((size_t)ninc);
-    std::vector<uint8_t> ca((size_t)ninc);
-    std::vector<uint16_t> rec((size_t)ninc * nb);
+    auto &ce = T.ce;
+    auto &ca = T.ca;
+    auto &rec = T.rec;
+    ce.assign((size_t)ninc, 0);
+    ca.assign((size_t)ninc, 0);
+    rec.assign((size_t)ninc * nb, 0);
     {
         std::vector<int64_t> lane_mark((size_t)h.nn, -1), cell_mark((size_t)h.nn, -1);
         std::vector<int32_t> cell_loc((size_t)h.nn, 0);
@@ -468,19 +469,40 @@ static soptx_status setup_contract_rows(soptx_mesh_s &m, const RefElement &ref, 
                 }
         }
     }
-    soptx_status s = upload(&m.d.cgeo, cg, st, m.device_bytes, "cell geometry");
-    if (s == SOPTX_OK) s = upload(&m.d.Mf, mf, st, m.device_bytes, "reference integrals (FP32)");
-    std::vector<int4> nrec((size_t)h.nn);
+    auto &nrec = T.nrec;
+    nrec.assign((size_t)h.nn, make_int4(0, 0, 0, 0));
     for (int64_t i = 0; i < h.nn; i++) {
         const int64_t n = order[(size_t)i], off = h.node_off[(size_t)n];
         const int32_t deg = (int32_t)(h.node_off[(size_t)n + 1] - off), q0 = h.inc_ptr[(size_t)n],
                       cnt = h.inc_ptr[(size_t)n + 1] - q0;
         nrec[(size_t)i] = make_int4((int)(uint32_t)off, (int)(off >> 32), q0, (int)(((uint32_t)cnt << 16) | (uint32_t)deg));
     }
-    if (s == SOPTX_OK) s = upload(&m.d.cnrec, nrec, st, m.device_bytes, "node records");
-    if (s == SOPTX_OK) s = upload(&m.d.cinc_e, ce, st, m.device_bytes, "contraction cell chains");
-    if (s == SOPTX_OK) s = upload(&m.d.cinc_a, ca, st, m.device_bytes, "contraction local indices");
-    if (s == SOPTX_OK) s = upload(&m.d.crec, rec, st, m.device_bytes, "contraction lane records");
+    return true;
+}
+
+static soptx_status setup_contract_rows(soptx_mesh_s &m, const RefElement &ref, cudaStream_t st)
+{
+    const HostMesh &h = m.h;
+    const int d = h.dim, nb = h.nb, ng = d * d + 1, n4 = d == 3 ? 3 : 2, mp = d == 3 ? 12 : 4;
+    RowTables T;
+    if (!build_row_tables(h, T)) return SOPTX_OK;
+    std::vector<float4> cg((size_t)h.nc * n4, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int64_t e = 0; e < h.nc; e++) {
+        float *dst = reinterpret_cast<float *>(&cg[(size_t)e * n4]);
+        for (int t = 0; t < ng; t++) dst[t] = (float)h.geo[(size_t)e * ng + t];
+    }
+    std::vector<float> mf((size_t)nb * nb * mp, 0.f);
+    for (int a = 0; a < nb; a++)
+        for (int b = 0; b < nb; b++)
+            for (int k = 0; k < d; k++)
+                for (int l = 0; l < d; l++)
+                    mf[((size_t)a * nb + b) * mp + k * d + l] = (float)ref.M[(((size_t)k * d + l) * nb + a) * nb + b];
+    soptx_status s = upload(&m.d.cgeo, cg, st, m.device_bytes, "cell geometry");
+    if (s == SOPTX_OK) s = upload(&m.d.Mf, mf, st, m.device_bytes, "reference integrals (FP32)");
+    if (s == SOPTX_OK) s = upload(&m.d.cnrec, T.nrec, st, m.device_bytes, "node records");
+    if (s == SOPTX_OK) s = upload(&m.d.cinc_e, T.ce, st, m.device_bytes, "contraction cell chains");
+    if (s == SOPTX_OK) s = upload(&m.d.cinc_a, T.ca, st, m.device_bytes, "contraction local indices");
+    if (s == SOPTX_OK) s = upload(&m.d.crec, T.rec, st, m.device_bytes, "contraction lane records");
     if (s == SOPTX_OK) s = upload(&m.d.cticket, std::vector<unsigned>(2, 0u), st, m.device_bytes, "round counter");
     if (s == SOPTX_OK) m.d.contract = true;
     return s;
@@ -803,6 +825,36 @@ soptx_status soptx_host_pair_tables(int dim, soptx_cell cell, int order, int64_t
         if (pair_meta && nt) std::memcpy(pair_meta, T.meta.data(), (size_t)nt * 32 * sizeof(uint32_t));
         if (record_cell && nrec) std::memcpy(record_cell, T.re.data(), (size_t)nrec * sizeof(int32_t));
         if (record_pair && nrec) std::memcpy(record_pair, T.rm.data(), (size_t)nrec * sizeof(uint16_t));
+    } catch (const std::bad_alloc &) {
+        SOPTX_FAIL(SOPTX_ENOMEM, "host allocation failed");
+    }
+    return SOPTX_OK;
+}
+
+soptx_status soptx_host_row_tables(int dim, soptx_cell cell, int order, int64_t n_vertices, const double *coords,
+                                   int64_t n_cells, const int32_t *cell_vertices, int64_t *n_nodes,
+                                   int64_t *n_incidences, int32_t *nb, int32_t *node_records, int32_t *chain_cell,
+                                   uint8_t *chain_local, uint16_t *lane_records)
+{
+    RefElement ref;
+    HostMesh h;
+    try {
+        const soptx_status s = plan_on_host(dim, cell, order, n_vertices, coords, n_cells, cell_vertices, ref, h);
+        if (s != SOPTX_OK) return s;
+        if (nb) *nb = h.nb;
+        RowTables T;
+        if (h.dim != 3 || !contract_fits(h.dim, h.nb, h.max_deg) || !build_row_tables(h, T)) {
+            if (n_nodes) *n_nodes = -1;
+            if (n_incidences) *n_incidences = 0;
+            return SOPTX_OK;
+        }
+        const int64_t ninc = (int64_t)T.ce.size();
+        if (n_nodes) *n_nodes = h.nn;
+        if (n_incidences) *n_incidences = ninc;
+        if (node_records && h.nn) std::memcpy(node_records, T.nrec.data(), (size_t)h.nn * sizeof(int4));
+        if (chain_cell && ninc) std::memcpy(chain_cell, T.ce.data(), (size_t)ninc * sizeof(int32_t));
+        if (chain_local && ninc) std::memcpy(chain_local, T.ca.data(), (size_t)ninc * sizeof(uint8_t));
+        if (lane_records && ninc) std::memcpy(lane_records, T.rec.data(), (size_t)ninc * h.nb * sizeof(uint16_t));
     } catch (const std::bad_alloc &) {
         SOPTX_FAIL(SOPTX_ENOMEM, "host allocation failed");
     }
