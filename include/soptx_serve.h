@@ -99,6 +99,17 @@ soptx_status soptx_server_create(const soptx_server_opts *opts, soptx_server *ou
  * admission and reported through the result). */
 soptx_status soptx_serve_submit(soptx_server srv, const soptx_request *req, uint64_t *ticket);
 
+/* Host only (no device work, usable without a GPU): an upper bound of the
+ * device bytes soptx_mesh_create allocates for the request's mesh, from its
+ * description alone (the device buffers are not read).  The server makes this
+ * much room under hbm_cap_bytes (evicting idle meshes) before it builds a
+ * job's mesh, then accounts the mesh's actual bytes: a job whose bound exceeds
+ * the cap is still built once nothing else is resident, and fails with ENOMEM
+ * only if its actual bytes do.  One pass over the cell array (the most cells
+ * at a vertex bounds the padding of the pair kernel's tables).  Errors: EINVAL
+ * for a NULL argument or a malformed mesh description, ENOMEM. */
+soptx_status soptx_serve_mesh_bytes_bound(const soptx_request *req, int64_t *bytes);
+
 /* Waits up to timeout_us (< 0: forever) for the ticket; on success fills *res
  * and forgets the ticket.  ETIMEOUT if it did not complete in time (the ticket
  * stays valid), ENOTFOUND for an unknown or already collected ticket. */

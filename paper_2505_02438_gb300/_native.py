@@ -105,6 +105,7 @@ SIGNATURES = {
     "soptx_oc_update": (i32, [i64, P, P, P, P, ctypes.POINTER(OcOpts), P, P, P]),
     "soptx_server_create": (i32, [ctypes.POINTER(ServerOpts), PP]),
     "soptx_serve_submit": (i32, [P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "soptx_serve_mesh_bytes_bound": (i32, [ctypes.POINTER(Request), Pi64]),
     "soptx_serve_wait": (i32, [P, ctypes.c_uint64, i64, ctypes.POINTER(Result)]),
     "soptx_serve_poll": (i32, [P, ctypes.c_uint64, Pi32]),
     "soptx_server_stats_get": (i32, [P, ctypes.POINTER(ServerStats)]),

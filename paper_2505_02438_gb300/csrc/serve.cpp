@@ -42,6 +42,7 @@ struct Job {
     int stream = 0;
     int64_t nnz = 0;
     int64_t known_bytes = 0;   // device bytes of this job's mesh once it has been built
+    int64_t bound_bytes = 0;   // mesh_bytes_bound of its request, before it has been built
 };
 
 struct Req {
@@ -54,18 +55,48 @@ struct Req {
     Job *job = nullptr;
 };
 
-// Upper bound of a mesh's device bytes from its input sizes alone (every
-// array of soptx_mesh_create at its largest), used before the mesh exists.
+// The most cells at one vertex of a request's mesh: a bound on the cells that
+// any two of its nodes share (those cells all hold a vertex of the first node's
+// edge, face or cell).  Ids out of range are skipped (mesh creation rejects them).
+int64_t max_cells_at_vertex(const soptx_request &r, int nv)
+{
+    if (!r.cell_vertices || r.n_cells <= 0) return 0;
+    std::vector<int32_t> cnt((size_t)r.n_vertices, 0);
+    int32_t best = 0;
+    for (int64_t q = 0; q < r.n_cells * nv; q++) {
+        const int32_t v = r.cell_vertices[q];
+        if (v >= 0 && v < r.n_vertices) best = std::max(best, ++cnt[(size_t)v]);
+    }
+    return best;
+}
+
+// Upper bound of a mesh's device bytes from its input alone (every array of
+// soptx_mesh_create at its largest), used before the mesh exists.  The node-pair
+// tables of the pair kernel hold R records (a pair and one cell of it: at most
+// nb (nb + 1) / 2 per cell in 2D, nb^2 in 3D) padded per tile of 32 pairs to its
+// largest count; within a window of pairs sorted by count a tile's largest is at
+// most the previous tile's smallest, so a window pads at most 32 times its
+// largest count (at most the most cells at a vertex, c) above its own records,
+// and windows hold 4096 pairs or more but the last.  In 2D with FP64 element
+// matrices each record also carries its 2 x 2 block (32 bytes).
 int64_t mesh_bytes_bound(const soptx_request &r)
 {
     static const int nb_tab[4][4] = {{0, 3, 6, 10}, {0, 4, 10, 20}, {0, 4, 9, 16}, {0, 8, 27, 64}};
+    static const int nv_tab[4] = {3, 4, 4, 8};
     const int64_t nb = nb_tab[r.cell][std::min(std::max(r.order, 1), 3)];
     const int64_t ldof = r.dim * nb, nc = r.n_cells;
     const int64_t ee = nc * ldof * ldof;          // >= nnz
     const int64_t nn = r.n_vertices + nc * nb;    // >= nodes
-    return ee * 8 /* K_e (cached) */ + ee * 4 /* indices */ + nc * nb * nb * 2 /* pos */ +
-           nc * nb * (4 + 4 + 4 + 1 + 8) /* cell_node, inc, inc_e, inc_a, partials */ + nn * r.dim * (8 + 8) +
-           nn * 20 + nc * 120 + (1 << 20);
+    const int64_t base = ee * 8 /* K_e (cached) */ + ee * 4 /* indices */ + nc * nb * nb * 2 /* pos */ +
+                         nc * nb * (4 + 4 + 4 + 1 + 8) /* cell_node, inc, inc_e, inc_a, partials */ +
+                         nn * r.dim * (8 + 8) + nn * 20 + nc * 120 + (1 << 20);
+    const int64_t c = std::min<int64_t>(max_cells_at_vertex(r, nv_tab[r.cell]), 1023);
+    const int64_t rec = nc * (r.dim == 2 ? nb * (nb + 1) / 2 : nb * nb);
+    const int64_t windows = rec / 4096 + 1;
+    const int64_t padded = rec + windows * 32 * c;
+    const int64_t lanes = rec + windows * 32 + 7 * 32;   // and the last chunk of 8 tiles filled
+    const int64_t per_rec = 4 + 2 + (r.dim == 2 && r.prec == SOPTX_ELEM_FP64 ? 32 : 0);
+    return base + padded * per_rec + lanes * 12 + (lanes / 32 + 32) * 4 + 64;
 }
 
 }  // namespace
@@ -265,7 +296,8 @@ struct soptx_server_s {
                 Job *j = jp;
                 q->job = j;
                 if (!j->mesh) {
-                    const int64_t bound = j->known_bytes ? j->known_bytes : mesh_bytes_bound(q->r);
+                    if (!j->known_bytes && !j->bound_bytes) j->bound_bytes = mesh_bytes_bound(q->r);
+                    const int64_t bound = j->known_bytes ? j->known_bytes : j->bound_bytes;
                     const bool fits = make_room(std::min(bound, opts.hbm_cap_bytes - 0));
                     if (!fits && resident > 0) {   // wait for jobs in flight to go idle
                         ++it;
@@ -424,6 +456,20 @@ soptx_status soptx_serve_submit(soptx_server s, const soptx_request *r, uint64_t
     }
     s->cv_sched.notify_one();
     *ticket = q->ticket;
+    return SOPTX_OK;
+}
+
+soptx_status soptx_serve_mesh_bytes_bound(const soptx_request *r, int64_t *bytes)
+{
+    if (!r || !bytes) SOPTX_FAIL(SOPTX_EINVAL, "request / bytes is NULL");
+    if (r->dim < 2 || r->dim > 3 || (int)r->cell < SOPTX_TRI || (int)r->cell > SOPTX_HEX || r->order < 1 ||
+        r->order > 3 || r->n_cells < 0 || r->n_vertices < 1 || !r->coords || (r->n_cells > 0 && !r->cell_vertices))
+        SOPTX_FAIL(SOPTX_EINVAL, "malformed mesh description in the request");
+    try {
+        *bytes = mesh_bytes_bound(*r);
+    } catch (const std::bad_alloc &) {
+        SOPTX_FAIL(SOPTX_ENOMEM, "host allocation failed");
+    }
     return SOPTX_OK;
 }
 

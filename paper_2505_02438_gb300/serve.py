@@ -11,6 +11,31 @@ import torch
 from . import _native as N
 
 
+def _mesh_request(wl, coords, cells):
+    """A request whose mesh description is the workload's (device buffers unset)."""
+    r = N.Request()
+    r.dim = coords.shape[1]
+    r.cell = N.CELL[wl.cell]
+    r.order = int(wl.order)
+    r.n_vertices = coords.shape[0]
+    r.coords = coords.ctypes.data_as(ctypes.c_void_p)
+    r.n_cells = cells.shape[0]
+    r.cell_vertices = cells.ctypes.data_as(ctypes.c_void_p)
+    r.mat = N.Material(wl.E0, wl.Emin, wl.nu, wl.p, int(wl.plane_strain))
+    r.prec = N.PREC[getattr(wl, "elem_prec", "fp64")]
+    return r
+
+
+def mesh_bytes_bound(wl):
+    """The device bytes the server makes room for before it builds the mesh of
+    the workload `wl` (an upper bound of soptx_mesh_create's; host only)."""
+    coords = np.ascontiguousarray(wl.coords, np.float64)
+    cells = np.ascontiguousarray(wl.cells, np.int32)
+    b = ctypes.c_int64()
+    N.check(N.lib().soptx_serve_mesh_bytes_bound(ctypes.byref(_mesh_request(wl, coords, cells)), ctypes.byref(b)))
+    return b.value
+
+
 class Server:
     def __init__(self, hbm_cap_bytes=120 << 30, max_slots=16, n_streams=8, max_queue=4096, device=None,
                  group_small=True):
@@ -33,17 +58,8 @@ class Server:
             dc = torch.empty(nc, dtype=torch.float64, device=self.device)
         if c is None:
             c = torch.empty(1, dtype=torch.float64, device=self.device)
-        r = N.Request()
+        r = _mesh_request(wl, coords, cells)
         r.job = int(job)
-        r.dim = coords.shape[1]
-        r.cell = N.CELL[wl.cell]
-        r.order = int(wl.order)
-        r.n_vertices = coords.shape[0]
-        r.coords = coords.ctypes.data_as(ctypes.c_void_p)
-        r.n_cells = nc
-        r.cell_vertices = cells.ctypes.data_as(ctypes.c_void_p)
-        r.mat = N.Material(wl.E0, wl.Emin, wl.nu, wl.p, int(wl.plane_strain))
-        r.prec = N.PREC[getattr(wl, "elem_prec", "fp64")]
         r.d_rho = ctypes.c_void_p(rho.data_ptr())
         r.d_u = ctypes.c_void_p(u.data_ptr())
         r.d_vals = ctypes.c_void_p(vals.data_ptr()) if vals is not None else None

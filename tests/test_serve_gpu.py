@@ -61,6 +61,30 @@ def test_lowered_cap_evicts_idle_meshes(lib):
     assert stats["peak_resident_bytes"] <= cap
 
 
+def _rectangles(nx, ny):
+    coords, cells = W.structured_quad(nx, ny)
+    coords = coords.copy()
+    coords[:, 0] += 0.01 * coords[:, 0] ** 2
+    return coords, cells
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_admission_bound_covers_each_built_mesh(lib, prec):
+    """The bytes the server makes room for before building a job's mesh are at
+    least what soptx_mesh_create allocates, on every assembly route."""
+    from paper_2505_02438_gb300.serve import mesh_bytes_bound
+    g = np.random.default_rng(5)
+    cases = [("tri", 1, W.triangle_grid(60, 40, 0.2, g)), ("tri", 3, W.triangle_grid(40, 20, 0.2, g)),
+             ("quad", 3, _rectangles(30, 20)), ("quad", 2, W.quad_grid(20, 10, 0.2, g)),
+             ("tet", 2, W.kuhn_tets(6, 4, 4, 0.1, g)), ("hex", 1, W.structured_hex(20, 10, 10)),
+             ("hex", 2, W.structured_hex(6, 4, 4)), ("hex", 3, W.hex_grid(3, 3, 2, 0.1, g))]
+    for cell, k, (coords, cells) in cases:
+        wl = W.Workload("bound", cell, k, coords, cells, elem_prec=prec)
+        m = lib.Mesh.from_workload(wl)
+        assert mesh_bytes_bound(wl) >= m.device_bytes, (cell, k, m.routes)
+        m.close()
+
+
 def test_error_paths(lib):
     from paper_2505_02438_gb300 import _native as N
     from paper_2505_02438_gb300.serve import Server
