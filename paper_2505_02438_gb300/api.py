@@ -262,9 +262,10 @@ def host_pair_tables(cell, order, coords, cells, local_pair_bytes=False):
     N.check(L.soptx_host_pair_tables(*args, ctypes.byref(nt), ctypes.byref(nr), None, None, None, None, None, None))
     if nt.value < 0:
         return None
+    lanes = max(nt.value, 1) * 32
     out = dict(n_tiles=nt.value, tile_offsets=np.zeros(nt.value + 1, np.uint32),
-               pair_block=np.zeros(max(nt.value, 1) * 32, np.uint32), pair_block_t=np.zeros(max(nt.value, 1) * 32, np.uint32),
-               pair_meta=np.zeros(max(nt.value, 1) * 32, np.uint32), record_cell=np.zeros(max(nr.value, 1), np.int32),
+               pair_block=np.zeros(lanes, np.uint32), pair_block_t=np.zeros(lanes, np.uint32),
+               pair_meta=np.zeros(lanes, np.uint32), record_cell=np.zeros(max(nr.value, 1), np.int32),
                record_pair=np.zeros(max(nr.value, 1), np.uint16))
     ptr = lambda k: out[k].ctypes.data_as(ctypes.c_void_p)
     N.check(L.soptx_host_pair_tables(*args, None, None, ptr("tile_offsets"), ptr("pair_block"), ptr("pair_block_t"),

@@ -130,9 +130,10 @@ static soptx_status setup_strain(soptx_mesh_s &m, const RefElement &ref, cudaStr
         for (double x : w1) sf.push_back(split_pair(x));
         for (double x : val) sf.push_back(split_pair(x));
         for (double x : der) sf.push_back(split_pair(x));
-        for (int a = 0; a < h.nb; a++)
-            sf.push_back(make_float2((float)(ref.lat[(size_t)a][0] + n * ref.lat[(size_t)a][1] + n * n * ref.lat[(size_t)a][2]),
-                                     0.f));
+        for (int a = 0; a < h.nb; a++) {
+            const int *la = ref.lat[(size_t)a].data();
+            sf.push_back(make_float2((float)(la[0] + n * la[1] + n * n * la[2]), 0.f));
+        }
         s = upload(&m.d.ssf, sf, st, m.device_bytes, "1D factors of the rule");
     }
     if (s == SOPTX_OK) {
@@ -288,8 +289,8 @@ static bool build_pair_tables(const HostMesh &h, bool bytes, PairTables &T)
             const int64_t offb = h.node_off[(size_t)b];
             const int degb = (int)(h.node_off[(size_t)b + 1] - offb);
             const uint32_t pa = (uint32_t)(d * off + p), pb = sym ? (uint32_t)(d * offb + pba) : pa;
-            win.push_back(WPair{pa, pb, (uint32_t)c | ((uint32_t)(d * deg) << 10) | ((uint32_t)(d * (sym ? degb : deg)) << 21),
-                                wre.size()});
+            const uint32_t rla = (uint32_t)(d * deg), rlb = (uint32_t)(d * (sym ? degb : deg));
+            win.push_back(WPair{pa, pb, (uint32_t)c | rla << 10 | rlb << 21, wre.size()});
             wre.insert(wre.end(), te.begin() + sstart[(size_t)p], te.begin() + sstart[(size_t)p + 1]);
             wrm.insert(wrm.end(), tm.begin() + sstart[(size_t)p], tm.begin() + sstart[(size_t)p + 1]);
         }
@@ -382,7 +383,8 @@ static bool build_row_tables(const HostMesh &h, RowTables &T)
         std::vector<int64_t> start((size_t)cmax + 2, 0);
         for (int64_t n = 0; n < h.nn; n++) start[(size_t)(cmax - (h.inc_ptr[n + 1] - h.inc_ptr[n])) + 1]++;
         for (size_t c = 1; c < start.size(); c++) start[c] += start[c - 1];
-        for (int64_t n = 0; n < h.nn; n++) order[(size_t)start[(size_t)(cmax - (h.inc_ptr[n + 1] - h.inc_ptr[n]))]++] = (int32_t)n;
+        for (int64_t n = 0; n < h.nn; n++)
+            order[(size_t)start[(size_t)(cmax - (h.inc_ptr[n + 1] - h.inc_ptr[n]))]++] = (int32_t)n;
     }
     // Each node's cells as a chain: the next cell is the unvisited one that holds
     // the most of the nodes the group's lanes hold now (ties: the lowest cell id);
@@ -475,7 +477,8 @@ static bool build_row_tables(const HostMesh &h, RowTables &T)
         const int64_t n = order[(size_t)i], off = h.node_off[(size_t)n];
         const int32_t deg = (int32_t)(h.node_off[(size_t)n + 1] - off), q0 = h.inc_ptr[(size_t)n],
                       cnt = h.inc_ptr[(size_t)n + 1] - q0;
-        nrec[(size_t)i] = make_int4((int)(uint32_t)off, (int)(off >> 32), q0, (int)(((uint32_t)cnt << 16) | (uint32_t)deg));
+        nrec[(size_t)i] =
+            make_int4((int)(uint32_t)off, (int)(off >> 32), q0, (int)(((uint32_t)cnt << 16) | (uint32_t)deg));
     }
     return true;
 }
