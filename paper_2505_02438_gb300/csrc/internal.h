@@ -131,17 +131,18 @@ struct DeviceMesh {
     bool contract = false;         // the assembly takes k_contract_pairs (2D) or k_contract_rows (3D)
     float4 *cgeo = nullptr;        //   [nc][2 or 3] G and |det J| in FP32
     float *Mf = nullptr;           //   [nb][nb][4 or 12] reference integrals in FP32
-    // 2D: node pairs {a, b} (b = a, or b after a), in tiles of 32; also for the cached
-    // FP64 element matrices of 2D affine meshes (pcached: the pair kernel reads them)
+    // node pairs in tiles of 32 (2D: {a, b} with b = a or b after a; 3D: every
+    // ordered pair); also for the cached FP64 element matrices of 2D affine meshes
+    // (pcached) and the one element matrix of a uniform mesh (puniform)
     bool pcached = false;
     bool puniform = false;         //   the pair kernel over the one element matrix of a uniform mesh
     int64_t ptiles = 0;            //   tiles
     uint32_t *ptoff = nullptr;     //   [8 chunks + 16] first record of each tile / 32
-    uint32_t *pia = nullptr;       //   [256 chunks] value index of block (a, b) / 2
-    uint32_t *pib = nullptr;       //   [256 chunks] value index of block (b, a) / 2
+    uint32_t *pia = nullptr;       //   [256 chunks] value index of block (a, b) / d
+    uint32_t *pib = nullptr;       //   [256 chunks] value index of block (b, a) / d (3D: = pia)
     uint32_t *pmeta = nullptr;     //   [256 chunks] cells | a's row length << 10 | b's << 21
     int32_t *pre = nullptr;        //   per record: the cell (ascending per pair)
-    uint16_t *prm = nullptr;       //   per record: a_loc nb + b_loc (pcached: a_loc << 8 | b_loc)
+    uint16_t *prm = nullptr;       //   per record: a_loc nb + b_loc (pcached, puniform: a_loc << 8 | b_loc)
     float4 *pblk = nullptr;        //   pcached: per record its 2 x 2 block of K_e^0 (2 float4s)
     // 3D: each node's cells as a chain, walked by the node's group of lanes
     int4 *cnrec = nullptr;         //   [nn] nodes by incident-cell count, largest first: row block
