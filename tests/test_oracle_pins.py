@@ -627,6 +627,56 @@ def test_sensitivity_consistency_and_euler_identity(cell, k):
         assert math.isnan(cs)
 
 
+def _cell_volumes(cell, coords, cells):
+    """|e| from the vertices alone: simplices by the determinant of their edge
+    vectors, parallelograms / parallelepipeds (corners lexicographic, x
+    fastest) by that of the edges from corner 0."""
+    x = coords[cells]
+    if cell == "tri":
+        return np.abs(np.linalg.det(np.stack([x[:, 1] - x[:, 0], x[:, 2] - x[:, 0]], 1))) / 2
+    if cell == "tet":
+        return np.abs(np.linalg.det(np.stack([x[:, m] - x[:, 0] for m in (1, 2, 3)], 1))) / 6
+    if cell == "quad":
+        return np.abs(np.linalg.det(np.stack([x[:, 1] - x[:, 0], x[:, 2] - x[:, 0]], 1)))
+    return np.abs(np.linalg.det(np.stack([x[:, 1] - x[:, 0], x[:, 2] - x[:, 0], x[:, 4] - x[:, 0]], 1)))
+
+
+@pytest.mark.parametrize("cell,k", [("tri", 1), ("tri", 2), ("tri", 3), ("tet", 1), ("tet", 2), ("tet", 3),
+                                    ("quad", 1), ("quad", 2), ("quad", 3), ("hex", 1), ("hex", 2), ("hex", 3)])
+def test_sensitivity_of_an_affine_field_cell_by_cell(cell, k):
+    """u = A x + b is reproduced by every element space, so its strain eps =
+    (A + A^T) / 2 is constant and each cell's s_e = u_e^T K_e^0 u_e equals
+    |e| (lam (tr eps)^2 + 2 mu eps:eps) at unit modulus -- cell by cell, with
+    |e| from the vertices and lam, mu from the plane-stress / plane-strain /
+    3D formulas."""
+    g = np.random.default_rng(17)
+    d = W.DIM[cell]
+    if cell in ("tri", "tet"):
+        coords, cells = small_mesh(cell, jitter=0.15, seed=3)
+    else:
+        coords, cells = small_mesh(cell)
+        B = np.eye(d) + 0.3 * g.uniform(-1, 1, (d, d))   # parallelograms / parallelepipeds
+        coords = coords @ B.T
+    xn = oracle.node_coords(cell, k, coords, cells)
+    A, b = g.standard_normal((d, d)), g.standard_normal(d)
+    u = (xn @ A.T + b).ravel()
+    eps = (A + A.T) / 2
+    rho = g.uniform(0.1, 1.0, len(cells))
+    vol = _cell_volumes(cell, coords, cells)
+    assert np.all(vol > 0)
+    for nu, ps in ((0.3, 0), (0.25, 1)):
+        if d == 3 or ps:
+            lam = nu / ((1 + nu) * (1 - 2 * nu))
+        else:
+            lam = nu / (1 - nu * nu)
+        mu = 1 / (2 * (1 + nu))
+        want = vol * (lam * np.trace(eps) ** 2 + 2 * mu * np.sum(eps * eps))
+        dc, s, c = oracle.sensitivity(cell, k, coords, cells, (1.0, 1e-9, nu, 3.0, ps), rho, u)
+        np.testing.assert_allclose(s, want, rtol=1e-11, atol=1e-12 * want.max())
+        E = 1e-9 + rho ** 3 * (1.0 - 1e-9)
+        assert abs(c - np.dot(E, want)) < 1e-11 * np.dot(E, want)
+
+
 def test_compliance_vjp_central_differences():
     """f(rho) = u^T K(rho) u is cubic in each rho_e (p = 3), so the central
     difference error is exactly (E0 - Emin) s_e h^2 plus rounding."""
