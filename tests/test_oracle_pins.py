@@ -637,22 +637,30 @@ def _cell_volumes(cell, coords, cells):
     if cell == "tet":
         return np.abs(np.linalg.det(np.stack([x[:, m] - x[:, 0] for m in (1, 2, 3)], 1))) / 6
     if cell == "quad":
-        return np.abs(np.linalg.det(np.stack([x[:, 1] - x[:, 0], x[:, 2] - x[:, 0]], 1)))
+        # the polygon 0, 1, 3, 2 (shoelace): a bilinear cell has straight edges
+        p = x[:, [0, 1, 3, 2]]
+        q = np.roll(p, -1, axis=1)
+        return np.abs(np.sum(p[..., 0] * q[..., 1] - q[..., 0] * p[..., 1], axis=1)) / 2
     return np.abs(np.linalg.det(np.stack([x[:, 1] - x[:, 0], x[:, 2] - x[:, 0], x[:, 4] - x[:, 0]], 1)))
 
 
-@pytest.mark.parametrize("cell,k", [("tri", 1), ("tri", 2), ("tri", 3), ("tet", 1), ("tet", 2), ("tet", 3),
-                                    ("quad", 1), ("quad", 2), ("quad", 3), ("hex", 1), ("hex", 2), ("hex", 3)])
-def test_sensitivity_of_an_affine_field_cell_by_cell(cell, k):
-    """u = A x + b is reproduced by every element space, so its strain eps =
-    (A + A^T) / 2 is constant and each cell's s_e = u_e^T K_e^0 u_e equals
-    |e| (lam (tr eps)^2 + 2 mu eps:eps) at unit modulus -- cell by cell, with
-    |e| from the vertices and lam, mu from the plane-stress / plane-strain /
-    3D formulas."""
+@pytest.mark.parametrize("cell,k,general", [
+    ("tri", 1, False), ("tri", 2, False), ("tri", 3, False), ("tet", 1, False), ("tet", 2, False),
+    ("tet", 3, False), ("quad", 1, False), ("quad", 2, False), ("quad", 3, False), ("hex", 1, False),
+    ("hex", 2, False), ("hex", 3, False), ("quad", 1, True), ("quad", 2, True), ("quad", 3, True)])
+def test_sensitivity_of_an_affine_field_cell_by_cell(cell, k, general):
+    """u = A x + b is reproduced by every element space (on general
+    quadrilaterals too: x and y are in the span of the bilinear map), so its
+    strain eps = (A + A^T) / 2 is constant and each cell's s_e = u_e^T K_e^0 u_e
+    equals |e| (lam (tr eps)^2 + 2 mu eps:eps) at unit modulus -- cell by cell,
+    with |e| from the vertices and lam, mu from the plane-stress /
+    plane-strain / 3D formulas."""
     g = np.random.default_rng(17)
     d = W.DIM[cell]
     if cell in ("tri", "tet"):
         coords, cells = small_mesh(cell, jitter=0.15, seed=3)
+    elif general:
+        coords, cells = W.quad_grid(4, 3, 0.2, g)
     else:
         coords, cells = small_mesh(cell)
         B = np.eye(d) + 0.3 * g.uniform(-1, 1, (d, d))   # parallelograms / parallelepipeds
