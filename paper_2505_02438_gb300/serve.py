@@ -9,6 +9,17 @@ import numpy as np
 import torch
 
 from . import _native as N
+from .api import _dptr
+
+
+def _cuda_f64(t, name):
+    """A contiguous FP64 CUDA tensor whose length only the mesh fixes (u holds
+    ndof values, vals nnz: the caller sizes them from the job's mesh)."""
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("%s must be a contiguous torch.float64 tensor" % name)
+    return ctypes.c_void_p(t.data_ptr())
 
 
 def _mesh_request(wl, coords, cells):
@@ -60,11 +71,11 @@ class Server:
             c = torch.empty(1, dtype=torch.float64, device=self.device)
         r = _mesh_request(wl, coords, cells)
         r.job = int(job)
-        r.d_rho = ctypes.c_void_p(rho.data_ptr())
-        r.d_u = ctypes.c_void_p(u.data_ptr())
-        r.d_vals = ctypes.c_void_p(vals.data_ptr()) if vals is not None else None
-        r.d_dc = ctypes.c_void_p(dc.data_ptr())
-        r.d_c = ctypes.c_void_p(c.data_ptr())
+        r.d_rho = _dptr(rho, torch.float64, nc, "rho")
+        r.d_u = _cuda_f64(u, "u")
+        r.d_vals = _cuda_f64(vals, "vals") if vals is not None else None
+        r.d_dc = _dptr(dc, torch.float64, nc, "dc")
+        r.d_c = _dptr(c, torch.float64, 1, "c")
         t = ctypes.c_uint64()
         N.check(N.lib().soptx_serve_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
         self._keep[t.value] = (coords, cells, rho, u, vals, dc, c)
