@@ -71,3 +71,14 @@ def test_malformed_request_rejected():
     b = ctypes.c_int64()
     assert N.lib().soptx_serve_mesh_bytes_bound(ctypes.byref(r), ctypes.byref(b)) == 1
     assert N.lib().soptx_serve_mesh_bytes_bound(None, ctypes.byref(b)) == 1
+
+
+def test_ids_out_of_range_are_skipped():
+    """The bound reads the cell array before mesh creation validates it: ids
+    outside [0, n_vertices) are skipped there (creation then rejects the mesh)."""
+    from paper_2505_02438_gb300.serve import mesh_bytes_bound
+    coords, cells = W.triangle_grid(6, 4, 0.0)
+    bad = cells.copy()
+    bad[0, 0], bad[1, 2] = 10 ** 6, -5
+    good = mesh_bytes_bound(W.Workload("t", "tri", 2, coords, cells))
+    assert 0 < mesh_bytes_bound(W.Workload("t", "tri", 2, coords, bad)) <= good
